@@ -1,0 +1,205 @@
+"""Plain serial CPU oracle for the Poisson-asynchronous Glauber cellular array.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
+and the CPU-baseline / reference leg of ``bench.py`` may import this package.
+The library (``paper_cs_0502039_gb300``) never imports it, and nothing here
+imports the library: the two implement the same definitions independently.
+
+The arithmetic lives in ``ac_oracle.c`` (plain C99, compiled with gcc by
+:func:`build`); this module only marshals numpy arrays through ctypes.
+
+What it computes -- Lubachevsky, Sec. 1 (Poisson asynchrony, Glauber's
+continuous-time Ising model), Sec. 2 Eqs. (1)-(2), Sec. 3 Eq. (5) and the
+per-cell-stream remark after Fig. 3.6: all arrivals of all cells processed in
+global (tick, cell index) order from a binary heap, each seeing the spins
+just before it.  The spec readings R1-R7 are listed in ``ac_oracle.c``.
+
+Pins (tests/test_oracle_*.py, all CPU):
+  philox4x32_10   -- against triton's Philox4x32-10 (interpreter mode).
+  exp_ticks       -- against binary64 -ln u (|err| <= 8 ticks), monotone,
+                     ln 2 constant recomputed in exact decimal arithmetic.
+  thresholds      -- detailed balance, beta = 0, spin-flip symmetry,
+                     the appendix's x/(1+x) form.
+  run             -- brute-force linear-scan simulator (bit-exact), exact
+                     2x2 / 3x3 chain enumeration (stationary Boltzmann law,
+                     transient P0 exp(QT)), Poisson(T) counts, beta = 0
+                     closed form, Onsager energy and magnetisation.
+  time_rounds     -- round-1 fraction 1/5, long-run fraction ~0.121 (Sec. 4).
+  observables, checksum -- brute-force recomputation in numpy.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ac_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libacoracle.so")
+
+TICKS_PER_UNIT = 1 << 32
+INIT_RANDOM, INIT_UP, INIT_DOWN = 0, 1, 2
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ac_oracle.c into oracle/_build/libacoracle.so (gcc, -O2)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=gnu99", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+           _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    _lib = _bind(ctypes.CDLL(build()))
+    return _lib
+
+
+def _bind(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    P = ctypes.c_void_p
+    lib.aco_philox4x32_10.argtypes = [P, P, P]
+    lib.aco_philox4x32_10.restype = None
+    lib.aco_exp_ticks.argtypes = [ctypes.c_uint32]
+    lib.aco_exp_ticks.restype = ctypes.c_uint64
+    lib.aco_thresholds.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, P]
+    lib.aco_thresholds.restype = None
+    lib.aco_init.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, P, P, P]
+    lib.aco_init.restype = None
+    lib.aco_run.argtypes = [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_uint64, P, P, P, ctypes.c_int64]
+    lib.aco_run.restype = ctypes.c_int64
+    lib.aco_time_rounds.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, P, P,
+                                    ctypes.c_int64, ctypes.c_int64, P]
+    lib.aco_time_rounds.restype = ctypes.c_int64
+    lib.aco_observables.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P]
+    lib.aco_observables.restype = None
+    lib.aco_checksum.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P]
+    lib.aco_checksum.restype = ctypes.c_uint64
+    lib.aco_exp_ticks_many.argtypes = [P, P, ctypes.c_int64]
+    lib.aco_exp_ticks_many.restype = None
+    lib.aco_philox_blocks.argtypes = [ctypes.c_uint64, P, P, ctypes.c_uint32, P, ctypes.c_int64]
+    lib.aco_philox_blocks.restype = None
+    return lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of one 4-word counter under a 2-word key -> uint32[4]."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.aco_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def exp_ticks(x: int) -> int:
+    """Integer exponential gap (ticks) for a 32-bit uniform word x."""
+    return int(_load().aco_exp_ticks(ctypes.c_uint32(int(x) & 0xFFFFFFFF)))
+
+
+def exp_ticks_many(xs) -> np.ndarray:
+    """exp_ticks over an array of 32-bit words -> uint64 array."""
+    x = np.ascontiguousarray(xs, dtype=np.uint32)
+    out = np.zeros(x.shape, dtype=np.uint64)
+    _load().aco_exp_ticks_many(_ptr(x), _ptr(out), x.size)
+    return out
+
+
+def philox_blocks(seed: int, cells, ks, w2: int = 0) -> np.ndarray:
+    """Philox({c, k, w2, 0}) under key (seed lo, seed hi) for arrays c, k -> uint32[n, 4]."""
+    c = np.ascontiguousarray(cells, dtype=np.uint32)
+    k = np.ascontiguousarray(np.broadcast_to(ks, c.shape), dtype=np.uint32)
+    out = np.zeros((c.size, 4), dtype=np.uint32)
+    _load().aco_philox_blocks(int(seed) & (2**64 - 1), _ptr(c), _ptr(k), int(w2), _ptr(out), c.size)
+    return out
+
+
+def thresholds(beta: float, J: float = 1.0, h: float = 0.0) -> np.ndarray:
+    """uint32[10] flip thresholds, index j + 5*(s>0), j = number of up neighbours."""
+    out = np.zeros(10, dtype=np.uint32)
+    _load().aco_thresholds(float(beta), float(J), float(h), _ptr(out))
+    return out
+
+
+class State:
+    """A lattice state: spins int8, next-arrival ticks int64, event counts uint32."""
+
+    def __init__(self, rows: int, cols: int, s: np.ndarray, t: np.ndarray, n: np.ndarray):
+        self.rows, self.cols = int(rows), int(cols)
+        self.s, self.t, self.n = s, t, n
+
+    def copy(self) -> "State":
+        return State(self.rows, self.cols, self.s.copy(), self.t.copy(), self.n.copy())
+
+
+def init(rows: int, cols: int, init_mode: int, seed: int) -> State:
+    """Initial state from the seed (readings R3, R4)."""
+    if rows < 2 or cols < 2:
+        raise ValueError("rows and cols must be >= 2")
+    N = rows * cols
+    s = np.zeros(N, dtype=np.int8)
+    t = np.zeros(N, dtype=np.int64)
+    n = np.zeros(N, dtype=np.uint32)
+    _load().aco_init(rows, cols, int(init_mode), int(seed) & (2**64 - 1), _ptr(s), _ptr(t), _ptr(n))
+    return State(rows, cols, s, t, n)
+
+
+def run(state: State, thr: np.ndarray, seed: int, t_end: int) -> int:
+    """Advance ``state`` in place until every tick >= t_end; returns events committed."""
+    thr = np.ascontiguousarray(thr, dtype=np.uint32)
+    ev = _load().aco_run(state.rows, state.cols, _ptr(thr), int(seed) & (2**64 - 1),
+                         _ptr(state.s), _ptr(state.t), _ptr(state.n), int(t_end))
+    if ev < 0:
+        raise MemoryError("oracle heap allocation failed")
+    return int(ev)
+
+
+def simulate(rows: int, cols: int, beta: float, J: float, h: float, seed: int, T: float,
+             init_mode: int = INIT_RANDOM) -> State:
+    """Fresh lattice run to time T (t_end = T * 2^32 ticks, rounded down)."""
+    st = init(rows, cols, init_mode, seed)
+    run(st, thresholds(beta, J, h), seed, int(T * TICKS_PER_UNIT))
+    return st
+
+
+def time_rounds(state: State, seed: int, t_end: int, max_rounds: int = 1 << 20):
+    """Time-only synchronous rounds (Sec. 4 model of Fig. 3.2); advances state.t/.n in place.
+
+    Returns int64 array with the number of advancing cells in each round.
+    """
+    buf = np.zeros(max_rounds, dtype=np.int64)
+    r = _load().aco_time_rounds(state.rows, state.cols, int(seed) & (2**64 - 1), _ptr(state.t),
+                                _ptr(state.n), int(t_end), int(max_rounds), _ptr(buf))
+    if r < 0:
+        raise MemoryError("oracle allocation failed")
+    return buf[:min(r, max_rounds)].copy()
+
+
+def observables(state: State):
+    """(sum of spins, sum over right+down bonds of s s')."""
+    out = np.zeros(2, dtype=np.int64)
+    _load().aco_observables(state.rows, state.cols, _ptr(state.s), _ptr(out))
+    return int(out[0]), int(out[1])
+
+
+def checksum(state: State) -> int:
+    """Order-independent 64-bit fingerprint of (s, t, n)."""
+    return int(_load().aco_checksum(state.rows, state.cols, _ptr(state.s), _ptr(state.t),
+                                    _ptr(state.n)))

@@ -1,0 +1,342 @@
+/*
+ * ac_oracle.c -- plain serial CPU oracle for the Poisson-asynchronous Glauber
+ * (continuous-time Ising) cellular array of Lubachevsky, "Efficient Parallel
+ * Simulations of Asynchronous Cellular Arrays".
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * definition that the GPU kernels are checked against.  Only the test suite,
+ * the package smoke check and the benchmark's CPU-baseline leg may load it;
+ * the library's product path never calls, links or includes it, and it
+ * includes nothing from the library.
+ *
+ * What it computes (Sec. 1 "Poisson asynchrony"; Sec. 2, Eqs. (1)-(2)):
+ *   every cell of a rows x cols torus owns an independent rate-1 Poisson
+ *   clock; at each arrival the cell's spin is re-drawn by the Glauber
+ *   heat-bath rule from the spins of its four neighbours just before the
+ *   arrival.  The standard serial procedure of Sec. 1 (arrivals handled one
+ *   at a time in global time order) with one random stream per cell
+ *   (Sec. 3, invariance remark after Fig. 3.6) is implemented literally:
+ *   a binary min-heap over the cells, keyed by (next-arrival tick, cell
+ *   index), is popped until the top tick reaches t_end.
+ *
+ * Readings of points the paper leaves open (each also listed in the design
+ * notes of the repository):
+ *   R1 order   strict total order on (tick, row-major index); on equal
+ *              ticks the smaller index goes first (the paper assumes no
+ *              ties, Sec. 3 condition (ii)).
+ *   R2 end     arrivals with tick < t_end are committed; after a run every
+ *              cell's tick is its first uncommitted arrival, >= t_end
+ *              (Fig. 3.1 loop condition "t(c) < end_time").
+ *   R3 first   the first arrival is at t0 = exp_ticks(B(c,0).x) > 0, a
+ *              plain Poisson process (the appendix program's extra event at
+ *              time 0 is not reproduced).
+ *   R4 random  Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
+ *              (seed & 0xffffffff, seed >> 32).  Event block
+ *              B(c,k) = Philox({c, k, 0, 0}); init block I(c) =
+ *              Philox({c, 0, 1, 0}).  The commit of arrival n (n = 0,1,..)
+ *              draws B(c, n+1): .y is its acceptance uniform and .x the gap
+ *              to arrival n+1.  Random initial spin = +1 iff I(c).x is odd.
+ *              This is the "each PE its own reproducible sequence" of
+ *              Sec. 5, refined to one counter stream per cell.
+ *   R5 gap     exp_ticks(x): an all-integer stand-in for -ln r in Eq. (5)
+ *              with 2^32 ticks per unit time (see exp_ticks below).
+ *   R6 table   p = 1 / (1 + exp(beta * dE)), dE = 2 s (J S + h), in IEEE
+ *              binary64; thr = min(floor(p * 2^32), 2^32 - 1); flip iff
+ *              u32 < thr.  Same probabilities as the appendix's x/(1+x),
+ *              x = exp(-dE/T).  Index j + 5*(s > 0), j = number of up
+ *              neighbours, as in the appendix's prob[10].
+ *   R7 nbrs    4 nearest neighbours on the periodic torus, counted with
+ *              multiplicity (on a 2-wide torus both sides are one cell).
+ *
+ * Build: plain C99 + libm, -O2 -ffp-contract=off (no fused multiply-add, so
+ * the binary64 table is the same on every host).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al., SC'11, Sec. on the Philox family).   */
+/* One round: two 32x32->64 products of the even counter words with   */
+/* the round multipliers; the high halves are xored with the odd words */
+/* and the round key, the words are permuted; the key is bumped by the */
+/* Weyl increments between rounds.                                     */
+/* ------------------------------------------------------------------ */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void aco_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void philox_block(uint64_t seed, uint32_t c, uint32_t w1, uint32_t w2, uint32_t out[4])
+{
+    uint32_t ctr[4] = {c, w1, w2, 0u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    aco_philox4x32_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* exp_ticks(x): integer exponential gap, reading R5.                  */
+/*   m  = 2x + 1 (odd), so u = m / 2^33 lies strictly inside (0, 1);   */
+/*   k  = floor(log2 m);  y = m scaled to a Q1.31 mantissa in           */
+/*        [2^31, 2^32) (truncating when k = 32);                        */
+/*   32 fraction bits of log2(y / 2^31) by repeated squaring: square,   */
+/*        keep Q1.31 (truncate), and when the square reaches 2 emit a   */
+/*        1 bit and halve (the textbook bit-by-bit binary logarithm);   */
+/*   lg = k + f / 2^32 ~ log2 m;  nl = 33 - lg ~ -log2 u  (Q.32, >= 1); */
+/*   gap = floor(nl * ln2 * 2^64 / 2^64) + 1 ticks, with               */
+/*        LN2_Q64 = floor(ln 2 * 2^64) and an exact 128-bit product.   */
+/* The +1 keeps next_t > t (Eq. (2)).                                  */
+/* ------------------------------------------------------------------ */
+#define LN2_Q64 0xB17217F7D1CF79ABull
+
+uint64_t aco_exp_ticks(uint32_t x)
+{
+    uint64_t m = 2ull * (uint64_t)x + 1ull;
+    int k = 0;
+    while ((m >> (k + 1)) != 0) ++k;            /* k = floor(log2 m), 0..32 */
+    uint64_t y = (k >= 31) ? (m >> (k - 31)) : (m << (31 - k));
+    uint64_t f = 0;
+    for (int i = 0; i < 32; ++i) {
+        y = (y * y) >> 31;
+        f <<= 1;
+        if (y >= (1ull << 32)) {
+            y >>= 1;
+            f |= 1ull;
+        }
+    }
+    uint64_t lg = ((uint64_t)k << 32) | f;
+    uint64_t nl = (33ull << 32) - lg;
+    unsigned __int128 prod = (unsigned __int128)nl * (unsigned __int128)LN2_Q64;
+    return (uint64_t)(prod >> 64) + 1ull;
+}
+
+/* ------------------------------------------------------------------ */
+/* Flip-threshold table, reading R6 (appendix, flip probabilities).   */
+/* ------------------------------------------------------------------ */
+void aco_thresholds(double beta, double J, double h, uint32_t thr[10])
+{
+    for (int sp = 0; sp < 2; ++sp) {
+        double s = sp ? 1.0 : -1.0;
+        for (int j = 0; j < 5; ++j) {
+            double S = (double)(2 * j - 4);
+            double dE = 2.0 * s * (J * S + h);
+            double p = 1.0 / (1.0 + exp(beta * dE));
+            double v = ldexp(p, 32);
+            uint32_t t;
+            if (!(v < 4294967295.0))
+                t = 0xFFFFFFFFu;          /* p = 1 (or NaN): saturate */
+            else
+                t = (uint32_t)floor(v);
+            thr[j + 5 * sp] = t;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Initial state (readings R3, R4).  init: 0 random, 1 all up, 2 down. */
+/* ------------------------------------------------------------------ */
+void aco_init(int32_t rows, int32_t cols, int32_t init, uint64_t seed,
+              int8_t *s, int64_t *t, uint32_t *n)
+{
+    uint64_t N = (uint64_t)rows * (uint64_t)cols;
+    for (uint64_t c = 0; c < N; ++c) {
+        uint32_t b0[4], ib[4];
+        philox_block(seed, (uint32_t)c, 0u, 0u, b0);
+        if (init == 1)
+            s[c] = 1;
+        else if (init == 2)
+            s[c] = -1;
+        else {
+            philox_block(seed, (uint32_t)c, 0u, 1u, ib);
+            s[c] = (ib[0] & 1u) ? 1 : -1;
+        }
+        t[c] = (int64_t)aco_exp_ticks(b0[0]);
+        n[c] = 0u;
+    }
+}
+
+/* Torus neighbours of c in the order up, down, left, right. */
+static void neighbours(int32_t rows, int32_t cols, uint64_t c, uint64_t nb[4])
+{
+    int64_t r = (int64_t)(c / (uint64_t)cols), q = (int64_t)(c % (uint64_t)cols);
+    nb[0] = (uint64_t)(((r - 1 + rows) % rows) * cols + q);
+    nb[1] = (uint64_t)(((r + 1) % rows) * cols + q);
+    nb[2] = (uint64_t)(r * cols + (q - 1 + cols) % cols);
+    nb[3] = (uint64_t)(r * cols + (q + 1) % cols);
+}
+
+/* ------------------------------------------------------------------ */
+/* Binary min-heap over cells keyed by (t[c], c)  (reading R1).        */
+/* ------------------------------------------------------------------ */
+static int key_less(const int64_t *t, uint32_t a, uint32_t b)
+{
+    return (t[a] < t[b]) || (t[a] == t[b] && a < b);
+}
+
+static void sift_down(uint32_t *heap, uint64_t size, uint64_t i, const int64_t *t)
+{
+    for (;;) {
+        uint64_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < size && key_less(t, heap[l], heap[m])) m = l;
+        if (r < size && key_less(t, heap[r], heap[m])) m = r;
+        if (m == i) return;
+        uint32_t tmp = heap[i]; heap[i] = heap[m]; heap[m] = tmp;
+        i = m;
+    }
+}
+
+/*
+ * Continue the trajectory from state (s, t, n) until every cell's next
+ * arrival is >= t_end (reading R2).  Returns the number of committed
+ * arrivals, or -1 if the heap could not be allocated.
+ */
+int64_t aco_run(int32_t rows, int32_t cols, const uint32_t thr[10], uint64_t seed,
+                int8_t *s, int64_t *t, uint32_t *n, int64_t t_end)
+{
+    uint64_t N = (uint64_t)rows * (uint64_t)cols;
+    uint32_t *heap = (uint32_t *)malloc(N * sizeof(uint32_t));
+    if (!heap) return -1;
+    for (uint64_t c = 0; c < N; ++c) heap[c] = (uint32_t)c;
+    for (uint64_t i = N / 2; i-- > 0;) sift_down(heap, N, i, t);
+
+    int64_t events = 0;
+    while (t[heap[0]] < t_end) {
+        uint32_t c = heap[0];
+        uint64_t nb[4];
+        neighbours(rows, cols, c, nb);
+        int up = 0;                                   /* spins just before t(c) */
+        for (int d = 0; d < 4; ++d) up += (s[nb[d]] > 0);
+        uint32_t b[4];
+        philox_block(seed, c, n[c] + 1u, 0u, b);
+        if (b[1] < thr[up + 5 * (s[c] > 0)]) s[c] = (int8_t)(-s[c]);  /* Eq. (1) */
+        t[c] += (int64_t)aco_exp_ticks(b[0]);                          /* Eq. (5) */
+        n[c] += 1u;
+        sift_down(heap, N, 0, t);
+        ++events;
+    }
+    free(heap);
+    return events;
+}
+
+/* ------------------------------------------------------------------ */
+/* Time-only round model of Sec. 4 applied to the synchronous          */
+/* one-cell-per-PE algorithm (Fig. 3.2): in each round every cell whose */
+/* key is below all of its neighbours' keys and whose tick is < t_end   */
+/* advances its time; only times are tracked (for the Ising law the     */
+/* next arrival does not depend on the spins).  The per-round number of */
+/* advancing cells is written to enabled[] (up to max_rounds entries).  */
+/* Returns the number of rounds with at least one advancing cell.       */
+/* ------------------------------------------------------------------ */
+int64_t aco_time_rounds(int32_t rows, int32_t cols, uint64_t seed, int64_t *t, uint32_t *n,
+                        int64_t t_end, int64_t max_rounds, int64_t *enabled)
+{
+    uint64_t N = (uint64_t)rows * (uint64_t)cols;
+    uint8_t *en = (uint8_t *)malloc(N);
+    if (!en) return -1;
+    int64_t rounds = 0;
+    for (;;) {
+        int64_t cnt = 0;
+        for (uint64_t c = 0; c < N; ++c) {
+            uint64_t nb[4];
+            neighbours(rows, cols, c, nb);
+            int ok = t[c] < t_end;
+            for (int d = 0; d < 4 && ok; ++d)
+                if (!key_less(t, (uint32_t)c, (uint32_t)nb[d])) ok = 0;
+            en[c] = (uint8_t)ok;
+            cnt += ok;
+        }
+        if (cnt == 0) break;
+        for (uint64_t c = 0; c < N; ++c) {
+            if (!en[c]) continue;
+            uint32_t b[4];
+            philox_block(seed, (uint32_t)c, n[c] + 1u, 0u, b);
+            t[c] += (int64_t)aco_exp_ticks(b[0]);
+            n[c] += 1u;
+        }
+        if (rounds < max_rounds) enabled[rounds] = cnt;
+        ++rounds;
+    }
+    free(en);
+    return rounds;
+}
+
+/* ------------------------------------------------------------------ */
+/* Observables and a state fingerprint.                                */
+/* Energy  E = -J sum_bonds s s' - h sum s  over right and down bonds   */
+/* (appendix, energy comment), with the same multiplicity as the        */
+/* neighbour sum.  out[0] = sum s, out[1] = sum over bonds of s s'.     */
+/* ------------------------------------------------------------------ */
+void aco_observables(int32_t rows, int32_t cols, const int8_t *s, int64_t out[2])
+{
+    int64_t m = 0, b = 0;
+    for (int64_t r = 0; r < rows; ++r)
+        for (int64_t q = 0; q < cols; ++q) {
+            int64_t c = r * cols + q;
+            m += s[c];
+            b += (int64_t)s[c] * s[r * cols + (q + 1) % cols];
+            b += (int64_t)s[c] * s[((r + 1) % rows) * cols + q];
+        }
+    out[0] = m;
+    out[1] = b;
+}
+
+/* SplitMix64 finaliser (Steele, Lea, Flood, OOPSLA'14) used as a mixer. */
+static uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/*
+ * Order-independent fingerprint of a full state:
+ *   sum over cells c of mix(mix(mix(c) ^ t[c]) ^ (2 n[c] + [s[c] > 0]))  (mod 2^64).
+ */
+uint64_t aco_checksum(int32_t rows, int32_t cols, const int8_t *s, const int64_t *t,
+                      const uint32_t *n)
+{
+    uint64_t N = (uint64_t)rows * (uint64_t)cols, acc = 0;
+    for (uint64_t c = 0; c < N; ++c) {
+        uint64_t z = mix64(c);
+        z = mix64(z ^ (uint64_t)t[c]);
+        z = mix64(z ^ ((uint64_t)n[c] << 1 | (uint64_t)(s[c] > 0)));
+        acc += z;
+    }
+    return acc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Batch helpers for tests (loops over the scalar definitions above).  */
+/* ------------------------------------------------------------------ */
+void aco_exp_ticks_many(const uint32_t *x, uint64_t *out, int64_t count)
+{
+    for (int64_t i = 0; i < count; ++i) out[i] = aco_exp_ticks(x[i]);
+}
+
+/* out[4*i .. 4*i+3] = Philox({c[i], k[i], w2, 0}) under the seed's key. */
+void aco_philox_blocks(uint64_t seed, const uint32_t *c, const uint32_t *k, uint32_t w2,
+                       uint32_t *out, int64_t count)
+{
+    for (int64_t i = 0; i < count; ++i) philox_block(seed, c[i], k[i], w2, out + 4 * i);
+}
