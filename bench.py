@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: committed cell events per second of the exact parallel
+simulator of the Poisson-asynchronous Glauber (continuous-time Ising) array.
+
+Workload (one step): the 4096 x 4096 periodic Ising torus at beta = 0.30,
+0.4407 and 0.60 (J = 1, h = 0, random +-1 initial spins from seed 7, Poisson
+rate 1 per cell, 2^32 ticks per unit time), each initialised on the device and
+run to T = 50 -- about 2.5e9 committed arrivals per step, all bit-exact against
+the serial oracle (tests/).  The three lattices run in one graph-captured
+launch of the blocked persistent kernel.  The state (3 x 201 MB) is larger than
+the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores on a bounded prefix of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+T32 = 1 << 32
+BYTES_PER_EVENT = 26          # read + write of a cell's 13-byte state (int8 spin, int64 tick, uint32 count)
+WORKLOAD = dict(name="ising4096x4096_T50", rows=4096, cols=4096, betas=[0.30, 0.4407, 0.60], J=1.0, h=0.0,
+                seed=7, init=0, T=50)
+CPU_SAMPLE_T = 0.5            # oracle sample: time prefix [0, 0.5) of the beta = 0.4407 lattice
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--kernel", default="blocked", choices=["blocked", "round"])
+    ap.add_argument("--lb", type=int, default=64)
+    ap.add_argument("--rounds", type=int, default=1, help="round kernel: rounds per launch; blocked: refresh")
+    ap.add_argument("--polls", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the per-kernel side measurements")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("ac_kernels.cu", "ac_device.cuh"):
+        with open(os.path.join(ROOT, "paper_cs_0502039_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def committed_traffic(kernel_name, lb):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(f"{kernel_name}_lb{lb}")
+    if not ent or ent.get("source_sha256") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch_full")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(sample_T=CPU_SAMPLE_T):
+    import oracle
+    w = WORKLOAD
+    st = oracle.init(w["rows"], w["cols"], w["init"], w["seed"])
+    thr = oracle.thresholds(0.4407, w["J"], w["h"])
+    t0 = time.perf_counter()
+    ev = oracle.run(st, thr, w["seed"], int(sample_T * T32))
+    dt = time.perf_counter() - t0
+    return {"value": ev / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+            "sample": f"{w['rows']}x{w['cols']} beta=0.4407 seed {w['seed']}, arrivals in [0, {sample_T}) "
+                      f"({ev} events, {dt:.1f} s, single-threaded C heap simulator)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w = WORKLOAD
+    sample_T = 0.25
+    times, evs = [], []
+    for i in range(args.warmup + args.steps):
+        st = oracle.init(w["rows"], w["cols"], w["init"], w["seed"])
+        thr = oracle.thresholds(0.4407, w["J"], w["h"])
+        t0 = time.perf_counter()
+        ev = oracle.run(st, thr, w["seed"], int(sample_T * T32))
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            evs.append(ev)
+    value = sum(evs) / sum(times)
+    sample = (f"{w['rows']}x{w['cols']} beta=0.4407 seed {w['seed']}, arrivals in [0, {sample_T}) per step "
+              f"(~{evs[0]} events), single-threaded C heap oracle")
+    out = {"metric": "cell_events_per_sec", "value": value, "unit": "events/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": w["name"], "rows": w["rows"], "cols": w["cols"], "betas": w["betas"],
+                      "T": w["T"], "sample": sample},
+           "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import paper_cs_0502039_gb300 as ac
+
+    w = WORKLOAD
+    kern = ac.AC_KERNEL_BLOCKED if args.kernel == "blocked" else ac.AC_KERNEL_ROUND
+    # weak scaling: every rank runs its own replica batch (seed offset by rank)
+    seed = w["seed"] + 1000 * rank
+    sims = [ac.Sim(w["rows"], w["cols"], b, w["J"], w["h"], seed, init=w["init"], kernel=kern, Lb=args.lb,
+                   rounds=args.rounds, polls=args.polls) for b in w["betas"]]
+    handles = [s.handle for s in sims]
+    t_end = [w["T"] * T32] * len(sims)
+
+    def step():
+        for s in sims:
+            s.reset(seed, w["init"])
+        if kern == ac.AC_KERNEL_BLOCKED:
+            ac.ac_batch_run_until(handles, t_end)
+        else:
+            for s in sims:
+                s.run_until_ticks(t_end[0])
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+
+    # the trajectory is deterministic: every step commits the same arrivals, so the
+    # per-step event count and the kernel's duration are read on passes outside the
+    # timed region (stats() runs a reduction kernel)
+    kern_ms_list, ev_step = [], None
+    for _ in range(2):
+        step()
+        st = [s.stats() for s in sims]
+        ev_step = sum(x["events"] for x in st)
+        if kern == ac.AC_KERNEL_BLOCKED:
+            kern_ms_list.append(st[0]["device_ms"])          # one batched launch (same on every handle)
+        else:
+            kern_ms_list.append(sum(x["device_ms"] for x in st))
+    launches_per_step = (len(sims) + 2 if kern == ac.AC_KERNEL_BLOCKED
+                         else sum(2 + x["launches"] for x in st))
+
+    sync_all()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record()
+        for _ in range(args.steps):
+            step()
+        stop.record()
+        torch.cuda.synchronize()
+    ev_total = ev_step * args.steps
+    launches = launches_per_step * args.steps
+    kern_ms = statistics.median(kern_ms_list) * args.steps
+    elapsed_ms = start.elapsed_time(stop)
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        e = torch.tensor([float(ev_total)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(e)
+        ev_all = float(e.item())
+    else:
+        ev_all = float(ev_total)
+    value = ev_all / (elapsed_ms / 1000.0)
+    ev_per_step_rank = ev_total / args.steps
+
+    # roofline of the dominant kernel: algorithmic bytes per launch / its CUDA-event duration
+    peak, peak_src = measured_peaks()
+    kern_launch_ms = kern_ms / args.steps if kern == ac.AC_KERNEL_BLOCKED else kern_ms / args.steps
+    achieved = BYTES_PER_EVENT * ev_per_step_rank / (kern_launch_ms / 1000.0) / 1e9
+    kname = "blocked_kernel" if kern == ac.AC_KERNEL_BLOCKED else "round_kernel"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": committed_traffic(kname, args.lb), "peak_source": peak_src,
+                "kernel": f"{kname}<{args.lb}>", "bytes_per_event": BYTES_PER_EVENT,
+                "events_per_launch": ev_per_step_rank, "launch_ms": kern_launch_ms}
+
+    # end-to-end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        N = w["rows"] * w["cols"]
+        init_state = []
+        for s in sims:
+            s.reset(seed, w["init"])
+            host = (torch.empty(N, dtype=torch.int8).pin_memory(), torch.empty(N, dtype=torch.int64).pin_memory(),
+                    torch.empty(N, dtype=torch.int32).pin_memory())
+            ac.ac_read_state(s.handle, host[0].numpy(), host[1].numpy(), host[2].numpy().view(np.uint32))
+            init_state.append(host)
+        outs = [(torch.empty(N, dtype=torch.int8).pin_memory(), torch.empty(N, dtype=torch.int64).pin_memory(),
+                 torch.empty(N, dtype=torch.int32).pin_memory()) for _ in sims]
+        sync_all()
+        e_steps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        e_ev = 0
+        for _ in range(e_steps):
+            for s, (hs, ht, hn) in zip(sims, init_state):
+                s.reset(seed, w["init"])    # clears counters and history; state replaced below
+                ac.ac_load_state(s.handle, hs.numpy(), ht.numpy(), hn.numpy().view(np.uint32), 0)
+            if kern == ac.AC_KERNEL_BLOCKED:
+                ac.ac_batch_run_until(handles, t_end)
+            else:
+                for s in sims:
+                    s.run_until_ticks(t_end[0])
+            for s, (os_, ot, on) in zip(sims, outs):
+                ac.ac_read_state(s.handle, os_.numpy(), ot.numpy(), on.numpy().view(np.uint32))
+                e_ev += int(on.numpy().view(np.uint32).astype(np.int64).sum())
+        torch.cuda.synchronize()
+        e_dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e_dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_dt = float(t.item())
+            e = torch.tensor([float(e_ev)], device="cuda", dtype=torch.float64)
+            dist.all_reduce(e)
+            e_ev = e.item()
+        e2e = {"value": e_ev / e_dt, "unit": "events/s", "h2d_bytes_per_step": 12 * N * len(sims),
+               "d2h_bytes_per_step": 12 * N * len(sims), "steps": e_steps,
+               "path": "ac_load_state(host) + run + ac_read_state(host) per lattice"}
+
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra = side_measurements(ac, w, seed)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    stats0 = sims[0].stats()
+    for s in sims:
+        s.close()
+    if rank == 0:
+        out = {"metric": "cell_events_per_sec", "value": value, "unit": "events/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+               "data": "synthetic",
+               "config": {"workload": w["name"], "rows": w["rows"], "cols": w["cols"], "betas": w["betas"],
+                          "J": w["J"], "h": w["h"], "seed": w["seed"], "T": w["T"], "init": "random",
+                          "kernel": kname, "Lb": args.lb, "polls": args.polls, "rounds": args.rounds,
+                          "events_per_step": ev_all / args.steps,
+                          "l2": "state 3 x 201 MB > 129 MB L2 (no flush)",
+                          "parallelism": f"replicas x{world}"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clk.summary(),
+               "blocked_stats": {k: stats0[k] for k in ("visits", "polls", "rounds", "scanned", "enabled",
+                                                        "grid", "ctas_per_sm")},
+               "kernels": extra}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def side_measurements(ac, w, seed):
+    """Single-lattice numbers for each kernel (beta = 0.4407 lattice, one run each)."""
+    res = {}
+    configs = [("round_r1_lb64", ac.AC_KERNEL_ROUND, 64, 1, 0), ("round_r8_lb64", ac.AC_KERNEL_ROUND, 64, 8, 0),
+               ("blocked_lb32", ac.AC_KERNEL_BLOCKED, 32, 1, 8), ("blocked_lb64", ac.AC_KERNEL_BLOCKED, 64, 1, 8),
+               ("blocked_lb128", ac.AC_KERNEL_BLOCKED, 128, 1, 8)]
+    for name, kern, lb, rounds, polls in configs:
+        with ac.Sim(w["rows"], w["cols"], 0.4407, w["J"], w["h"], seed, init=w["init"], kernel=kern, Lb=lb,
+                    rounds=rounds, polls=polls) as s:
+            s.run_until(w["T"])        # warm-up run
+            s.reset(seed, w["init"])
+            s.run_until(w["T"])
+            st = s.stats()
+        res[name] = {"events": st["events"], "device_ms": st["device_ms"],
+                     "events_per_s": st["events"] / (st["device_ms"] / 1000.0),
+                     "hbm_frac_effective": BYTES_PER_EVENT * st["events"] / (st["device_ms"] / 1000.0) / 1e9 / 6787.9,
+                     "launches": st["launches"], "enabled_frac": st["enabled_frac_mean"],
+                     "visits": st["visits"], "polls": st["polls"], "grid": st["grid"]}
+    return res
+
+
+if __name__ == "__main__":
+    sys.exit(main())

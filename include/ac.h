@@ -1,0 +1,216 @@
+/*
+ * ac.h -- C ABI of libac, an exact GB300 (sm_103a) simulator of
+ * Poisson-asynchronous cellular arrays: Glauber's continuous-time Ising model
+ * on a periodic 2D lattice, after Lubachevsky, "Efficient Parallel Simulations
+ * of Asynchronous Cellular Arrays".
+ *
+ * Model (Sec. 1 "Poisson asynchrony"; Sec. 2, Eqs. (1)-(2)).  Each cell of a
+ * rows x cols torus has an independent rate-1 Poisson clock.  At an arrival
+ * the cell's spin s = +-1 flips with the heat-bath probability
+ * p = 1 / (1 + exp(beta * dE)), dE = 2 s (J S + h), S the sum of the four
+ * neighbour spins just before the arrival.  Energy E = -J sum s s' - h sum s
+ * (appendix).  Arrivals are committed in global (tick, row-major index) order,
+ * which every kernel reproduces exactly (the uniqueness argument of Sec. 3).
+ *
+ * Exact arithmetic conventions (shared by every entry point):
+ *   time       int64 ticks, 2^32 ticks per unit time; a run to T commits every
+ *              arrival with tick < t_end = T * 2^32.
+ *   randomness Philox4x32-10 with key (seed & 0xffffffff, seed >> 32): arrival
+ *              n of cell c (n = 0, 1, ...) uses block Philox({c, n+1, 0, 0});
+ *              word y is its acceptance uniform, word x gives the gap to arrival
+ *              n+1; block {c, 0, 0, 0} gives the first arrival, block
+ *              {c, 0, 1, 0} the random initial spin (odd x: up).  One counter
+ *              stream per cell (Sec. 5, and the invariance remark after
+ *              Fig. 3.6).
+ *   gap        integer stand-in for -ln r of Eq. (5): for a 32-bit word x,
+ *              u = (2x+1)/2^33, gap = floor((33 - log2(2x+1)) ln2 * 2^32) + 1
+ *              with log2 by 32 steps of truncated repeated squaring (Q1.31) and
+ *              ln 2 = 0xB17217F7D1CF79AB / 2^64.
+ *   threshold  thr[j + 5*(s > 0)] = min(floor(p * 2^32), 2^32 - 1) in IEEE
+ *              binary64 on the host, j = number of up neighbours (0..4); the
+ *              spin flips iff y < thr (the appendix's prob[] table).
+ *   state      per cell: spin int8 (+1 / -1), next-arrival tick int64 (>= 1),
+ *              committed-arrival count uint32; arrays row-major, rows*cols long.
+ *
+ * Ownership: the library owns all device memory of a simulation; every host
+ * buffer passed in is owned by the caller and only read or written during the
+ * call.  Calls on one handle are not thread-safe; distinct handles are
+ * independent.  Every call returns a status; on failure ac_last_error() holds a
+ * thread-local message.  Run calls are synchronous (they return when the device
+ * work on the handle's stream has completed).
+ */
+#ifndef AC_H
+#define AC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ac_sim ac_sim;
+
+typedef enum {
+  AC_OK = 0,
+  AC_ERR_ARG = 1,     /* invalid argument; nothing was changed */
+  AC_ERR_OOM = 2,     /* device or host allocation failed */
+  AC_ERR_CUDA = 3,    /* a CUDA call failed; the handle's state is undefined */
+  AC_ERR_STALL = 4,   /* the blocked kernel's watchdog saw no progress; state undefined */
+  AC_ERR_STATE = 5    /* call not valid in the handle's current state */
+} ac_status;
+
+typedef enum { AC_INIT_RANDOM = 0, AC_INIT_UP = 1, AC_INIT_DOWN = 2 } ac_init;
+
+typedef enum {
+  AC_KERNEL_ROUND = 0,    /* (a) synchronous rounds, Fig. 3.2 */
+  AC_KERNEL_BLOCKED = 1   /* (b) blocked persistent kernel, Fig. 3.4 */
+} ac_kernel;
+
+/* rows, cols >= 2 and rows * cols < 2^32. */
+typedef struct {
+  int32_t rows, cols;
+  int32_t init; /* ac_init */
+} ac_lattice;
+
+/*
+ * Create a simulation at time 0 (Sec. 2, initial state; first arrivals as
+ * above).  beta >= 0, J and h finite.  Allocates key/count arrays (12 bytes per
+ * cell) plus edge words for the tiling, and initialises them on the device.
+ * Defaults: blocked kernel, tile side 64.  *out receives the handle.
+ * Errors: AC_ERR_ARG (bad sizes or parameters), AC_ERR_OOM, AC_ERR_CUDA.
+ */
+ac_status ac_create(ac_lattice lat, double beta, double J, double h, uint64_t seed, ac_sim** out);
+
+/* Use `cuda_stream` (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+ * for all later device work of this handle.  NULL selects the legacy default stream. */
+ac_status ac_set_stream(ac_sim* sim, void* cuda_stream);
+
+/*
+ * Choose the kernel and its tuning for later run calls.
+ *   kernel  AC_KERNEL_ROUND or AC_KERNEL_BLOCKED
+ *   Lb      tile side: 32, 64 or 128 (threads per CTA = 4 * Lb)
+ *   rounds  round kernel: tile rounds per launch (1 = exact synchronous rounds of
+ *           Fig. 3.2 with per-round enabled counts); blocked kernel: halo refresh
+ *           period in rounds (>= 1)
+ *   polls   blocked kernel: halo polls before a blocked tile is left (>= 0)
+ * The trajectory does not depend on any of these (Sec. 3, invariance of the
+ * aggregated algorithm under re-partitioning); only the speed does.
+ * Errors: AC_ERR_ARG, AC_ERR_OOM (edge-word reallocation), AC_ERR_CUDA.
+ */
+ac_status ac_configure(ac_sim* sim, int32_t kernel, int32_t Lb, int32_t rounds, int32_t polls);
+
+/*
+ * Advance the trajectory: commit every arrival with tick < t_end (Fig. 3.1 loop
+ * condition); afterwards every cell's tick is its first uncommitted arrival,
+ * >= t_end.  t_end must be >= the previous t_end of this handle and < 2^61.
+ * ac_run_until(T) uses t_end = floor(T * 2^32) (exact for integral T).
+ * Errors: AC_ERR_ARG (t_end decreasing or out of range), AC_ERR_STALL,
+ * AC_ERR_CUDA.
+ */
+ac_status ac_run_until(ac_sim* sim, double T);
+ac_status ac_run_until_ticks(ac_sim* sim, int64_t t_end);
+
+/*
+ * Copy the state to caller-owned HOST arrays of rows*cols elements (row-major):
+ * s (+1/-1), t (next-arrival ticks), n (committed arrivals per cell).  Any
+ * pointer may be NULL to skip that array.  Errors: AC_ERR_ARG, AC_ERR_CUDA.
+ */
+ac_status ac_read_state(const ac_sim* sim, int8_t* s, int64_t* t, uint32_t* n);
+
+/* Same as ac_read_state into caller-owned DEVICE arrays (e.g. torch CUDA tensors). */
+ac_status ac_read_state_device(const ac_sim* sim, int8_t* s_dev, int64_t* t_dev, uint32_t* n_dev);
+
+/*
+ * Replace the state from caller-owned HOST arrays (the inverse of
+ * ac_read_state) and declare it the state at time t_done: every s must be +-1
+ * and every t in [max(t_done, 1), 2^61).  Together with ac_read_state this is
+ * checkpoint/resume: the random streams are positioned by the counts n.
+ * Errors: AC_ERR_ARG (invalid state), AC_ERR_CUDA.
+ */
+ac_status ac_load_state(ac_sim* sim, const int8_t* s, const int64_t* t, const uint32_t* n,
+                        int64_t t_done);
+
+typedef struct {
+  uint64_t events;          /* arrivals committed by run calls since create/load */
+  uint64_t rounds;          /* tile rounds (commit phases) executed */
+  uint64_t launches;        /* hot-path kernel launches */
+  uint64_t scanned;         /* enable tests performed */
+  uint64_t enabled;         /* enable tests that passed */
+  uint64_t visits;          /* blocked kernel: tile visits */
+  uint64_t polls;           /* blocked kernel: halo polls of blocked tiles */
+  uint64_t global_rounds;   /* round kernel with rounds=1: synchronous rounds run */
+  double device_ms;         /* device time of the run calls (CUDA events) */
+  double enabled_frac_mean; /* Sec. 4 efficiency: mean over synchronous rounds of
+                               enabled/N (round kernel, rounds=1); else enabled/scanned */
+  int64_t sum_s;            /* current sum of spins */
+  int64_t sum_bonds;        /* current sum over right and down bonds of s s' */
+  uint64_t checksum;        /* sum_c mix(mix(mix(c) ^ t) ^ (2n + [s>0])) mod 2^64,
+                               mix = SplitMix64 finaliser */
+  uint64_t total_counts;    /* sum of per-cell counts */
+  int64_t t_done;           /* t_end of the last completed run call */
+  int32_t kernel, Lb, threads, rounds_per_launch;
+  int32_t grid;             /* CTAs of the last launch */
+  int32_t ctas_per_sm;      /* blocked kernel: resident CTAs per SM */
+} ac_stats_t;
+
+/* Statistics and observables of the handle (runs a reduction on the device). */
+ac_status ac_stats(const ac_sim* sim, ac_stats_t* out);
+
+/* Per-round enabled counts of the synchronous rounds run so far with the round
+ * kernel at rounds=1 (Sec. 4 efficiency = counts / N).  Writes up to `cap`
+ * entries and the number available to *n_rounds. */
+ac_status ac_round_history(const ac_sim* sim, uint64_t* counts, int32_t cap, int32_t* n_rounds);
+
+/*
+ * Return the handle to time 0 with a new seed and initial condition, reusing its
+ * device memory (the same initial state as ac_create; counters and statistics of
+ * the trajectory restart).  No allocation.  Errors: AC_ERR_ARG, AC_ERR_CUDA.
+ */
+ac_status ac_reset(ac_sim* sim, uint64_t seed, int32_t init);
+
+/* Tuning and verification options (ac_set_option):
+ *   AC_OPT_WATCHDOG_NS   blocked kernel: no-progress limit in ns before the run
+ *                        returns AC_ERR_STALL (default 5e9, >= 1e6)
+ *   AC_OPT_MAX_ROUNDS    blocked kernel: cap on tile rounds per visit (0 = none)
+ *   AC_OPT_DROP_PUBLISH  verification hook: 1 suppresses the publication of
+ *                        boundary commits, so that a lattice of several tiles
+ *                        cannot finish and the watchdog must end the run with
+ *                        AC_ERR_STALL (no fault, no unbounded wait); 0 restores it. */
+enum { AC_OPT_WATCHDOG_NS = 1, AC_OPT_MAX_ROUNDS = 2, AC_OPT_DROP_PUBLISH = 3 };
+ac_status ac_set_option(ac_sim* sim, int32_t option, int64_t value);
+
+/* Free all memory of the handle (NULL is ignored). */
+void ac_destroy(ac_sim* sim);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* ac_last_error(void);
+
+/* The threshold table the library uses for (beta, J, h) (the appendix's prob[],
+ * quantised as above), written to thr[10]. */
+ac_status ac_thresholds(double beta, double J, double h, uint32_t thr[10]);
+
+/*
+ * Batching.  ac_batch_create makes n independent simulations (arrays of n
+ * lattices and parameters; seeds distinguish lattices, the counter carries no
+ * lattice id) into out[0..n-1], each usable with every call above.
+ * ac_batch_run_until advances sims[0..n-1] to t_end[i] each in ONE persistent
+ * blocked-kernel launch over all their tiles, replayed from a CUDA graph that is
+ * captured on the first call for that exact list of handles.  All handles must
+ * share the stream of sims[0] and a tile side.  Results are bit-identical to
+ * running each handle alone.  Errors as for ac_run_until_ticks.
+ */
+ac_status ac_batch_create(int32_t n, const ac_lattice* lats, const double* beta, const double* J,
+                          const double* h, const uint64_t* seed, ac_sim** out);
+ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_end);
+
+/* Device-primitive probes (DEVICE pointers, n elements), for verification:
+ * out[i] = gap of x[i];  out4[4i..4i+3] = Philox({c[i], k[i], w2, 0}) under seed. */
+ac_status ac_dev_exp_ticks(const uint32_t* x_dev, uint64_t* out_dev, int64_t n);
+ac_status ac_dev_philox(uint64_t seed, const uint32_t* c_dev, const uint32_t* k_dev, uint32_t w2,
+                        uint32_t* out4_dev, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AC_H */

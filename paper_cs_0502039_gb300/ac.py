@@ -1,0 +1,274 @@
+"""ctypes binding of libac (include/ac.h): same names, argument marshalling only.
+
+Every step of the simulation runs in the CUDA kernels of ``libac.so``; this
+module converts Python values and numpy / torch buffers into the C ABI's plain
+pointers and sizes and turns non-zero statuses into :class:`ACError`.  If the
+shared library is missing the import fails loudly -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libac.so")
+
+AC_OK, AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA, AC_ERR_STALL, AC_ERR_STATE = range(6)
+AC_INIT_RANDOM, AC_INIT_UP, AC_INIT_DOWN = 0, 1, 2
+AC_KERNEL_ROUND, AC_KERNEL_BLOCKED = 0, 1
+AC_OPT_WATCHDOG_NS, AC_OPT_MAX_ROUNDS, AC_OPT_DROP_PUBLISH = 1, 2, 3
+TICKS_PER_UNIT = 1 << 32
+
+_STATUS = {AC_ERR_ARG: "AC_ERR_ARG", AC_ERR_OOM: "AC_ERR_OOM", AC_ERR_CUDA: "AC_ERR_CUDA",
+           AC_ERR_STALL: "AC_ERR_STALL", AC_ERR_STATE: "AC_ERR_STATE"}
+
+
+class ACError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ac_lattice(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32), ("init", ctypes.c_int32)]
+
+
+class ac_stats_t(ctypes.Structure):
+    _fields_ = [("events", ctypes.c_uint64), ("rounds", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("scanned", ctypes.c_uint64), ("enabled", ctypes.c_uint64), ("visits", ctypes.c_uint64),
+                ("polls", ctypes.c_uint64), ("global_rounds", ctypes.c_uint64),
+                ("device_ms", ctypes.c_double), ("enabled_frac_mean", ctypes.c_double),
+                ("sum_s", ctypes.c_int64), ("sum_bonds", ctypes.c_int64), ("checksum", ctypes.c_uint64),
+                ("total_counts", ctypes.c_uint64), ("t_done", ctypes.c_int64),
+                ("kernel", ctypes.c_int32), ("Lb", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("rounds_per_launch", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+EXPORTS = ["ac_create", "ac_set_stream", "ac_configure", "ac_run_until", "ac_run_until_ticks",
+           "ac_read_state", "ac_read_state_device", "ac_load_state", "ac_stats", "ac_round_history",
+           "ac_destroy", "ac_last_error", "ac_thresholds", "ac_reset", "ac_set_option", "ac_batch_create", "ac_batch_run_until",
+           "ac_dev_exp_ticks", "ac_dev_philox"]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libac.so not found at {path}: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, U64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    sig = {
+        "ac_create": ([ac_lattice, D, D, D, U64, ctypes.POINTER(P)], I32),
+        "ac_set_stream": ([P, P], I32),
+        "ac_configure": ([P, I32, I32, I32, I32], I32),
+        "ac_run_until": ([P, D], I32),
+        "ac_run_until_ticks": ([P, I64], I32),
+        "ac_read_state": ([P, P, P, P], I32),
+        "ac_read_state_device": ([P, P, P, P], I32),
+        "ac_load_state": ([P, P, P, P, I64], I32),
+        "ac_stats": ([P, ctypes.POINTER(ac_stats_t)], I32),
+        "ac_round_history": ([P, P, I32, ctypes.POINTER(I32)], I32),
+        "ac_destroy": ([P], None),
+        "ac_reset": ([P, U64, I32], I32),
+        "ac_set_option": ([P, I32, I64], I32),
+        "ac_last_error": ([], ctypes.c_char_p),
+        "ac_thresholds": ([D, D, D, P], I32),
+        "ac_batch_create": ([I32, P, P, P, P, P, P], I32),
+        "ac_batch_run_until": ([I32, P, P], I32),
+        "ac_dev_exp_ticks": ([P, P, I64], I32),
+        "ac_dev_philox": ([U64, P, P, ctypes.c_uint32, P, I64], I32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = load_library()
+
+
+def _check(status: int) -> None:
+    if status != AC_OK:
+        raise ACError(status, _lib.ac_last_error().decode(errors="replace"))
+
+
+def _np_ptr(a: np.ndarray, dtype) -> ctypes.c_void_p:
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous {np.dtype(dtype).name} array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# ----------------------------------------------------------- same-name wrappers
+def ac_create(rows: int, cols: int, init: int, beta: float, J: float, h: float, seed: int) -> int:
+    out = ctypes.c_void_p()
+    _check(_lib.ac_create(ac_lattice(rows, cols, init), beta, J, h, seed & (2**64 - 1), ctypes.byref(out)))
+    return out.value
+
+
+def ac_set_stream(sim: int, stream: int) -> None:
+    _check(_lib.ac_set_stream(sim, stream))
+
+
+def ac_configure(sim: int, kernel: int, Lb: int, rounds: int, polls: int) -> None:
+    _check(_lib.ac_configure(sim, kernel, Lb, rounds, polls))
+
+
+def ac_run_until(sim: int, T: float) -> None:
+    _check(_lib.ac_run_until(sim, float(T)))
+
+
+def ac_run_until_ticks(sim: int, t_end: int) -> None:
+    _check(_lib.ac_run_until_ticks(sim, int(t_end)))
+
+
+def ac_read_state(sim: int, s: np.ndarray | None, t: np.ndarray | None, n: np.ndarray | None) -> None:
+    _check(_lib.ac_read_state(sim, None if s is None else _np_ptr(s, np.int8),
+                              None if t is None else _np_ptr(t, np.int64),
+                              None if n is None else _np_ptr(n, np.uint32)))
+
+
+def ac_read_state_device(sim: int, s_ptr: int | None, t_ptr: int | None, n_ptr: int | None) -> None:
+    _check(_lib.ac_read_state_device(sim, s_ptr, t_ptr, n_ptr))
+
+
+def ac_load_state(sim: int, s: np.ndarray, t: np.ndarray, n: np.ndarray, t_done: int) -> None:
+    _check(_lib.ac_load_state(sim, _np_ptr(s, np.int8), _np_ptr(t, np.int64), _np_ptr(n, np.uint32),
+                              int(t_done)))
+
+
+def ac_stats(sim: int) -> dict:
+    st = ac_stats_t()
+    _check(_lib.ac_stats(sim, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def ac_round_history(sim: int) -> np.ndarray:
+    n = ctypes.c_int32()
+    _check(_lib.ac_round_history(sim, None, 0, ctypes.byref(n)))
+    buf = np.zeros(max(n.value, 1), dtype=np.uint64)
+    _check(_lib.ac_round_history(sim, _np_ptr(buf, np.uint64), n.value, ctypes.byref(n)))
+    return buf[:n.value].copy()
+
+
+def ac_destroy(sim: int) -> None:
+    _lib.ac_destroy(sim)
+
+
+def ac_reset(sim: int, seed: int, init: int) -> None:
+    _check(_lib.ac_reset(sim, seed & (2**64 - 1), init))
+
+
+def ac_set_option(sim: int, option: int, value: int) -> None:
+    _check(_lib.ac_set_option(sim, option, int(value)))
+
+
+def ac_thresholds(beta: float, J: float = 1.0, h: float = 0.0) -> np.ndarray:
+    out = np.zeros(10, dtype=np.uint32)
+    _check(_lib.ac_thresholds(beta, J, h, _np_ptr(out, np.uint32)))
+    return out
+
+
+def ac_batch_create(lattices, betas, Js, hs, seeds) -> list[int]:
+    n = len(lattices)
+    lats = (ac_lattice * n)(*[ac_lattice(r, c, i) for (r, c, i) in lattices])
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    j = np.ascontiguousarray(Js, dtype=np.float64)
+    h = np.ascontiguousarray(hs, dtype=np.float64)
+    s = np.ascontiguousarray([int(x) & (2**64 - 1) for x in seeds], dtype=np.uint64)
+    out = (ctypes.c_void_p * n)()
+    _check(_lib.ac_batch_create(n, ctypes.cast(lats, ctypes.c_void_p), _np_ptr(b, np.float64),
+                                _np_ptr(j, np.float64), _np_ptr(h, np.float64), _np_ptr(s, np.uint64),
+                                ctypes.cast(out, ctypes.c_void_p)))
+    return [out[i] for i in range(n)]
+
+
+def ac_batch_run_until(sims, t_end) -> None:
+    n = len(sims)
+    arr = (ctypes.c_void_p * n)(*sims)
+    te = np.ascontiguousarray([int(x) for x in t_end], dtype=np.int64)
+    _check(_lib.ac_batch_run_until(n, ctypes.cast(arr, ctypes.c_void_p), _np_ptr(te, np.int64)))
+
+
+def ac_dev_exp_ticks(x_ptr: int, out_ptr: int, n: int) -> None:
+    _check(_lib.ac_dev_exp_ticks(x_ptr, out_ptr, n))
+
+
+def ac_dev_philox(seed: int, c_ptr: int, k_ptr: int, w2: int, out_ptr: int, n: int) -> None:
+    _check(_lib.ac_dev_philox(seed & (2**64 - 1), c_ptr, k_ptr, w2, out_ptr, n))
+
+
+# --------------------------------------------------------------- convenience
+class Sim:
+    """One lattice handle (owns its device memory; freed on close / GC)."""
+
+    def __init__(self, rows: int, cols: int, beta: float, J: float = 1.0, h: float = 0.0, seed: int = 0,
+                 init: int = AC_INIT_RANDOM, kernel: int | None = None, Lb: int | None = None,
+                 rounds: int = 1, polls: int = 8, handle: int | None = None):
+        self.rows, self.cols = int(rows), int(cols)
+        self.beta, self.J, self.h, self.seed = float(beta), float(J), float(h), int(seed)
+        self.handle = handle if handle is not None else ac_create(rows, cols, init, beta, J, h, seed)
+        if kernel is not None or Lb is not None:
+            self.configure(AC_KERNEL_BLOCKED if kernel is None else kernel, 64 if Lb is None else Lb,
+                           rounds, polls)
+
+    def configure(self, kernel: int, Lb: int, rounds: int = 1, polls: int = 8) -> "Sim":
+        ac_configure(self.handle, kernel, Lb, rounds, polls)
+        return self
+
+    def set_stream(self, stream: int) -> None:
+        ac_set_stream(self.handle, stream)
+
+    def run_until(self, T: float) -> None:
+        ac_run_until(self.handle, T)
+
+    def run_until_ticks(self, t_end: int) -> None:
+        ac_run_until_ticks(self.handle, t_end)
+
+    def read_state(self):
+        N = self.rows * self.cols
+        s = np.empty(N, dtype=np.int8)
+        t = np.empty(N, dtype=np.int64)
+        n = np.empty(N, dtype=np.uint32)
+        ac_read_state(self.handle, s, t, n)
+        return s, t, n
+
+    def load_state(self, s, t, n, t_done: int) -> None:
+        ac_load_state(self.handle, np.ascontiguousarray(s, dtype=np.int8),
+                      np.ascontiguousarray(t, dtype=np.int64), np.ascontiguousarray(n, dtype=np.uint32),
+                      t_done)
+
+    def stats(self) -> dict:
+        return ac_stats(self.handle)
+
+    def reset(self, seed: int, init: int = AC_INIT_RANDOM) -> None:
+        ac_reset(self.handle, seed, init)
+        self.seed = int(seed)
+
+    def set_option(self, option: int, value: int) -> None:
+        ac_set_option(self.handle, option, value)
+
+    def round_history(self) -> np.ndarray:
+        return ac_round_history(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            ac_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,759 @@
+// ac_api.cu -- host runtime behind the C ABI of include/ac.h.
+//
+// Owns device memory and streams, computes the heat-bath threshold table (the
+// only floating-point step of the method, appendix flip probabilities, in IEEE
+// binary64 on the host), drives the round kernel (one launch per synchronous
+// round of Fig. 3.2, checked for completion in chunks) and the blocked
+// persistent kernel (one cooperative launch per run call, Fig. 3.4), and
+// captures batched runs into CUDA graphs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ac.h"
+#include "ac_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+ac_status fail(ac_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define AC_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(AC_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                  __FILE__, __LINE__);                                                     \
+  } while (0)
+
+constexpr double kTicksPerUnit = 4294967296.0;
+constexpr long long kTickLimit = 1ll << 61;
+
+// Heat-bath thresholds: p = 1/(1 + exp(beta dE)), dE = 2 s (J S + h);
+// thr = min(floor(p * 2^32), 2^32 - 1), index j + 5*(s > 0), S = 2j - 4.
+void make_thresholds(double beta, double J, double h, uint32_t thr[10]) {
+  for (int up = 0; up < 2; ++up) {
+    const double s = up ? 1.0 : -1.0;
+    for (int j = 0; j < 5; ++j) {
+      const double S = (double)(2 * j - 4);
+      const double dE = 2.0 * s * (J * S + h);
+      const double p = 1.0 / (1.0 + std::exp(beta * dE));
+      const double v = std::ldexp(p, 32);
+      thr[j + 5 * up] = (v < 4294967295.0) ? (uint32_t)std::floor(v) : 0xFFFFFFFFu;
+    }
+  }
+}
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+struct ac_sim {
+  int rows = 0, cols = 0, init = 0;
+  double beta = 0, J = 0, h = 0;
+  uint64_t seed = 0;
+  cudaStream_t stream = nullptr;
+  ac::LaunchCfg cfg{};
+  uint32_t thr[10] = {};
+  int tr = 0, tc = 0;
+
+  unsigned long long* key = nullptr;
+  unsigned int* cnt = nullptr;
+  unsigned long long* pub = nullptr;
+  unsigned long long* pub2 = nullptr;
+  size_t pub_words = 0;
+  unsigned long long* d_events = nullptr;   // per-lattice event counter
+  ac::LatDesc* d_desc = nullptr;
+  ac::DevCounters* d_ctr = nullptr;
+  unsigned int* d_tile_done = nullptr;
+  size_t tile_done_cap = 0;
+  unsigned long long* d_hist = nullptr;     // enabled counts per synchronous round
+  int hist_cap = 0;
+  unsigned long long* d_red = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  long long t_done = 0;
+  // accumulated statistics
+  unsigned long long events = 0, rounds = 0, launches = 0, scanned = 0, enabled = 0, visits = 0,
+                     polls = 0, global_rounds = 0, enabled_r1 = 0;
+  double device_ms = 0.0;
+  int last_grid = 0, ctas_per_sm = 0;
+  int drop_publish = 0;
+
+  size_t ncells() const { return (size_t)rows * (size_t)cols; }
+  int tiles() const { return tr * tc; }
+
+  ac::LatDesc host_desc(long long t_end, int tile_base) const {
+    ac::LatDesc d{};
+    d.key = key;
+    d.cnt = cnt;
+    d.pub = pub;
+    d.pub2 = pub2;
+    d.events = d_events;
+    d.rows = rows;
+    d.cols = cols;
+    d.tr = tr;
+    d.tc = tc;
+    d.lb = cfg.lb;
+    d.tile_base = tile_base;
+    std::memcpy(d.thr, thr, sizeof thr);
+    d.seed_lo = (unsigned)(seed & 0xffffffffu);
+    d.seed_hi = (unsigned)(seed >> 32);
+    d.t_end = t_end;
+    d.t2 = 2ull * (unsigned long long)t_end;
+    d.drop_publish = drop_publish;
+    return d;
+  }
+};
+
+namespace {
+
+// ---------------------------------------------------------------- batch graphs
+struct BatchRunner {
+  std::vector<ac_sim*> sims;
+  ac::LatDesc* h_desc = nullptr;   // pinned; read by the graph's copy node at replay
+  ac::LatDesc* d_desc = nullptr;
+  ac::DevCounters* d_ctr = nullptr;
+  unsigned int* d_tile_done = nullptr;
+  unsigned long long* h_before = nullptr;
+  int total_tiles = 0, grid = 0, lb = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  ac::LaunchCfg cfg{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+std::mutex g_batch_mu;
+std::map<std::vector<ac_sim*>, BatchRunner*> g_runners;
+
+void free_runner(BatchRunner* r) {
+  if (!r) return;
+  if (r->exec) cudaGraphExecDestroy(r->exec);
+  if (r->graph) cudaGraphDestroy(r->graph);
+  if (r->h_desc) cudaFreeHost(r->h_desc);
+  if (r->d_desc) cudaFree(r->d_desc);
+  if (r->d_ctr) cudaFree(r->d_ctr);
+  if (r->d_tile_done) cudaFree(r->d_tile_done);
+  if (r->ev0) cudaEventDestroy(r->ev0);
+  if (r->ev1) cudaEventDestroy(r->ev1);
+  if (r->own_stream) cudaStreamDestroy(r->own_stream);
+  delete r;
+}
+
+void drop_runners_of(ac_sim* sim) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (auto it = g_runners.begin(); it != g_runners.end();) {
+    if (std::find(it->first.begin(), it->first.end(), sim) != it->first.end()) {
+      free_runner(it->second);
+      it = g_runners.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+ac_status alloc_edges(ac_sim* s) {
+  s->tr = ceil_div(s->rows, s->cfg.lb);
+  s->tc = ceil_div(s->cols, s->cfg.lb);
+  const size_t words = (size_t)s->tiles() * 4 * s->cfg.lb;
+  if (words > s->pub_words) {
+    if (s->pub) cudaFree(s->pub);
+    if (s->pub2) cudaFree(s->pub2);
+    s->pub = s->pub2 = nullptr;
+    s->pub_words = 0;
+    if (cudaMalloc(&s->pub, words * 8) != cudaSuccess || cudaMalloc(&s->pub2, words * 8) != cudaSuccess)
+      return fail(AC_ERR_OOM, "edge words: cudaMalloc of %zu bytes failed", words * 16);
+    s->pub_words = words;
+  }
+  if ((size_t)s->tiles() > s->tile_done_cap) {
+    if (s->d_tile_done) cudaFree(s->d_tile_done);
+    s->d_tile_done = nullptr;
+    if (cudaMalloc(&s->d_tile_done, (size_t)s->tiles() * 4) != cudaSuccess)
+      return fail(AC_ERR_OOM, "tile flags: cudaMalloc failed");
+    s->tile_done_cap = (size_t)s->tiles();
+  }
+  return AC_OK;
+}
+
+void free_sim(ac_sim* s) {
+  if (!s) return;
+  cudaFree(s->key);
+  cudaFree(s->cnt);
+  cudaFree(s->pub);
+  cudaFree(s->pub2);
+  cudaFree(s->d_events);
+  cudaFree(s->d_desc);
+  cudaFree(s->d_ctr);
+  cudaFree(s->d_tile_done);
+  cudaFree(s->d_hist);
+  cudaFree(s->d_red);
+  if (s->ev0) cudaEventDestroy(s->ev0);
+  if (s->ev1) cudaEventDestroy(s->ev1);
+  delete s;
+}
+
+ac_status check_params(const ac_lattice& lat, double beta, double J, double h) {
+  if (lat.rows < 2 || lat.cols < 2)
+    return fail(AC_ERR_ARG, "rows and cols must be >= 2 (got %d x %d)", lat.rows, lat.cols);
+  if ((unsigned long long)lat.rows * (unsigned long long)lat.cols >= (1ull << 32))
+    return fail(AC_ERR_ARG, "rows * cols must be < 2^32");
+  if (lat.init < AC_INIT_RANDOM || lat.init > AC_INIT_DOWN)
+    return fail(AC_ERR_ARG, "init must be AC_INIT_RANDOM, AC_INIT_UP or AC_INIT_DOWN");
+  if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(AC_ERR_ARG, "beta must be finite and >= 0");
+  if (!std::isfinite(J) || !std::isfinite(h)) return fail(AC_ERR_ARG, "J and h must be finite");
+  return AC_OK;
+}
+
+ac_status create_one(ac_lattice lat, double beta, double J, double h, uint64_t seed, ac_sim** out) {
+  ac_sim* s = new (std::nothrow) ac_sim();
+  if (!s) return fail(AC_ERR_OOM, "host allocation failed");
+  s->rows = lat.rows;
+  s->cols = lat.cols;
+  s->init = lat.init;
+  s->beta = beta;
+  s->J = J;
+  s->h = h;
+  s->seed = seed;
+  s->cfg.kernel = ac::kKernelBlocked;
+  s->cfg.lb = 64;
+  s->cfg.threads = 256;
+  s->cfg.rounds = 1;
+  s->cfg.polls = 8;
+  s->cfg.refresh = 1;
+  s->cfg.max_rounds = 0;
+  s->cfg.watchdog_ns = 5ll * 1000 * 1000 * 1000;
+  make_thresholds(beta, J, h, s->thr);
+  const size_t N = s->ncells();
+  if (cudaMalloc(&s->key, N * 8) != cudaSuccess || cudaMalloc(&s->cnt, N * 4) != cudaSuccess ||
+      cudaMalloc(&s->d_events, 8) != cudaSuccess || cudaMalloc(&s->d_desc, sizeof(ac::LatDesc)) != cudaSuccess ||
+      cudaMalloc(&s->d_ctr, sizeof(ac::DevCounters)) != cudaSuccess ||
+      cudaMalloc(&s->d_red, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    free_sim(s);
+    return fail(AC_ERR_OOM, "cudaMalloc of the lattice state (%zu cells) failed", N);
+  }
+  ac_status st = alloc_edges(s);
+  if (st != AC_OK) {
+    free_sim(s);
+    return st;
+  }
+  if (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess) {
+    free_sim(s);
+    return fail(AC_ERR_CUDA, "cudaEventCreate failed");
+  }
+  const ac::LatDesc d = s->host_desc(0, 0);
+  cudaError_t e = ac::launch_init(&d, lat.init, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    free_sim(s);
+    return fail(AC_ERR_CUDA, "init kernel failed: %s", cudaGetErrorString(e));
+  }
+  *out = s;
+  return AC_OK;
+}
+
+ac_status accumulate(ac_sim* s, const ac::DevCounters& c, float ms, bool round_kernel) {
+  s->rounds += c.rounds;
+  s->scanned += c.scanned;
+  s->enabled += c.enabled;
+  s->visits += c.visits;
+  s->polls += c.polls;
+  s->device_ms += ms;
+  if (round_kernel) {
+    s->launches += c.launched;
+    if (s->cfg.rounds == 1) {
+      s->global_rounds += c.launched;
+      s->enabled_r1 += c.enabled;
+    }
+  } else {
+    s->launches += 1;
+  }
+  if (c.error) return fail((ac_status)c.error, "device watchdog: no progress (block %d)", c.err_block);
+  return AC_OK;
+}
+
+ac_status run_round(ac_sim* s, long long t_end) {
+  const int total = s->tiles();
+  const ac::LatDesc d = s->host_desc(t_end, 0);
+  AC_CUDA(cudaMemcpyAsync(s->d_desc, &d, sizeof d, cudaMemcpyHostToDevice, s->stream));
+  AC_CUDA(cudaMemsetAsync(s->d_ctr, 0, sizeof(ac::DevCounters), s->stream));
+  AC_CUDA(ac::launch_publish(s->d_desc, 1, total, s->cfg.lb, 0, s->stream));
+  const bool exact = (s->cfg.rounds == 1);
+  if (exact && s->d_hist == nullptr) {
+    s->hist_cap = 1 << 16;
+    if (cudaMalloc(&s->d_hist, (size_t)s->hist_cap * 8) != cudaSuccess)
+      return fail(AC_ERR_OOM, "round history allocation failed");
+    AC_CUDA(cudaMemsetAsync(s->d_hist, 0, (size_t)s->hist_cap * 8, s->stream));
+  }
+  AC_CUDA(cudaEventRecord(s->ev0, s->stream));
+  const double span = (double)(t_end - s->t_done) / kTicksPerUnit;
+  int chunk = (int)std::min(4096.0, 9.0 * std::ceil(span) / std::max(1, s->cfg.rounds) + 16.0);
+  int launch_idx = 0, parity = 0;
+  unsigned active = 1;
+  for (;;) {
+    for (int i = 0; i < chunk; ++i) {
+      AC_CUDA(ac::launch_round(s->d_desc, 1, total, s->cfg, parity, launch_idx, s->d_ctr,
+                               exact ? s->d_hist : nullptr, s->hist_cap,
+                               (int)std::min<unsigned long long>(s->global_rounds + launch_idx, 1u << 30),
+                               s->stream));
+      parity ^= 1;
+      ++launch_idx;
+    }
+    AC_CUDA(cudaMemcpyAsync(&active, &s->d_ctr->active[(launch_idx - 1) % 3], sizeof active,
+                            cudaMemcpyDeviceToHost, s->stream));
+    AC_CUDA(cudaStreamSynchronize(s->stream));
+    if (active == 0) break;
+    // every synchronous round commits the globally smallest pending arrival, so a
+    // run needs at most (pending arrivals) rounds; far beyond the ~8.3 rounds per
+    // unit time of Sec. 4 only a defect could keep tiles active
+    if ((double)launch_idx > 64.0 * (9.0 * std::ceil(span) + 16.0) + 4096.0)
+      return fail(AC_ERR_STALL, "round kernel: no completion after %d launches", launch_idx);
+    chunk = 16;
+  }
+  AC_CUDA(cudaEventRecord(s->ev1, s->stream));
+  ac::DevCounters c{};
+  AC_CUDA(cudaMemcpyAsync(&c, s->d_ctr, sizeof c, cudaMemcpyDeviceToHost, s->stream));
+  AC_CUDA(cudaStreamSynchronize(s->stream));
+  float ms = 0.f;
+  AC_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+  s->last_grid = total;
+  if (exact) {
+    // rounds with at least one commit form a prefix of this call's launches
+    const long long first = (long long)s->global_rounds;
+    const long long m = std::max(0ll, std::min<long long>(c.launched, (long long)s->hist_cap - first));
+    std::vector<unsigned long long> h((size_t)m);
+    if (m > 0) {
+      AC_CUDA(cudaMemcpyAsync(h.data(), s->d_hist + first, (size_t)m * 8, cudaMemcpyDeviceToHost, s->stream));
+      AC_CUDA(cudaStreamSynchronize(s->stream));
+    }
+    unsigned productive = 0;
+    while (productive < (unsigned)m && h[productive] != 0) ++productive;
+    c.launched = productive;
+  }
+  return accumulate(s, c, ms, true);
+}
+
+ac_status run_blocked(ac_sim* s, long long t_end) {
+  const int total = s->tiles();
+  int per_sm = 0;
+  const int maxc = ac::blocked_max_ctas(s->cfg.lb, &per_sm);
+  if (maxc <= 0) return fail(AC_ERR_CUDA, "blocked kernel cannot be resident (tile side %d)", s->cfg.lb);
+  const int grid = std::min(total, maxc);
+  const ac::LatDesc d = s->host_desc(t_end, 0);
+  AC_CUDA(cudaMemcpyAsync(s->d_desc, &d, sizeof d, cudaMemcpyHostToDevice, s->stream));
+  AC_CUDA(cudaMemsetAsync(s->d_ctr, 0, sizeof(ac::DevCounters), s->stream));
+  AC_CUDA(cudaMemsetAsync(s->d_tile_done, 0, (size_t)total * 4, s->stream));
+  AC_CUDA(ac::launch_publish(s->d_desc, 1, total, s->cfg.lb, 0, s->stream));
+  AC_CUDA(cudaEventRecord(s->ev0, s->stream));
+  AC_CUDA(ac::launch_blocked(s->d_desc, 1, total, s->cfg, grid, s->d_tile_done, s->d_ctr, s->stream));
+  AC_CUDA(cudaEventRecord(s->ev1, s->stream));
+  ac::DevCounters c{};
+  AC_CUDA(cudaMemcpyAsync(&c, s->d_ctr, sizeof c, cudaMemcpyDeviceToHost, s->stream));
+  AC_CUDA(cudaStreamSynchronize(s->stream));
+  float ms = 0.f;
+  AC_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+  s->last_grid = grid;
+  s->ctas_per_sm = per_sm;
+  return accumulate(s, c, ms, false);
+}
+
+ac_status read_event_counter(ac_sim* s, unsigned long long* v) {
+  AC_CUDA(cudaMemcpyAsync(v, s->d_events, 8, cudaMemcpyDeviceToHost, s->stream));
+  AC_CUDA(cudaStreamSynchronize(s->stream));
+  return AC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ac_last_error(void) { return g_err.c_str(); }
+
+ac_status ac_thresholds(double beta, double J, double h, uint32_t thr[10]) {
+  if (!thr) return fail(AC_ERR_ARG, "thr is NULL");
+  if (!(beta >= 0.0) || !std::isfinite(beta) || !std::isfinite(J) || !std::isfinite(h))
+    return fail(AC_ERR_ARG, "beta must be finite and >= 0; J, h finite");
+  make_thresholds(beta, J, h, thr);
+  return AC_OK;
+}
+
+ac_status ac_create(ac_lattice lat, double beta, double J, double h, uint64_t seed, ac_sim** out) {
+  if (!out) return fail(AC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  ac_status st = check_params(lat, beta, J, h);
+  if (st != AC_OK) return st;
+  return create_one(lat, beta, J, h, seed, out);
+}
+
+ac_status ac_set_stream(ac_sim* sim, void* stream) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  sim->stream = (cudaStream_t)stream;
+  drop_runners_of(sim);
+  return AC_OK;
+}
+
+ac_status ac_configure(ac_sim* sim, int32_t kernel, int32_t Lb, int32_t rounds, int32_t polls) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  if (kernel != AC_KERNEL_ROUND && kernel != AC_KERNEL_BLOCKED)
+    return fail(AC_ERR_ARG, "kernel must be AC_KERNEL_ROUND or AC_KERNEL_BLOCKED");
+  if (Lb != 32 && Lb != 64 && Lb != 128) return fail(AC_ERR_ARG, "Lb must be 32, 64 or 128");
+  if (rounds < 1 || rounds > 1 << 20) return fail(AC_ERR_ARG, "rounds must be in [1, 2^20]");
+  if (polls < 0 || polls > 1 << 20) return fail(AC_ERR_ARG, "polls must be in [0, 2^20]");
+  sim->cfg.kernel = kernel;
+  sim->cfg.lb = Lb;
+  sim->cfg.threads = 4 * Lb;
+  if (kernel == AC_KERNEL_ROUND) {
+    sim->cfg.rounds = rounds;
+  } else {
+    sim->cfg.refresh = rounds;
+    sim->cfg.polls = polls;
+  }
+  drop_runners_of(sim);
+  return alloc_edges(sim);
+}
+
+ac_status ac_run_until_ticks(ac_sim* sim, int64_t t_end) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  if (t_end < sim->t_done) return fail(AC_ERR_ARG, "t_end %lld is below the previous t_end %lld",
+                                       (long long)t_end, sim->t_done);
+  if (t_end >= kTickLimit) return fail(AC_ERR_ARG, "t_end must be < 2^61");
+  unsigned long long before = 0, after = 0;
+  ac_status st = read_event_counter(sim, &before);
+  if (st != AC_OK) return st;
+  st = (sim->cfg.kernel == ac::kKernelRound) ? run_round(sim, t_end) : run_blocked(sim, t_end);
+  if (st != AC_OK) return st;
+  st = read_event_counter(sim, &after);
+  if (st != AC_OK) return st;
+  sim->events += after - before;
+  sim->t_done = t_end;
+  return AC_OK;
+}
+
+ac_status ac_run_until(ac_sim* sim, double T) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  if (!std::isfinite(T) || T < 0.0) return fail(AC_ERR_ARG, "T must be finite and >= 0");
+  const double ticks = std::floor(T * kTicksPerUnit);
+  if (ticks >= (double)kTickLimit) return fail(AC_ERR_ARG, "T too large (t_end must be < 2^61)");
+  return ac_run_until_ticks(sim, (int64_t)ticks);
+}
+
+ac_status ac_read_state(const ac_sim* sim, int8_t* s, int64_t* t, uint32_t* n) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  const size_t N = sim->ncells();
+  if (s || t) {
+    std::vector<int64_t> tmp;
+    int64_t* kbuf = t;
+    if (!kbuf) {
+      tmp.resize(N);
+      kbuf = tmp.data();
+    }
+    AC_CUDA(cudaMemcpyAsync(kbuf, sim->key, N * 8, cudaMemcpyDeviceToHost, sim->stream));
+    AC_CUDA(cudaStreamSynchronize(sim->stream));
+    for (size_t c = 0; c < N; ++c) {
+      const uint64_t k = (uint64_t)kbuf[c];
+      if (s) s[c] = (k & 1u) ? 1 : -1;
+      if (t) t[c] = (int64_t)(k >> 1);
+    }
+  }
+  if (n) {
+    AC_CUDA(cudaMemcpyAsync(n, sim->cnt, N * 4, cudaMemcpyDeviceToHost, sim->stream));
+    AC_CUDA(cudaStreamSynchronize(sim->stream));
+  }
+  return AC_OK;
+}
+
+ac_status ac_read_state_device(const ac_sim* sim, int8_t* s, int64_t* t, uint32_t* n) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  const ac::LatDesc d = sim->host_desc(sim->t_done, 0);
+  AC_CUDA(ac::launch_unpack(&d, s, (long long*)t, n, sim->stream));
+  AC_CUDA(cudaStreamSynchronize(sim->stream));
+  return AC_OK;
+}
+
+ac_status ac_load_state(ac_sim* sim, const int8_t* s, const int64_t* t, const uint32_t* n,
+                        int64_t t_done) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  if (!s || !t || !n) return fail(AC_ERR_ARG, "s, t and n are required");
+  if (t_done < 0 || t_done >= kTickLimit) return fail(AC_ERR_ARG, "t_done out of range");
+  const size_t N = sim->ncells();
+  std::vector<uint64_t> packed(N);
+  const long long tmin = std::max<long long>(t_done, 1);
+  for (size_t c = 0; c < N; ++c) {
+    if (s[c] != 1 && s[c] != -1) return fail(AC_ERR_ARG, "spin of cell %zu is %d (must be +-1)", c, s[c]);
+    if (t[c] < tmin || t[c] >= kTickLimit)
+      return fail(AC_ERR_ARG, "tick of cell %zu is %lld, outside [%lld, 2^61)", c, (long long)t[c], tmin);
+    packed[c] = ((uint64_t)t[c] << 1) | (s[c] > 0 ? 1u : 0u);
+  }
+  AC_CUDA(cudaMemcpyAsync(sim->key, packed.data(), N * 8, cudaMemcpyHostToDevice, sim->stream));
+  AC_CUDA(cudaMemcpyAsync(sim->cnt, n, N * 4, cudaMemcpyHostToDevice, sim->stream));
+  AC_CUDA(cudaStreamSynchronize(sim->stream));
+  sim->t_done = t_done;
+  return AC_OK;
+}
+
+ac_status ac_stats(const ac_sim* sim, ac_stats_t* o) {
+  if (!sim || !o) return fail(AC_ERR_ARG, "sim and out are required");
+  std::memset(o, 0, sizeof *o);
+  unsigned long long r[4] = {0, 0, 0, 0};
+  const ac::LatDesc d = sim->host_desc(sim->t_done, 0);
+  AC_CUDA(cudaMemsetAsync(sim->d_red, 0, sizeof r, sim->stream));
+  AC_CUDA(ac::launch_reduce(&d, sim->d_red, sim->stream));
+  AC_CUDA(cudaMemcpyAsync(r, sim->d_red, sizeof r, cudaMemcpyDeviceToHost, sim->stream));
+  AC_CUDA(cudaStreamSynchronize(sim->stream));
+  o->events = sim->events;
+  o->rounds = sim->rounds;
+  o->launches = sim->launches;
+  o->scanned = sim->scanned;
+  o->enabled = sim->enabled;
+  o->visits = sim->visits;
+  o->polls = sim->polls;
+  o->global_rounds = sim->global_rounds;
+  o->device_ms = sim->device_ms;
+  if (sim->global_rounds > 0)
+    o->enabled_frac_mean = (double)sim->enabled_r1 / ((double)sim->global_rounds * (double)sim->ncells());
+  else if (sim->scanned > 0)
+    o->enabled_frac_mean = (double)sim->enabled / (double)sim->scanned;
+  o->sum_s = (int64_t)r[0];
+  o->sum_bonds = (int64_t)r[1];
+  o->checksum = r[2];
+  o->total_counts = r[3];
+  o->t_done = sim->t_done;
+  o->kernel = sim->cfg.kernel;
+  o->Lb = sim->cfg.lb;
+  o->threads = sim->cfg.threads;
+  o->rounds_per_launch = sim->cfg.kernel == ac::kKernelRound ? sim->cfg.rounds : sim->cfg.refresh;
+  o->grid = sim->last_grid;
+  o->ctas_per_sm = sim->ctas_per_sm;
+  return AC_OK;
+}
+
+ac_status ac_round_history(const ac_sim* sim, uint64_t* counts, int32_t cap, int32_t* n_rounds) {
+  if (!sim || !n_rounds) return fail(AC_ERR_ARG, "sim and n_rounds are required");
+  const int avail = (int)std::min<unsigned long long>(sim->global_rounds, (unsigned long long)sim->hist_cap);
+  *n_rounds = avail;
+  if (counts && cap > 0 && avail > 0 && sim->d_hist) {
+    const int m = std::min(avail, cap);
+    AC_CUDA(cudaMemcpyAsync(counts, sim->d_hist, (size_t)m * 8, cudaMemcpyDeviceToHost, sim->stream));
+    AC_CUDA(cudaStreamSynchronize(sim->stream));
+  }
+  return AC_OK;
+}
+
+ac_status ac_reset(ac_sim* sim, uint64_t seed, int32_t init) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  if (init < AC_INIT_RANDOM || init > AC_INIT_DOWN) return fail(AC_ERR_ARG, "bad init mode");
+  sim->seed = seed;
+  sim->init = init;
+  const ac::LatDesc d = sim->host_desc(0, 0);
+  AC_CUDA(ac::launch_init(&d, init, sim->stream));
+  AC_CUDA(cudaMemsetAsync(sim->d_events, 0, 8, sim->stream));
+  if (sim->d_hist) AC_CUDA(cudaMemsetAsync(sim->d_hist, 0, (size_t)sim->hist_cap * 8, sim->stream));
+  AC_CUDA(cudaStreamSynchronize(sim->stream));
+  sim->t_done = 0;
+  sim->events = sim->rounds = sim->launches = sim->scanned = sim->enabled = sim->visits = sim->polls = 0;
+  sim->global_rounds = sim->enabled_r1 = 0;
+  sim->device_ms = 0.0;
+  drop_runners_of(sim);
+  return AC_OK;
+}
+
+ac_status ac_set_option(ac_sim* sim, int32_t option, int64_t value) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  switch (option) {
+    case AC_OPT_WATCHDOG_NS:
+      if (value < 1000000) return fail(AC_ERR_ARG, "watchdog must be >= 1e6 ns");
+      sim->cfg.watchdog_ns = value;
+      break;
+    case AC_OPT_MAX_ROUNDS:
+      if (value < 0 || value > (1 << 30)) return fail(AC_ERR_ARG, "max rounds out of range");
+      sim->cfg.max_rounds = (int)value;
+      break;
+    case AC_OPT_DROP_PUBLISH:
+      sim->drop_publish = value ? 1 : 0;
+      break;
+    default:
+      return fail(AC_ERR_ARG, "unknown option %d", option);
+  }
+  drop_runners_of(sim);
+  return AC_OK;
+}
+
+void ac_destroy(ac_sim* sim) {
+  if (!sim) return;
+  drop_runners_of(sim);
+  cudaStreamSynchronize(sim->stream);
+  free_sim(sim);
+}
+
+ac_status ac_batch_create(int32_t n, const ac_lattice* lats, const double* beta, const double* J,
+                          const double* h, const uint64_t* seed, ac_sim** out) {
+  if (n <= 0 || !lats || !beta || !J || !h || !seed || !out)
+    return fail(AC_ERR_ARG, "n > 0 and all arrays are required");
+  for (int i = 0; i < n; ++i) {
+    ac_status st = check_params(lats[i], beta[i], J[i], h[i]);
+    if (st != AC_OK) return fail(st, "lattice %d: %s", i, g_err.c_str());
+  }
+  for (int i = 0; i < n; ++i) out[i] = nullptr;
+  for (int i = 0; i < n; ++i) {
+    ac_status st = create_one(lats[i], beta[i], J[i], h[i], seed[i], &out[i]);
+    if (st != AC_OK) {
+      for (int k = 0; k < i; ++k) {
+        free_sim(out[k]);
+        out[k] = nullptr;
+      }
+      return st;
+    }
+  }
+  return AC_OK;
+}
+
+ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_end) {
+  if (n <= 0 || !sims || !t_end) return fail(AC_ERR_ARG, "n > 0, sims and t_end are required");
+  for (int i = 0; i < n; ++i) {
+    if (!sims[i]) return fail(AC_ERR_ARG, "sims[%d] is NULL", i);
+    if (sims[i]->cfg.lb != sims[0]->cfg.lb) return fail(AC_ERR_ARG, "all handles must share a tile side");
+    if (sims[i]->stream != sims[0]->stream) return fail(AC_ERR_ARG, "all handles must share a stream");
+    if (t_end[i] < sims[i]->t_done) return fail(AC_ERR_ARG, "t_end[%d] is below its previous t_end", i);
+    if (t_end[i] >= kTickLimit) return fail(AC_ERR_ARG, "t_end[%d] must be < 2^61", i);
+    for (int k = 0; k < i; ++k)
+      if (sims[k] == sims[i]) return fail(AC_ERR_ARG, "handle %d appears twice", i);
+  }
+  std::vector<ac_sim*> keyv(sims, sims + n);
+  BatchRunner* R = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    auto it = g_runners.find(keyv);
+    if (it != g_runners.end()) R = it->second;
+  }
+  if (!R) {
+    R = new BatchRunner();
+    R->sims = keyv;
+    R->lb = sims[0]->cfg.lb;
+    // graph capture needs a capturable stream: the legacy default stream is not one,
+    // so such handles get a blocking stream of the runner (ordered with the legacy stream)
+    if (sims[0]->stream == nullptr) {
+      if (cudaStreamCreate(&R->own_stream) != cudaSuccess) {
+        free_runner(R);
+        return fail(AC_ERR_CUDA, "cudaStreamCreate failed");
+      }
+      R->stream = R->own_stream;
+    } else {
+      R->stream = sims[0]->stream;
+    }
+    const cudaStream_t stream = R->stream;
+    R->cfg = sims[0]->cfg;
+    R->cfg.kernel = ac::kKernelBlocked;
+    int per_sm = 0;
+    const int maxc = ac::blocked_max_ctas(R->lb, &per_sm);
+    int total = 0;
+    for (int i = 0; i < n; ++i) total += sims[i]->tiles();
+    R->total_tiles = total;
+    R->grid = std::min(total, maxc);
+    if (maxc <= 0 || cudaHostAlloc(&R->h_desc, sizeof(ac::LatDesc) * n, cudaHostAllocDefault) != cudaSuccess ||
+        cudaMalloc(&R->d_desc, sizeof(ac::LatDesc) * n) != cudaSuccess ||
+        cudaMalloc(&R->d_ctr, sizeof(ac::DevCounters)) != cudaSuccess ||
+        cudaMalloc(&R->d_tile_done, (size_t)total * 4) != cudaSuccess ||
+        cudaEventCreate(&R->ev0) != cudaSuccess || cudaEventCreate(&R->ev1) != cudaSuccess) {
+      cudaGetLastError();
+      free_runner(R);
+      return fail(AC_ERR_OOM, "batch runner allocation failed");
+    }
+    int base = 0;
+    for (int i = 0; i < n; ++i) {
+      R->h_desc[i] = sims[i]->host_desc(t_end[i], base);
+      base += sims[i]->tiles();
+    }
+    cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R->d_desc, R->h_desc, sizeof(ac::LatDesc) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(R->d_ctr, 0, sizeof(ac::DevCounters), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(R->d_tile_done, 0, (size_t)total * 4, stream);
+    if (e == cudaSuccess) e = ac::launch_publish(R->d_desc, n, total, R->lb, 0, stream);
+    if (e == cudaSuccess) e = ac::launch_blocked(R->d_desc, n, total, R->cfg, R->grid, R->d_tile_done, R->d_ctr, stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(stream, &g);
+    if (e == cudaSuccess) e = e2;
+    R->graph = g;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&R->exec, g, 0);
+    if (e != cudaSuccess) {
+      free_runner(R);
+      return fail(AC_ERR_CUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_runners[keyv] = R;
+  }
+  const cudaStream_t stream = R->stream;
+  // per-lattice event counters before the launch
+  std::vector<unsigned long long> before(n), after(n);
+  for (int i = 0; i < n; ++i)
+    AC_CUDA(cudaMemcpyAsync(&before[i], sims[i]->d_events, 8, cudaMemcpyDeviceToHost, stream));
+  AC_CUDA(cudaStreamSynchronize(stream));
+  int base = 0;
+  for (int i = 0; i < n; ++i) {
+    R->h_desc[i] = sims[i]->host_desc(t_end[i], base);
+    base += sims[i]->tiles();
+  }
+  // the timed interval covers the whole graph: descriptor copy, flag resets, the edge-word
+  // publish kernel (a few microseconds) and the blocked kernel
+  AC_CUDA(cudaEventRecord(R->ev0, stream));
+  AC_CUDA(cudaGraphLaunch(R->exec, stream));
+  AC_CUDA(cudaEventRecord(R->ev1, stream));
+  ac::DevCounters c{};
+  AC_CUDA(cudaMemcpyAsync(&c, R->d_ctr, sizeof c, cudaMemcpyDeviceToHost, stream));
+  for (int i = 0; i < n; ++i)
+    AC_CUDA(cudaMemcpyAsync(&after[i], sims[i]->d_events, 8, cudaMemcpyDeviceToHost, stream));
+  AC_CUDA(cudaStreamSynchronize(stream));
+  float ms = 0.f;
+  AC_CUDA(cudaEventElapsedTime(&ms, R->ev0, R->ev1));
+  if (c.error) return fail((ac_status)c.error, "device watchdog: no progress (block %d)", c.err_block);
+  for (int i = 0; i < n; ++i) {
+    ac_sim* s = sims[i];
+    s->events += after[i] - before[i];
+    s->t_done = t_end[i];
+    s->launches += 1;
+    s->device_ms += ms;
+    s->last_grid = R->grid;
+  }
+  // aggregate counters are attributed to the first handle
+  sims[0]->rounds += c.rounds;
+  sims[0]->scanned += c.scanned;
+  sims[0]->enabled += c.enabled;
+  sims[0]->visits += c.visits;
+  sims[0]->polls += c.polls;
+  return AC_OK;
+}
+
+ac_status ac_dev_exp_ticks(const uint32_t* x, uint64_t* out, int64_t n) {
+  if (n < 0 || (n > 0 && (!x || !out))) return fail(AC_ERR_ARG, "bad arguments");
+  AC_CUDA(ac::launch_exp_ticks(x, (unsigned long long*)out, n, nullptr));
+  AC_CUDA(cudaStreamSynchronize(nullptr));
+  return AC_OK;
+}
+
+ac_status ac_dev_philox(uint64_t seed, const uint32_t* c, const uint32_t* k, uint32_t w2, uint32_t* out4,
+                        int64_t n) {
+  if (n < 0 || (n > 0 && (!c || !k || !out4))) return fail(AC_ERR_ARG, "bad arguments");
+  AC_CUDA(ac::launch_philox(seed, c, k, w2, out4, n, nullptr));
+  AC_CUDA(cudaStreamSynchronize(nullptr));
+  return AC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// ac_internal.h -- structures shared by the kernels (ac_kernels.cu) and the host
+// runtime (ac_api.cu).  Not part of the public C ABI (include/ac.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ac {
+
+// Per-lattice descriptor, resident in device memory for the kernels.
+//
+// Device state of a rows x cols torus (row-major):
+//   key[c] = tick << 1 | (spin > 0)   next-arrival tick and current spin
+//   cnt[c] = number of committed arrivals of cell c
+// Tiling: tr x tc tiles; tile (i, j) covers rows [r0(i), r0(i)+h(i)) with
+// r0(i) = i*(rows/tr) + min(i, rows%tr), h(i) = rows/tr + (i < rows%tr), and the
+// same for columns; every tile side is <= lb.
+// Edge words: pub[(ti*tc + tj)*4*lb + e*lb + p] is the key of the tile's boundary
+// cell p on edge e (0 top row, 1 bottom row, 2 left column, 3 right column).
+struct LatDesc {
+  unsigned long long* key;
+  unsigned int* cnt;
+  unsigned long long* pub;   // edge words, live (blocked kernel) / round input
+  unsigned long long* pub2;  // round kernel output edge words (ping-pong)
+  unsigned long long* events;  // per-lattice committed-arrival counter
+  int rows, cols;
+  int tr, tc;
+  int lb;
+  int tile_base;             // first tile of this lattice in the launch's work list
+  unsigned int thr[10];      // flip thresholds, index j + 5*(s > 0)
+  unsigned int seed_lo, seed_hi;
+  long long t_end;           // commit arrivals with tick < t_end
+  unsigned long long t2;     // 2 * t_end: key < t2  <=>  tick < t_end
+  int drop_publish;          // verification hook: suppress edge-word publication
+  int pad_;
+};
+
+// Device counters of one run call (zeroed by the host before the call).
+struct DevCounters {
+  unsigned long long events;    // committed arrivals
+  unsigned long long rounds;    // tile rounds executed (commit phases)
+  unsigned long long scanned;   // cells tested by the enable test
+  unsigned long long enabled;   // cells found enabled
+  unsigned long long visits;    // tile visits (blocked kernel)
+  unsigned long long polls;     // halo polls while a tile was blocked
+  int error;                    // AC_ERR_* set by the device watchdog
+  int err_block;
+  unsigned int active[3];       // round kernel: tiles with pending arrivals (mod-3 ring)
+  unsigned int launched;        // round kernel: launches that did work
+};
+
+enum KernelKind { kKernelRound = 0, kKernelBlocked = 1 };
+
+struct LaunchCfg {
+  int kernel;       // KernelKind
+  int lb;           // 32, 64 or 128
+  int threads;      // 4 * lb
+  int rounds;       // round kernel: rounds per launch (1 = exact synchronous rounds)
+  int polls;        // blocked kernel: halo polls before a blocked tile is left
+  int refresh;      // blocked kernel: refresh halos every `refresh` rounds
+  int max_rounds;   // blocked kernel: cap on rounds per tile visit (0 = none)
+  long long watchdog_ns;  // blocked kernel: no-progress limit before AC_ERR_STALL
+};
+
+// ---- launchers (ac_kernels.cu) -------------------------------------------------
+size_t tile_smem_bytes(int lb);
+int blocked_max_ctas(int lb, int* per_sm);   // resident CTAs of the blocked kernel
+cudaError_t launch_init(const LatDesc* host_desc, int init_mode, cudaStream_t s);
+cudaError_t launch_publish(const LatDesc* d_desc, int nlat, int total_tiles, int lb, int to_pub2,
+                           cudaStream_t s);
+cudaError_t launch_round(const LatDesc* d_desc, int nlat, int total_tiles, const LaunchCfg& cfg,
+                         int parity, int launch_idx, DevCounters* ctr, unsigned long long* hist,
+                         int hist_len, int round_idx, cudaStream_t s);
+cudaError_t launch_blocked(const LatDesc* d_desc, int nlat, int total_tiles, const LaunchCfg& cfg,
+                           int grid, unsigned int* tile_done, DevCounters* ctr, cudaStream_t s);
+cudaError_t launch_reduce(const LatDesc* host_desc, unsigned long long* d_out4, cudaStream_t s);
+cudaError_t launch_unpack(const LatDesc* host_desc, int8_t* s_out, long long* t_out,
+                          unsigned int* n_out, cudaStream_t st);
+cudaError_t launch_pack(const LatDesc* host_desc, const int8_t* s_in, const long long* t_in,
+                        const unsigned int* n_in, cudaStream_t st);
+cudaError_t launch_exp_ticks(const uint32_t* x, unsigned long long* out, long long n, cudaStream_t s);
+cudaError_t launch_philox(unsigned long long seed, const uint32_t* c, const uint32_t* k, uint32_t w2,
+                          uint32_t* out4, long long n, cudaStream_t s);
+
+}  // namespace ac

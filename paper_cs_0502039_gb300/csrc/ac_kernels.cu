@@ -1,0 +1,781 @@
+// ac_kernels.cu -- sm_103a kernels of the exact parallel simulator of the
+// Poisson-asynchronous Glauber (continuous-time Ising) cellular array.
+//
+// Paper: Lubachevsky, "Efficient Parallel Simulations of Asynchronous Cellular
+// Arrays".  A cell may commit its next arrival once its (tick, index) key is
+// below the keys of all its neighbours (Fig. 3.1 with the tie rule that the
+// smaller row-major index goes first); the result is the unique trajectory of
+// the standard serial procedure (Sec. 1) whatever the execution schedule.
+//
+// Shared-memory tile engine (used by both kernels).  A CTA holds one tile of at
+// most LB x LB cells: the packed keys with a one-cell halo ring, the event
+// counts and a compacted work list.  One tile round is
+//   scan    every thread walks a column segment and tests its cells against
+//           the four neighbours (the enable test of Fig. 3.2, step 2); enabled
+//           cells are appended to the work list (warp prefix + one shared
+//           atomic per warp);
+//   commit  after a barrier, all threads take list entries: neighbour spin
+//           sum, one Philox4x32-10 block, flip decision against the threshold
+//           table (Eq. (1)) and the next arrival (Eq. (5)); enabled cells form
+//           an independent set, so they are updated in place; a barrier ends
+//           the round (Fig. 3.2's two synchronisations).
+// The enable test works on packed words: with key = tick<<1 | up,
+//   tick_c <  tick_n  <=>  (key_c | 1)  <  key_n    (neighbour with smaller index)
+//   tick_c <= tick_n  <=>  (key_c & ~1) <= key_n    (neighbour with larger index)
+// Inside a tile the up/left neighbours have smaller and the down/right
+// neighbours larger indices; at the torus wrap the order flips, which the halo
+// absorbs by storing key + 2 (turns "<" into "<=") or key - 2 (turns "<=" into
+// "<").  Halo cells never commit.
+//
+// (a) round kernel: one launch per R tile rounds; halos are frozen copies of the
+//     neighbour tiles' edge words of the previous launch (ping-pong), so R = 1 is
+//     exactly the synchronous one-cell-per-PE algorithm of Fig. 3.2 run over the
+//     whole lattice.
+// (b) blocked persistent kernel: the aggregated algorithm of Fig. 3.4 with one
+//     CTA per PE and a tile per subarray.  A CTA owns a fixed set of tiles and
+//     visits them in turn; boundary commits are published at once as edge words
+//     in HBM and neighbours refresh their halos from them.  A published word only
+//     grows, so a stale halo value is a lower bound of the neighbour's key and can
+//     only delay a commit, never admit a wrong one (the argument of Sec. 3 that a
+//     neighbour's state cannot change in (T1, T5)).  Blocked tiles poll a bounded
+//     number of times and are then left for the CTA's next tile; a
+//     %globaltimer watchdog turns a stall into an error code.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "ac_device.cuh"
+#include "ac_internal.h"
+
+namespace ac {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+struct Geom {
+  int ti, tj, r0, h, c0, w;
+};
+
+__device__ __forceinline__ Geom tile_geom(const LatDesc& L, int t) {
+  Geom g;
+  g.ti = t / L.tc;
+  g.tj = t - g.ti * L.tc;
+  int q = L.rows / L.tr, rm = L.rows - q * L.tr;
+  g.r0 = g.ti * q + min(g.ti, rm);
+  g.h = q + (g.ti < rm);
+  q = L.cols / L.tc;
+  rm = L.cols - q * L.tc;
+  g.c0 = g.tj * q + min(g.tj, rm);
+  g.w = q + (g.tj < rm);
+  return g;
+}
+
+// Lattice owning global tile `tile` (tile_base ascending).
+__device__ __forceinline__ int find_lattice(const LatDesc* lats, int nlat, int tile) {
+  int lo = 0, hi = nlat - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&lats[mid].tile_base) <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int LB>
+struct TileShape {
+  static constexpr int P = LB + 2;                 // key row pitch (words), halo ring included
+  static constexpr int NT = 4 * LB;                // threads: LB columns x 4 row groups
+  static constexpr int LIST = LB * LB / 2 + LB;    // enabled cells form an independent set
+  static constexpr size_t kBytes = size_t(P) * P * 8;
+  static constexpr size_t cBytes = size_t(LB) * LB * 4;
+  static constexpr size_t lBytes = ((size_t(LIST) * 2 + 15) / 16) * 16;
+  static constexpr size_t mBytes = 64;             // n_en[2], thr[10]
+  static constexpr size_t bytes = kBytes + cBytes + lBytes + mBytes;
+};
+
+template <int LB>
+struct Smem {
+  unsigned long long* K;
+  unsigned int* C;
+  unsigned short* list;
+  unsigned int* n_en;   // [2]
+  unsigned int* thr;    // [10]
+  __device__ __forceinline__ explicit Smem(unsigned char* base) {
+    using S = TileShape<LB>;
+    K = reinterpret_cast<unsigned long long*>(base);
+    C = reinterpret_cast<unsigned int*>(base + S::kBytes);
+    list = reinterpret_cast<unsigned short*>(base + S::kBytes + S::cBytes);
+    n_en = reinterpret_cast<unsigned int*>(base + S::kBytes + S::cBytes + S::lBytes);
+    thr = n_en + 2;
+  }
+};
+
+// Per-thread halo slot: thread tid handles edge e = tid / LB, position p = tid % LB.
+struct HaloSlot {
+  const unsigned long long* src;   // neighbour tile's edge word (nullptr: none / self-wrap)
+  long long adj;                   // +2 / -2 at the torus wrap, else 0
+  int slot;                        // index into K (-1: unused)
+  int mirror;                      // self-wrap: index into K of the mirrored own cell (-1: none)
+};
+
+template <int LB>
+__device__ __forceinline__ HaloSlot halo_slot(const LatDesc& L, const Geom& g,
+                                              const unsigned long long* pub) {
+  constexpr int P = TileShape<LB>::P;
+  const int e = threadIdx.x / LB, p = threadIdx.x % LB;
+  HaloSlot s{nullptr, 0, -1, -1};
+  const bool row_edge = e < 2;
+  if (row_edge ? (p >= g.w) : (p >= g.h)) return s;
+  switch (e) {
+    case 0: s.slot = p + 1; s.adj = (g.ti == 0) ? 2 : 0; break;                 // top halo
+    case 1: s.slot = (g.h + 1) * P + p + 1; s.adj = (g.ti == L.tr - 1) ? -2 : 0; break;
+    case 2: s.slot = (p + 1) * P; s.adj = (g.tj == 0) ? 2 : 0; break;            // left halo
+    default: s.slot = (p + 1) * P + g.w + 1; s.adj = (g.tj == L.tc - 1) ? -2 : 0; break;
+  }
+  const bool self = row_edge ? (L.tr == 1) : (L.tc == 1);
+  if (self) {
+    switch (e) {
+      case 0: s.mirror = g.h * P + p + 1; break;          // own row h-1
+      case 1: s.mirror = 1 * P + p + 1; break;            // own row 0
+      case 2: s.mirror = (p + 1) * P + g.w; break;        // own column w-1
+      default: s.mirror = (p + 1) * P + 1; break;         // own column 0
+    }
+    return s;
+  }
+  int nti = g.ti, ntj = g.tj, ne;
+  switch (e) {
+    case 0: nti = (g.ti + L.tr - 1) % L.tr; ne = 1; break;
+    case 1: nti = (g.ti + 1) % L.tr; ne = 0; break;
+    case 2: ntj = (g.tj + L.tc - 1) % L.tc; ne = 3; break;
+    default: ntj = (g.tj + 1) % L.tc; ne = 2; break;
+  }
+  s.src = pub + ((size_t)(nti * L.tc + ntj) * 4 + ne) * LB + p;
+  return s;
+}
+
+// Load the tile's interior keys (and counts) from HBM into shared memory.
+template <int LB, bool COUNTS>
+__device__ __forceinline__ void load_interior(const Smem<LB>& sm, const LatDesc& L, const Geom& g) {
+  constexpr int P = TileShape<LB>::P;
+  const int c = threadIdx.x % LB;
+  if (c >= g.w) return;
+  for (int r = threadIdx.x / LB; r < g.h; r += 4) {
+    const size_t gi = (size_t)(g.r0 + r) * L.cols + g.c0 + c;
+    sm.K[(r + 1) * P + c + 1] = L.key[gi];
+    if (COUNTS) sm.C[r * LB + c] = L.cnt[gi];
+  }
+}
+
+template <int LB, bool COUNTS>
+__device__ __forceinline__ bool store_interior(const Smem<LB>& sm, const LatDesc& L, const Geom& g) {
+  constexpr int P = TileShape<LB>::P;
+  const int c = threadIdx.x % LB;
+  bool unfinished = false;
+  if (c >= g.w) return false;
+  for (int r = threadIdx.x / LB; r < g.h; r += 4) {
+    const size_t gi = (size_t)(g.r0 + r) * L.cols + g.c0 + c;
+    const unsigned long long k = sm.K[(r + 1) * P + c + 1];
+    L.key[gi] = k;
+    if (COUNTS) L.cnt[gi] = sm.C[r * LB + c];
+    unfinished |= k < L.t2;
+  }
+  return unfinished;
+}
+
+// Enable test over the thread's column segment; appends enabled cells to the list.
+// Returns whether any of the thread's cells still has an arrival before t_end.
+template <int LB>
+__device__ __forceinline__ bool scan_tile(const Smem<LB>& sm, const Geom& g, unsigned long long t2,
+                                          unsigned int* n_slot, unsigned long long& scanned) {
+  constexpr int P = TileShape<LB>::P;
+  const int c = threadIdx.x % LB;
+  const int grp = threadIdx.x / LB;
+  const int rpg = (g.h + 3) >> 2;
+  const int rb = grp * rpg;
+  const int re = min(g.h, rb + rpg);
+  unsigned mask = 0;
+  bool live_any = false;
+  if (c < g.w && rb < re) {
+    const unsigned long long* col = sm.K + (rb + 1) * P + (c + 1);
+    unsigned long long up = col[-P];
+    unsigned long long cur = col[0];
+#pragma unroll 4
+    for (int r = rb; r < re; ++r) {
+      const unsigned long long down = col[P];
+      const unsigned long long left = col[-1];
+      const unsigned long long right = col[1];
+      const unsigned long long hi = cur | 1ull, lo = cur & ~1ull;
+      const bool live = cur < t2;
+      const bool en = live & (hi < up) & (hi < left) & (lo <= right) & (lo <= down);
+      live_any |= live;
+      mask |= (unsigned)en << (r - rb);
+      up = cur;
+      cur = down;
+      col += P;
+    }
+    scanned += (unsigned long long)(re - rb);
+  }
+  // warp-level compaction: inclusive prefix of per-thread counts, one atomic per warp
+  const int lane = threadIdx.x & 31;
+  const int cnt = __popc(mask);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
+  }
+  int base = 0;
+  if (lane == 31 && incl) base = (int)atomicAdd(n_slot, (unsigned)incl);
+  base = __shfl_sync(kFull, base, 31);
+  int off = base + incl - cnt;
+  while (mask) {
+    const int b = __ffs(mask) - 1;
+    mask &= mask - 1;
+    sm.list[off++] = (unsigned short)(((rb + b) << 8) | c);
+  }
+  return live_any;
+}
+
+// Commit the listed cells.  DIRECT: counts and keys are read from / written to HBM
+// (single exact round per launch); PUBLISH: boundary commits are published as
+// edge words (blocked kernel).
+template <int LB, bool DIRECT, bool PUBLISH>
+__device__ __forceinline__ void commit_tile(const Smem<LB>& sm, const LatDesc& L, const Geom& g,
+                                            unsigned long long* pub_tile, int n) {
+  constexpr int P = TileShape<LB>::P;
+  constexpr int NT = TileShape<LB>::NT;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const unsigned e = sm.list[i];
+    const int r = (int)(e >> 8), c = (int)(e & 255u);
+    unsigned long long* kp = sm.K + (r + 1) * P + (c + 1);
+    const unsigned long long key = *kp;
+    const unsigned j = ((unsigned)kp[-P] & 1u) + ((unsigned)kp[P] & 1u) +
+                       ((unsigned)kp[-1] & 1u) + ((unsigned)kp[1] & 1u);
+    const unsigned sp = (unsigned)key & 1u;
+    const uint32_t gidx = (uint32_t)(g.r0 + r) * (uint32_t)L.cols + (uint32_t)(g.c0 + c);
+    const unsigned n_old = DIRECT ? L.cnt[gidx] : sm.C[r * LB + c];
+    const Philox4 b = philox_event(gidx, n_old + 1u, 0u, L.seed_lo, L.seed_hi);
+    const unsigned flip = b.y < sm.thr[j + 5u * sp] ? 1u : 0u;
+    const unsigned long long nk = (key & ~1ull) + (exp_ticks(b.x) << 1) + (sp ^ flip);
+    *kp = nk;
+    if (DIRECT) {
+      L.key[gidx] = nk;
+      L.cnt[gidx] = n_old + 1u;
+    } else {
+      sm.C[r * LB + c] = n_old + 1u;
+    }
+    if (L.tr == 1) {                    // vertical self-wrap: keep the mirrored halo rows live
+      if (r == 0) sm.K[(g.h + 1) * P + c + 1] = nk - 2ull;
+      if (r == g.h - 1) sm.K[c + 1] = nk + 2ull;
+    } else if (PUBLISH && !L.drop_publish) {
+      if (r == 0) st_relaxed(pub_tile + c, nk);
+      if (r == g.h - 1) st_relaxed(pub_tile + LB + c, nk);
+    }
+    if (L.tc == 1) {
+      if (c == 0) sm.K[(r + 1) * P + g.w + 1] = nk - 2ull;
+      if (c == g.w - 1) sm.K[(r + 1) * P] = nk + 2ull;
+    } else if (PUBLISH && !L.drop_publish) {
+      if (c == 0) st_relaxed(pub_tile + 2 * LB + r, nk);
+      if (c == g.w - 1) st_relaxed(pub_tile + 3 * LB + r, nk);
+    }
+  }
+}
+
+// Fill the halo ring: neighbour edge words (+adj) or the mirrored own cells.
+template <int LB, bool RELAXED>
+__device__ __forceinline__ void fill_halo(const Smem<LB>& sm, const HaloSlot& hs) {
+  if (hs.slot < 0) return;
+  if (hs.mirror >= 0) {
+    sm.K[hs.slot] = sm.K[hs.mirror] + (unsigned long long)hs.adj;
+  } else {
+    const unsigned long long v = RELAXED ? ld_relaxed(hs.src) : __ldg(hs.src);
+    sm.K[hs.slot] = v + (unsigned long long)hs.adj;
+  }
+}
+
+// Write the tile's boundary cells to its edge words (after a round-kernel launch).
+template <int LB>
+__device__ __forceinline__ void write_edges(const Smem<LB>& sm, const Geom& g,
+                                            unsigned long long* pub_tile) {
+  constexpr int P = TileShape<LB>::P;
+  const int e = threadIdx.x / LB, p = threadIdx.x % LB;
+  if (e < 2) {
+    if (p < g.w) pub_tile[e * LB + p] = sm.K[(e == 0 ? 1 : g.h) * P + p + 1];
+  } else {
+    if (p < g.h) pub_tile[e * LB + p] = sm.K[(p + 1) * P + (e == 2 ? 1 : g.w)];
+  }
+}
+
+// ------------------------------------------------------------------- kernels
+
+__global__ void init_kernel(LatDesc L, int init_mode) {
+  const size_t N = (size_t)L.rows * L.cols;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const Philox4 b0 = philox_event((uint32_t)c, 0u, 0u, L.seed_lo, L.seed_hi);
+    unsigned up;
+    if (init_mode == 1) up = 1u;
+    else if (init_mode == 2) up = 0u;
+    else up = philox_event((uint32_t)c, 0u, 1u, L.seed_lo, L.seed_hi).x & 1u;
+    L.key[c] = (exp_ticks(b0.x) << 1) | up;
+    L.cnt[c] = 0u;
+  }
+}
+
+// Copy every tile's boundary cells from key[] into its edge words.
+template <int LB>
+__global__ void __launch_bounds__(4 * LB) publish_kernel(const LatDesc* __restrict__ lats, int nlat,
+                                                         int to_pub2) {
+  const int tile = blockIdx.x;
+  const LatDesc& L = lats[find_lattice(lats, nlat, tile)];
+  const int t = tile - L.tile_base;
+  const Geom g = tile_geom(L, t);
+  const int e = threadIdx.x / LB, p = threadIdx.x % LB;
+  int r, c;
+  if (e < 2) {
+    if (p >= g.w) return;
+    r = (e == 0) ? 0 : g.h - 1;
+    c = p;
+  } else {
+    if (p >= g.h) return;
+    r = p;
+    c = (e == 2) ? 0 : g.w - 1;
+  }
+  unsigned long long* pub = to_pub2 ? L.pub2 : L.pub;
+  pub[((size_t)t * 4 + e) * LB + p] = L.key[(size_t)(g.r0 + r) * L.cols + g.c0 + c];
+}
+
+// (a) Round kernel: R tile rounds per launch against frozen halos (edge words of
+// the previous launch); R = 1 is one global synchronous round of Fig. 3.2.
+template <int LB>
+__global__ void __launch_bounds__(4 * LB) round_kernel(const LatDesc* __restrict__ lats, int nlat,
+                                                       int R, int parity, int launch_idx,
+                                                       DevCounters* ctr, unsigned long long* hist,
+                                                       int hist_len, int round_idx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Smem<LB> sm(smem_raw);
+  if (launch_idx > 0) {
+    if (*(volatile unsigned*)&ctr->active[(launch_idx + 2) % 3] == 0u) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctr->active[(launch_idx + 1) % 3] = 0u;
+    atomicAdd(&ctr->launched, 1u);
+  }
+
+  const int tile = blockIdx.x;
+  const LatDesc& L = lats[find_lattice(lats, nlat, tile)];
+  const int t = tile - L.tile_base;
+  const Geom g = tile_geom(L, t);
+  const unsigned long long* pub_in = parity ? L.pub2 : L.pub;
+  unsigned long long* pub_out = (parity ? L.pub : L.pub2) + (size_t)t * 4 * LB;
+  const unsigned long long t2 = L.t2;
+  const bool direct = (R == 1);
+
+  if (direct) load_interior<LB, false>(sm, L, g);
+  else load_interior<LB, true>(sm, L, g);
+  if (threadIdx.x < 10) sm.thr[threadIdx.x] = L.thr[threadIdx.x];
+  if (threadIdx.x == 0) { sm.n_en[0] = 0u; sm.n_en[1] = 0u; }
+  const HaloSlot hs = halo_slot<LB>(L, g, pub_in);
+  __syncthreads();
+  fill_halo<LB, false>(sm, hs);
+  __syncthreads();
+
+  unsigned long long scanned = 0, events = 0, rounds = 0, enabled = 0;
+  int cur = 0;
+  for (int rr = 0; rr < R; ++rr) {
+    const bool live = scan_tile<LB>(sm, g, t2, &sm.n_en[cur], scanned);
+    const int any_live = __syncthreads_or(live);
+    const int n = (int)sm.n_en[cur];
+    if (rr == 0 && threadIdx.x == 0 && hist != nullptr && round_idx < hist_len && n > 0)
+      atomicAdd(&hist[round_idx], (unsigned long long)n);
+    if (n == 0 || !any_live) break;
+    if (direct) commit_tile<LB, true, false>(sm, L, g, nullptr, n);
+    else commit_tile<LB, false, false>(sm, L, g, nullptr, n);
+    if (threadIdx.x == 0) sm.n_en[cur ^ 1] = 0u;
+    events += (unsigned long long)n;
+    enabled += (unsigned long long)n;
+    ++rounds;
+    __syncthreads();
+    cur ^= 1;
+  }
+  bool unfinished;
+  if (direct) {
+    unfinished = false;
+    const int c = threadIdx.x % LB;
+    if (c < g.w)
+      for (int r = threadIdx.x / LB; r < g.h; r += 4)
+        unfinished |= sm.K[(r + 1) * TileShape<LB>::P + c + 1] < t2;
+  } else {
+    unfinished = store_interior<LB, true>(sm, L, g);
+  }
+  write_edges<LB>(sm, g, pub_out);
+  const int any_unfinished = __syncthreads_or(unfinished);
+  // reduce the scanned counter over the block (only thread-local so far)
+  for (int o = 16; o > 0; o >>= 1) scanned += __shfl_down_sync(kFull, scanned, o);
+  if ((threadIdx.x & 31) == 0 && scanned) atomicAdd(&ctr->scanned, scanned);
+  if (threadIdx.x == 0) {
+    if (any_unfinished) atomicAdd(&ctr->active[launch_idx % 3], 1u);
+    if (events) {
+      atomicAdd(&ctr->events, events);
+      atomicAdd(L.events, events);
+    }
+    if (enabled) atomicAdd(&ctr->enabled, enabled);
+    if (rounds) atomicAdd(&ctr->rounds, rounds);
+  }
+}
+
+// (b) Blocked persistent kernel (cooperative launch: all CTAs co-resident).
+template <int LB>
+__global__ void __launch_bounds__(4 * LB) blocked_kernel(const LatDesc* __restrict__ lats, int nlat,
+                                                         int total_tiles, int polls, int refresh,
+                                                         int max_rounds, long long watchdog_ns,
+                                                         unsigned int* tile_done, DevCounters* ctr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Smem<LB> sm(smem_raw);
+  unsigned long long scanned = 0, events = 0, rounds = 0, visits = 0, npolls = 0;
+  unsigned long long last_progress = global_ns();
+  bool failed = false;
+
+  for (;;) {
+    bool any_left = false, progressed = false;
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+      if (*(volatile unsigned*)&tile_done[tile]) continue;
+      any_left = true;
+      const LatDesc& L = lats[find_lattice(lats, nlat, tile)];
+      const int t = tile - L.tile_base;
+      const Geom g = tile_geom(L, t);
+      const unsigned long long t2 = L.t2;
+      unsigned long long* pub_tile = L.pub + (size_t)t * 4 * LB;
+
+      load_interior<LB, true>(sm, L, g);
+      if (threadIdx.x < 10) sm.thr[threadIdx.x] = L.thr[threadIdx.x];
+      if (threadIdx.x == 0) { sm.n_en[0] = 0u; sm.n_en[1] = 0u; }
+      const HaloSlot hs = halo_slot<LB>(L, g, L.pub);
+      __syncthreads();
+      fill_halo<LB, true>(sm, hs);
+      __syncthreads();
+      ++visits;
+
+      int cur = 0, stuck = 0, vrounds = 0;
+      bool done = false;
+      unsigned long long vevents = 0;
+      for (;;) {
+        const bool live = scan_tile<LB>(sm, g, t2, &sm.n_en[cur], scanned);
+        const int any_live = __syncthreads_or(live);
+        const int n = (int)sm.n_en[cur];
+        if (n == 0) {
+          if (!any_live) { done = true; break; }
+          if (stuck >= polls) break;
+          ++stuck;
+          ++npolls;
+          __nanosleep(256u << min(stuck, 4));
+          if (hs.src) fill_halo<LB, true>(sm, hs);
+          __syncthreads();
+          continue;
+        }
+        stuck = 0;
+        const bool do_refresh = (refresh > 0) && ((vrounds + 1) % refresh == 0) && hs.src;
+        unsigned long long fresh = 0;
+        if (do_refresh) fresh = ld_relaxed(hs.src);        // latency hidden by the commit phase
+        commit_tile<LB, false, true>(sm, L, g, pub_tile, n);
+        if (threadIdx.x == 0) sm.n_en[cur ^ 1] = 0u;
+        vevents += (unsigned long long)n;
+        ++vrounds;
+        __syncthreads();
+        cur ^= 1;
+        if (refresh > 0 && (vrounds % refresh) == 0) {
+          if (do_refresh) sm.K[hs.slot] = fresh + (unsigned long long)hs.adj;
+          __syncthreads();
+        }
+        if (max_rounds > 0 && vrounds >= max_rounds) break;
+      }
+      store_interior<LB, true>(sm, L, g);
+      if (threadIdx.x == 0) {
+        if (done) tile_done[tile] = 1u;
+        if (vevents) atomicAdd(L.events, vevents);
+      }
+      events += vevents;
+      rounds += (unsigned long long)vrounds;
+      if (vevents) progressed = true;
+      // one barrier both ends the visit and makes the error decision uniform
+      if (__syncthreads_or(threadIdx.x == 0 && *(volatile int*)&ctr->error != 0)) {
+        failed = true;
+        break;
+      }
+    }
+    if (failed || !any_left) break;
+    int stall = 0;
+    if (threadIdx.x == 0) {
+      const unsigned long long now = global_ns();
+      if (progressed) {
+        last_progress = now;
+      } else if ((long long)(now - last_progress) > watchdog_ns) {
+        if (atomicCAS(&ctr->error, 0, 4 /* AC_ERR_STALL */) == 0) ctr->err_block = (int)blockIdx.x;
+        stall = 1;
+      }
+    }
+    if (__syncthreads_or(stall)) break;
+  }
+  for (int o = 16; o > 0; o >>= 1) scanned += __shfl_down_sync(kFull, scanned, o);
+  if ((threadIdx.x & 31) == 0 && scanned) atomicAdd(&ctr->scanned, scanned);
+  if (threadIdx.x == 0) {
+    atomicAdd(&ctr->events, events);
+    atomicAdd(&ctr->enabled, events);
+    atomicAdd(&ctr->rounds, rounds);
+    atomicAdd(&ctr->visits, visits);
+    atomicAdd(&ctr->polls, npolls);
+  }
+}
+
+// ---- observables, packing, device-primitive probes ---------------------------
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// out[0] = sum of spins, out[1] = sum over right and down bonds of s s',
+// out[2] = state fingerprint sum_c mix(mix(mix(c) ^ t) ^ (2n + up)), out[3] = sum of counts.
+__global__ void reduce_kernel(LatDesc L, unsigned long long* out) {
+  const size_t N = (size_t)L.rows * L.cols;
+  long long ms = 0, bonds = 0;
+  unsigned long long fp = 0, ev = 0;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = c / L.cols, q = c - r * L.cols;
+    const unsigned long long k = L.key[c];
+    const int s = (k & 1ull) ? 1 : -1;
+    const int sr = (L.key[r * L.cols + (q + 1 == (size_t)L.cols ? 0 : q + 1)] & 1ull) ? 1 : -1;
+    const int sd = (L.key[(r + 1 == (size_t)L.rows ? 0 : r + 1) * L.cols + q] & 1ull) ? 1 : -1;
+    const unsigned n = L.cnt[c];
+    ms += s;
+    bonds += s * sr + s * sd;
+    unsigned long long z = mix64((unsigned long long)c);
+    z = mix64(z ^ (k >> 1));
+    z = mix64(z ^ (((unsigned long long)n << 1) | (k & 1ull)));
+    fp += z;
+    ev += n;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ms += __shfl_down_sync(kFull, ms, o);
+    bonds += __shfl_down_sync(kFull, bonds, o);
+    fp += __shfl_down_sync(kFull, fp, o);
+    ev += __shfl_down_sync(kFull, ev, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], (unsigned long long)ms);
+    atomicAdd(&out[1], (unsigned long long)bonds);
+    atomicAdd(&out[2], fp);
+    atomicAdd(&out[3], ev);
+  }
+}
+
+__global__ void unpack_kernel(LatDesc L, int8_t* s, long long* t, unsigned* n) {
+  const size_t N = (size_t)L.rows * L.cols;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = L.key[c];
+    if (s) s[c] = (k & 1ull) ? (int8_t)1 : (int8_t)-1;
+    if (t) t[c] = (long long)(k >> 1);
+    if (n) n[c] = L.cnt[c];
+  }
+}
+
+__global__ void pack_kernel(LatDesc L, const int8_t* s, const long long* t, const unsigned* n) {
+  const size_t N = (size_t)L.rows * L.cols;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+       c += (size_t)gridDim.x * blockDim.x) {
+    L.key[c] = ((unsigned long long)t[c] << 1) | (s[c] > 0 ? 1ull : 0ull);
+    L.cnt[c] = n[c];
+  }
+}
+
+__global__ void exp_ticks_kernel(const uint32_t* x, unsigned long long* out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = exp_ticks(x[i]);
+}
+
+__global__ void philox_kernel(unsigned long long seed, const uint32_t* c, const uint32_t* k,
+                              uint32_t w2, uint32_t* out4, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const Philox4 b = philox_event(c[i], k[i], w2, (uint32_t)seed, (uint32_t)(seed >> 32));
+    out4[4 * i + 0] = b.x;
+    out4[4 * i + 1] = b.y;
+    out4[4 * i + 2] = b.z;
+    out4[4 * i + 3] = b.w;
+  }
+}
+
+int grid_for(size_t n, int block) {
+  size_t g = (n + block - 1) / block;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <int LB>
+cudaError_t set_smem_attrs() {
+  static bool done = false;   // per process; attributes are per-function
+  if (done) return cudaSuccess;
+  const int bytes = (int)TileShape<LB>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(round_kernel<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(blocked_kernel<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  done = true;
+  return cudaSuccess;
+}
+
+template <int LB>
+cudaError_t round_launch(const LatDesc* d, int nlat, int total, const LaunchCfg& cfg, int parity,
+                         int launch_idx, DevCounters* ctr, unsigned long long* hist, int hist_len,
+                         int round_idx, cudaStream_t s) {
+  cudaError_t e = set_smem_attrs<LB>();
+  if (e != cudaSuccess) return e;
+  round_kernel<LB><<<total, 4 * LB, TileShape<LB>::bytes, s>>>(d, nlat, cfg.rounds, parity, launch_idx,
+                                                               ctr, hist, hist_len, round_idx);
+  return cudaGetLastError();
+}
+
+template <int LB>
+int blocked_resident(int* per_sm) {
+  if (set_smem_attrs<LB>() != cudaSuccess) return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blocked_kernel<LB>, 4 * LB,
+                                                    TileShape<LB>::bytes) != cudaSuccess)
+    return 0;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (per_sm) *per_sm = nb;
+  return nb * sms;
+}
+
+template <int LB>
+cudaError_t blocked_launch(const LatDesc* d, int nlat, int total, const LaunchCfg& cfg, int grid,
+                           unsigned* tile_done, DevCounters* ctr, cudaStream_t s) {
+  cudaError_t e = set_smem_attrs<LB>();
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)grid);
+  lc.blockDim = dim3(4 * LB);
+  lc.dynamicSmemBytes = TileShape<LB>::bytes;
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, blocked_kernel<LB>, d, nlat, total, cfg.polls, cfg.refresh,
+                            cfg.max_rounds, cfg.watchdog_ns, tile_done, ctr);
+}
+
+}  // namespace
+
+size_t tile_smem_bytes(int lb) {
+  switch (lb) {
+    case 32: return TileShape<32>::bytes;
+    case 64: return TileShape<64>::bytes;
+    case 128: return TileShape<128>::bytes;
+    default: return 0;
+  }
+}
+
+int blocked_max_ctas(int lb, int* per_sm) {
+  switch (lb) {
+    case 32: return blocked_resident<32>(per_sm);
+    case 64: return blocked_resident<64>(per_sm);
+    case 128: return blocked_resident<128>(per_sm);
+    default: return 0;
+  }
+}
+
+cudaError_t launch_init(const LatDesc* h, int init_mode, cudaStream_t s) {
+  const size_t N = (size_t)h->rows * h->cols;
+  init_kernel<<<grid_for(N, 256), 256, 0, s>>>(*h, init_mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_publish(const LatDesc* d, int nlat, int total, int lb, int to_pub2, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  switch (lb) {
+    case 32: publish_kernel<32><<<total, 128, 0, s>>>(d, nlat, to_pub2); break;
+    case 64: publish_kernel<64><<<total, 256, 0, s>>>(d, nlat, to_pub2); break;
+    case 128: publish_kernel<128><<<total, 512, 0, s>>>(d, nlat, to_pub2); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round(const LatDesc* d, int nlat, int total, const LaunchCfg& cfg, int parity,
+                         int launch_idx, DevCounters* ctr, unsigned long long* hist, int hist_len,
+                         int round_idx, cudaStream_t s) {
+  switch (cfg.lb) {
+    case 32: return round_launch<32>(d, nlat, total, cfg, parity, launch_idx, ctr, hist, hist_len, round_idx, s);
+    case 64: return round_launch<64>(d, nlat, total, cfg, parity, launch_idx, ctr, hist, hist_len, round_idx, s);
+    case 128: return round_launch<128>(d, nlat, total, cfg, parity, launch_idx, ctr, hist, hist_len, round_idx, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_blocked(const LatDesc* d, int nlat, int total, const LaunchCfg& cfg, int grid,
+                           unsigned* tile_done, DevCounters* ctr, cudaStream_t s) {
+  switch (cfg.lb) {
+    case 32: return blocked_launch<32>(d, nlat, total, cfg, grid, tile_done, ctr, s);
+    case 64: return blocked_launch<64>(d, nlat, total, cfg, grid, tile_done, ctr, s);
+    case 128: return blocked_launch<128>(d, nlat, total, cfg, grid, tile_done, ctr, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_reduce(const LatDesc* h, unsigned long long* d_out4, cudaStream_t s) {
+  const size_t N = (size_t)h->rows * h->cols;
+  reduce_kernel<<<grid_for(N, 256), 256, 0, s>>>(*h, d_out4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const LatDesc* h, int8_t* so, long long* to, unsigned* no, cudaStream_t st) {
+  const size_t N = (size_t)h->rows * h->cols;
+  unpack_kernel<<<grid_for(N, 256), 256, 0, st>>>(*h, so, to, no);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const LatDesc* h, const int8_t* si, const long long* ti, const unsigned* ni,
+                        cudaStream_t st) {
+  const size_t N = (size_t)h->rows * h->cols;
+  pack_kernel<<<grid_for(N, 256), 256, 0, st>>>(*h, si, ti, ni);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exp_ticks(const uint32_t* x, unsigned long long* out, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  exp_ticks_kernel<<<grid_for((size_t)n, 256), 256, 0, s>>>(x, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(unsigned long long seed, const uint32_t* c, const uint32_t* k, uint32_t w2,
+                          uint32_t* out4, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  philox_kernel<<<grid_for((size_t)n, 256), 256, 0, s>>>(seed, c, k, w2, out4, n);
+  return cudaGetLastError();
+}
+
+}  // namespace ac

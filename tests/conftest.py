@@ -9,3 +9,9 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU check")
+
+
+def pytest_sessionstart(session):
+    # build libac.so (and the oracle) before any test module imports the package
+    import __graft_entry__
+    __graft_entry__.build()

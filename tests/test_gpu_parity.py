@@ -1,0 +1,144 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, bit-exact.
+
+The trajectory of the Poisson-asynchronous Glauber array is unique given the
+per-cell random streams and the (tick, index) order (Sec. 3, uniqueness of the
+one-cell-per-PE trajectory; invariance of the aggregated algorithm under
+re-partitioning), so spins, next-arrival ticks and per-cell counts must agree
+exactly -- tolerance 0 -- for every kernel, tile side and tuning.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests.gpu_util import T32, assert_same, lib_state, oracle_state
+
+pytestmark = pytest.mark.gpu
+
+ac = pytest.importorskip("paper_cs_0502039_gb300")
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+ROUND, BLOCKED = ac.AC_KERNEL_ROUND, ac.AC_KERNEL_BLOCKED
+
+# (rows, cols, beta, J, h, seed, T, init): degenerate tori, ragged tiles, several tiles
+CASES = [
+    (2, 2, 0.44, 1.0, 0.0, 1, 8, 0),
+    (2, 3, 0.7, 1.0, 0.2, 2, 8, 0),
+    (3, 2, 0.3, 1.0, -0.1, 3, 8, 1),
+    (5, 7, 1.0, 1.0, 0.05, 4, 6, 0),
+    (33, 65, 0.44, 1.0, 0.0, 5, 4, 0),
+    (64, 64, 0.44, 1.0, 0.0, 1, 10, 0),        # 64x64, beta 0.44, seed 1, T = 10
+    (100, 130, 0.6, 1.0, 0.1, 6, 3, 2),
+    (130, 66, 0.2, 0.8, -0.3, 7, 3, 0),
+    (2, 200, 0.5, 1.0, 0.0, 8, 4, 0),
+    (257, 3, 0.5, 1.0, 0.0, 9, 4, 0),
+]
+
+CONFIGS = [
+    (ROUND, 32, 1, 0), (ROUND, 64, 1, 0), (ROUND, 32, 5, 0), (ROUND, 128, 3, 0),
+    (BLOCKED, 32, 1, 8), (BLOCKED, 64, 1, 8), (BLOCKED, 128, 1, 8), (BLOCKED, 32, 4, 0),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}")
+def test_all_kernels_match_oracle(case):
+    rows, cols, beta, J, h, seed, T, init = case
+    ref = oracle_state(rows, cols, beta, J, h, seed, T, init)
+    for kernel, Lb, rounds, polls in CONFIGS:
+        s, t, n, stats = lib_state(rows, cols, beta, J, h, seed, T, init, kernel, Lb, rounds, polls)
+        assert_same(ref, s, t, n, f"kernel={kernel} Lb={Lb} rounds={rounds} polls={polls}")
+        assert stats["events"] == int(ref.n.astype(np.int64).sum())
+
+
+def test_round_history_equals_time_only_model():
+    """Round kernel with one round per launch = Fig. 3.2: per-round enabled counts
+    equal those of the oracle's time-only round model (Sec. 4) exactly."""
+    rows, cols, seed, T = 64, 64, 1, 10
+    st = oracle.init(rows, cols, 0, seed)
+    en = oracle.time_rounds(st, seed, T * T32)
+    with ac.Sim(rows, cols, 0.44, 1.0, 0.0, seed, kernel=ROUND, Lb=32, rounds=1) as sim:
+        sim.run_until(T)
+        hist = sim.round_history()
+        stats = sim.stats()
+    assert np.array_equal(hist.astype(np.int64), en)
+    assert stats["global_rounds"] == len(en)
+    assert abs(stats["enabled_frac_mean"] - en.mean() / (rows * cols)) < 1e-12
+
+
+def test_stats_observables_and_checksum():
+    rows, cols, beta, seed, T = 96, 80, 0.5, 11, 5
+    ref = oracle_state(rows, cols, beta, 1.0, 0.2, seed, T)
+    s, t, n, stats = lib_state(rows, cols, beta, 1.0, 0.2, seed, T)
+    m, b = oracle.observables(ref)
+    assert stats["sum_s"] == m and stats["sum_bonds"] == b
+    assert stats["checksum"] == oracle.checksum(ref)
+    assert stats["total_counts"] == int(ref.n.astype(np.int64).sum())
+
+
+@pytest.mark.parametrize("kernel", [ROUND, BLOCKED])
+def test_run_splitting_and_checkpoint_resume(kernel):
+    rows, cols, beta, seed = 70, 90, 0.44, 13
+    ref = oracle_state(rows, cols, beta, 1.0, 0.0, seed, 6)
+    with ac.Sim(rows, cols, beta, 1.0, 0.0, seed, kernel=kernel, Lb=32) as a:
+        a.run_until_ticks(2 * T32 + 777)
+        a.run_until(4)
+        s, t, n = a.read_state()
+    with ac.Sim(rows, cols, beta, 1.0, 0.0, 999, kernel=kernel, Lb=64) as b:
+        b.load_state(s, t, n, 4 * T32)
+        # the seed is part of the state's identity: restore it with reset + load
+        b.reset(seed)
+        b.load_state(s, t, n, 4 * T32)
+        b.run_until(6)
+        s2, t2, n2 = b.read_state()
+    assert_same(ref, s2, t2, n2, "checkpoint/resume")
+
+
+def test_reset_reproduces_create():
+    with ac.Sim(40, 40, 0.44, 1.0, 0.0, 5) as a:
+        a.run_until(3)
+        a.reset(21, ac.AC_INIT_UP)
+        a.run_until(2)
+        s, t, n = a.read_state()
+    ref = oracle_state(40, 40, 0.44, 1.0, 0.0, 21, 2, init=1)
+    assert_same(ref, s, t, n, "reset")
+
+
+def test_read_state_device_matches_host():
+    with ac.Sim(50, 60, 0.44, 1.0, 0.0, 3) as sim:
+        sim.run_until(2)
+        s, t, n = sim.read_state()
+        ds = torch.empty(3000, dtype=torch.int8, device="cuda")
+        dt = torch.empty(3000, dtype=torch.int64, device="cuda")
+        dn = torch.empty(3000, dtype=torch.int32, device="cuda")
+        ac.ac_read_state_device(sim.handle, ds.data_ptr(), dt.data_ptr(), dn.data_ptr())
+        assert np.array_equal(ds.cpu().numpy(), s)
+        assert np.array_equal(dt.cpu().numpy(), t)
+        assert np.array_equal(dn.cpu().numpy().view(np.uint32), n)
+
+
+def test_watchdog_reports_stall_without_fault():
+    """With edge publication suppressed a multi-tile lattice cannot finish: the
+    bounded polls and the watchdog must end the run with AC_ERR_STALL, and the
+    device must stay usable."""
+    with ac.Sim(256, 256, 0.44, 1.0, 0.0, 1, kernel=BLOCKED, Lb=32, polls=2) as sim:
+        sim.set_option(ac.AC_OPT_WATCHDOG_NS, 50_000_000)
+        sim.set_option(ac.AC_OPT_DROP_PUBLISH, 1)
+        with pytest.raises(ac.ACError) as ei:
+            sim.run_until(20)
+        assert ei.value.status == ac.ac.AC_ERR_STALL
+    ref = oracle_state(64, 64, 0.44, 1.0, 0.0, 1, 2)
+    s, t, n, _ = lib_state(64, 64, 0.44, 1.0, 0.0, 1, 2, kernel=BLOCKED, Lb=32)
+    assert_same(ref, s, t, n, "after a stall")
+
+
+def test_invalid_arguments_are_rejected():
+    with ac.Sim(16, 16, 0.44, 1.0, 0.0, 1) as sim:
+        sim.run_until(2)
+        with pytest.raises(ac.ACError):
+            sim.run_until(1)                     # t_end decreasing
+        with pytest.raises(ac.ACError):
+            sim.configure(BLOCKED, 48)           # unsupported tile side
+        bad_t = np.zeros(256, dtype=np.int64)
+        with pytest.raises(ac.ACError):
+            sim.load_state(np.ones(256, np.int8), bad_t, np.zeros(256, np.uint32), 0)
