@@ -203,6 +203,35 @@ ac_status ac_batch_create(int32_t n, const ac_lattice* lats, const double* beta,
                           const double* h, const uint64_t* seed, ac_sim** out);
 ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_end);
 
+/*
+ * Run without allocating.  The paper has no counterpart to this entry point; it
+ * exists for callers that cannot let the library call cudaMalloc: code that
+ * runs while a CUDA graph is being captured, applications whose allocator owns
+ * all device memory, or hosts that give the library a fixed device budget.
+ *
+ * Advances the lattice stored in the caller's DEVICE buffers to t_end with the
+ * blocked persistent kernel (tile side 64), bit-identical to ac_run_until_ticks
+ * on a handle with the same state and parameters.
+ *   key_dev  rows*cols uint64, row-major: tick << 1 | (spin > 0); read and written
+ *   cnt_dev  rows*cols uint32: committed arrivals per cell; read and written
+ *   stream   cudaStream_t for the work (NULL: legacy default stream)
+ * All other buffers the kernel needs (lattice descriptor, counters, tile flags,
+ * edge words) live in one file-scope device array of AC_STATIC_SCRATCH_BYTES,
+ * which every GPU that loads the library holds until the process exits.  The
+ * call allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every call
+ * shares the array and clears what must start at zero, so calls whose GPU work
+ * overlaps (other streams, other threads) race and must not be issued.  The call
+ * is synchronous.  Errors: AC_ERR_ARG (bad arguments, or a lattice needing more
+ * scratch than the maximum: about 2000 tiles of 64 x 64, e.g. 2816 x 2816),
+ * AC_ERR_STALL, AC_ERR_CUDA.
+ */
+#define AC_STATIC_SCRATCH_BYTES (4u << 20)
+ac_status ac_run_blocked_static(int32_t rows, int32_t cols, double beta, double J, double h,
+                                uint64_t seed, uint64_t* key_dev, uint32_t* cnt_dev, int64_t t_end,
+                                void* stream);
+
 /* Device-primitive probes (DEVICE pointers, n elements), for verification:
  * out[i] = gap of x[i];  out4[4i..4i+3] = Philox({c[i], k[i], w2, 0}) under seed. */
 ac_status ac_dev_exp_ticks(const uint32_t* x_dev, uint64_t* out_dev, int64_t n);

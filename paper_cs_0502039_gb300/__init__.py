@@ -9,5 +9,5 @@ its thin ctypes binding.
 from .ac import (AC_OPT_DROP_PUBLISH, AC_OPT_MAX_ROUNDS, AC_OPT_WATCHDOG_NS, AC_INIT_DOWN, AC_INIT_RANDOM, AC_INIT_UP, AC_KERNEL_BLOCKED, AC_KERNEL_ROUND,  # noqa: F401
                  TICKS_PER_UNIT, ACError, Sim, ac_batch_create, ac_batch_run_until, ac_configure,
                  ac_create, ac_destroy, ac_dev_exp_ticks, ac_dev_philox, ac_load_state, ac_read_state,
-                 ac_read_state_device, ac_reset, ac_round_history, ac_set_option, ac_run_until, ac_run_until_ticks, ac_set_stream,
+                 ac_read_state_device, ac_reset, ac_round_history, ac_run_blocked_static, ac_set_option, ac_run_until, ac_run_until_ticks, ac_set_stream,
                  ac_stats, ac_thresholds)

@@ -53,7 +53,7 @@ class ac_stats_t(ctypes.Structure):
 EXPORTS = ["ac_create", "ac_set_stream", "ac_configure", "ac_run_until", "ac_run_until_ticks",
            "ac_read_state", "ac_read_state_device", "ac_load_state", "ac_stats", "ac_round_history",
            "ac_destroy", "ac_last_error", "ac_thresholds", "ac_reset", "ac_set_option", "ac_batch_create", "ac_batch_run_until",
-           "ac_dev_exp_ticks", "ac_dev_philox"]
+           "ac_dev_exp_ticks", "ac_dev_philox", "ac_run_blocked_static"]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ac_batch_run_until": ([I32, P, P], I32),
         "ac_dev_exp_ticks": ([P, P, I64], I32),
         "ac_dev_philox": ([U64, P, P, ctypes.c_uint32, P, I64], I32),
+        "ac_run_blocked_static": ([I32, I32, D, D, D, U64, P, P, I64, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -201,6 +202,13 @@ def ac_dev_exp_ticks(x_ptr: int, out_ptr: int, n: int) -> None:
 
 def ac_dev_philox(seed: int, c_ptr: int, k_ptr: int, w2: int, out_ptr: int, n: int) -> None:
     _check(_lib.ac_dev_philox(seed & (2**64 - 1), c_ptr, k_ptr, w2, out_ptr, n))
+
+
+def ac_run_blocked_static(rows: int, cols: int, beta: float, J: float, h: float, seed: int,
+                          key_ptr: int, cnt_ptr: int, t_end: int, stream: int = 0) -> None:
+    """Advance a lattice held in caller-owned device buffers without any allocation."""
+    _check(_lib.ac_run_blocked_static(rows, cols, beta, J, h, seed & (2**64 - 1), key_ptr, cnt_ptr,
+                                      int(t_end), stream))
 
 
 # --------------------------------------------------------------- convenience

@@ -65,6 +65,11 @@ int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 }  // namespace
 
+namespace ac {
+// Lets other translation units of the library report through ac_last_error().
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace ac
+
 struct ac_sim {
   int rows = 0, cols = 0, init = 0;
   double beta = 0, J = 0, h = 0;

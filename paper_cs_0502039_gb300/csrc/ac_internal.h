@@ -61,6 +61,9 @@ struct LaunchCfg {
   long long watchdog_ns;  // blocked kernel: no-progress limit before AC_ERR_STALL
 };
 
+// Sets the thread-local message returned by ac_last_error() (ac_api.cu).
+void set_last_error(const char* msg);
+
 // ---- launchers (ac_kernels.cu) -------------------------------------------------
 size_t tile_smem_bytes(int lb);
 int blocked_max_ctas(int lb, int* per_sm);   // resident CTAs of the blocked kernel
