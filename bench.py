@@ -39,13 +39,20 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--kernel", default="blocked", choices=["blocked", "round"])
+    ap.add_argument("--kernel", default="round", choices=["blocked", "round"])
     ap.add_argument("--lb", type=int, default=64)
-    ap.add_argument("--rounds", type=int, default=1, help="round kernel: rounds per launch; blocked: refresh")
+    ap.add_argument("--rounds", type=int, default=8,
+                    help="round kernel: synchronous rounds per launch (>1: temporal blocking); blocked: refresh")
     ap.add_argument("--polls", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the per-kernel side measurements")
+    ap.add_argument("--single", action="store_true",
+                    help="one lattice, one kernel configuration (the profiling case); prints one JSON line")
+    ap.add_argument("--rows", type=int, default=4096)
+    ap.add_argument("--cols", type=int, default=4096)
+    ap.add_argument("--beta", type=float, default=0.4407)
+    ap.add_argument("--T", type=float, default=5.0)
     return ap.parse_args()
 
 
@@ -120,18 +127,18 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def committed_traffic(kernel_name, lb):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel source."""
+def committed_traffic(kernel_name):
+    """DRAM bytes per step from the committed ncu summary, if it matches this kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    ent = rec.get(f"{kernel_name}_lb{lb}")
+    ent = rec.get(kernel_name)
     if not ent or ent.get("source_sha256") != kernel_source_hash():
         return None
-    return ent.get("dram_bytes_per_launch_full")
+    return ent.get("dram_bytes_per_step")
 
 
 def measured_peaks():
@@ -189,10 +196,44 @@ def run_reference(args):
     return 0
 
 
+def run_single(args):
+    """One lattice (seed 7, random init, J = 1, h = 0) run to T with one kernel configuration:
+    `warmup` untimed runs, then `steps` timed runs; reports the kernel's device time."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_cs_0502039_gb300 as ac
+    kern = ac.AC_KERNEL_BLOCKED if args.kernel == "blocked" else ac.AC_KERNEL_ROUND
+    with ac.Sim(args.rows, args.cols, args.beta, 1.0, 0.0, 7, kernel=kern, Lb=args.lb, rounds=args.rounds,
+                polls=args.polls) as sim:
+        for _ in range(args.warmup):
+            sim.reset(7)
+            sim.run_until(args.T)
+        res = []
+        for _ in range(args.steps):
+            sim.reset(7)
+            sim.run_until(args.T)
+            res.append(sim.stats())
+    ms = statistics.median(r["device_ms"] for r in res)
+    ev = res[-1]["events"]
+    print(json.dumps({"case": f"{args.rows}x{args.cols} beta={args.beta} T={args.T}", "kernel": args.kernel,
+                      "Lb": args.lb, "rounds": args.rounds, "polls": args.polls, "events": ev,
+                      "device_ms": ms, "events_per_s": ev / (ms / 1000.0),
+                      "hbm_frac_effective": BYTES_PER_EVENT * ev / (ms / 1000.0) / 1e9 / measured_peaks()[0],
+                      "launches": res[-1]["launches"], "visits": res[-1]["visits"], "polls_done": res[-1]["polls"],
+                      "tile_rounds": res[-1]["rounds"], "scanned": res[-1]["scanned"],
+                      "enabled_frac": res[-1]["enabled_frac_mean"], "checksum": res[-1]["checksum"]}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.single:
+        return run_single(args)
 
     import numpy as np
     import torch
@@ -251,8 +292,10 @@ def main():
             kern_ms_list.append(st[0]["device_ms"])          # one batched launch (same on every handle)
         else:
             kern_ms_list.append(sum(x["device_ms"] for x in st))
+    # init per lattice, then: blocked = publish + one kernel; round = (count-range check +)
+    # the round launches of each lattice
     launches_per_step = (len(sims) + 2 if kern == ac.AC_KERNEL_BLOCKED
-                         else sum(2 + x["launches"] for x in st))
+                         else sum(1 + (1 if args.rounds > 1 else 1) + x["launches"] for x in st))
 
     sync_all()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -282,10 +325,15 @@ def main():
     peak, peak_src = measured_peaks()
     kern_launch_ms = kern_ms / args.steps if kern == ac.AC_KERNEL_BLOCKED else kern_ms / args.steps
     achieved = BYTES_PER_EVENT * ev_per_step_rank / (kern_launch_ms / 1000.0) / 1e9
-    kname = "blocked_kernel" if kern == ac.AC_KERNEL_BLOCKED else "round_kernel"
+    if kern == ac.AC_KERNEL_BLOCKED:
+        kname = f"blocked_kernel<{args.lb}>"
+    elif args.rounds > 1:
+        kname = f"tb_kernel<{96 if args.rounds <= 12 else 128}>"
+    else:
+        kname = f"round_kernel<{args.lb}>"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": committed_traffic(kname, args.lb), "peak_source": peak_src,
-                "kernel": f"{kname}<{args.lb}>", "bytes_per_event": BYTES_PER_EVENT,
+                "traffic": committed_traffic(kname), "peak_source": peak_src,
+                "kernel": kname, "bytes_per_event": BYTES_PER_EVENT,
                 "events_per_launch": ev_per_step_rank, "launch_ms": kern_launch_ms}
 
     # end-to-end through the public API with host buffers (pinned), copies inside the timed region

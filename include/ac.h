@@ -89,9 +89,13 @@ ac_status ac_set_stream(ac_sim* sim, void* cuda_stream);
  * Choose the kernel and its tuning for later run calls.
  *   kernel  AC_KERNEL_ROUND or AC_KERNEL_BLOCKED
  *   Lb      tile side: 32, 64 or 128 (threads per CTA = 4 * Lb)
- *   rounds  round kernel: tile rounds per launch (1 = exact synchronous rounds of
- *           Fig. 3.2 with per-round enabled counts); blocked kernel: halo refresh
- *           period in rounds (>= 1)
+ *   rounds  round kernel: synchronous rounds per launch.  1 = one global round of
+ *           Fig. 3.2 per launch, with per-round enabled counts (ac_round_history).
+ *           2..16 = temporal blocking: each CTA loads its tile with a halo of depth
+ *           `rounds` into a 128 x 128 shared-memory region and runs `rounds` exact
+ *           synchronous rounds per launch (tile side 128 - 2*rounds, Lb unused;
+ *           needs rows, cols >= 4*rounds, otherwise Lb-tiles with frozen halos).
+ *           Blocked kernel: halo refresh period in rounds (>= 1).
  *   polls   blocked kernel: halo polls before a blocked tile is left (>= 0)
  * The trajectory does not depend on any of these (Sec. 3, invariance of the
  * aggregated algorithm under re-partitioning); only the speed does.

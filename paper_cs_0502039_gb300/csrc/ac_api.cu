@@ -81,6 +81,8 @@ struct ac_sim {
 
   unsigned long long* key = nullptr;
   unsigned int* cnt = nullptr;
+  unsigned long long* key2 = nullptr;       // second state buffer (temporal-blocked rounds)
+  unsigned int* cnt2 = nullptr;
   unsigned long long* pub = nullptr;
   unsigned long long* pub2 = nullptr;
   size_t pub_words = 0;
@@ -109,6 +111,9 @@ struct ac_sim {
     ac::LatDesc d{};
     d.key = key;
     d.cnt = cnt;
+    d.key2 = key2;
+    d.cnt2 = cnt2;
+    d.two = 2u;
     d.pub = pub;
     d.pub2 = pub2;
     d.events = d_events;
@@ -203,6 +208,8 @@ void free_sim(ac_sim* s) {
   if (!s) return;
   cudaFree(s->key);
   cudaFree(s->cnt);
+  cudaFree(s->key2);
+  cudaFree(s->cnt2);
   cudaFree(s->pub);
   cudaFree(s->pub2);
   cudaFree(s->d_events);
@@ -292,11 +299,121 @@ ac_status accumulate(ac_sim* s, const ac::DevCounters& c, float ms, bool round_k
   } else {
     s->launches += 1;
   }
-  if (c.error) return fail((ac_status)c.error, "device watchdog: no progress (block %d)", c.err_block);
+  if (c.error == AC_ERR_STALL) return fail(AC_ERR_STALL, "device watchdog: no progress (block %d)", c.err_block);
+  if (c.error) return fail((ac_status)c.error, "device reported error %d (count window)", c.error);
   return AC_OK;
 }
 
+// Tile grid of the temporal-blocked round kernel: tiles of side <= 128 - 2D, at
+// least 2 per dimension, and a tile count that fills the SMs' waves evenly.
+void tb_tiling(int rows, int cols, int region, int halo, int sms, int* tr, int* tc) {
+  const int own = region - 2 * halo;
+  const int r0 = std::max(2, ceil_div(rows, own)), c0 = std::max(2, ceil_div(cols, own));
+  double best = 1e300;
+  *tr = r0;
+  *tc = c0;
+  for (int a = r0; a < r0 + 8 && a <= rows / 2; ++a)
+    for (int b = c0; b < c0 + 8 && b <= cols / 2; ++b) {
+      const double waves = std::ceil((double)a * b / sms);
+      const double region = (std::ceil((double)rows / a) + 2 * halo) * (std::ceil((double)cols / b) + 2 * halo);
+      const double cost = waves * region;
+      if (cost < best - 1e-9) {
+        best = cost;
+        *tr = a;
+        *tc = b;
+      }
+    }
+}
+
+bool tb_applicable(const ac_sim* s) {
+  const int D = s->cfg.rounds;
+  return s->cfg.rounds > 1 && D <= ac::kTbMaxHalo && s->rows >= 4 * D && s->cols >= 4 * D;
+}
+
+// The temporal-blocked kernel keeps counts as 16-bit offsets within a window of
+// +-32768 around each region's centre; it may run only if no region's counts can
+// leave that window during the call.
+ac_status tb_counts_fit(ac_sim* s, long long t_end, bool* fits) {
+  const ac::LatDesc d = s->host_desc(s->t_done, 0);
+  unsigned init[2] = {0xFFFFFFFFu, 0u}, r[2] = {0u, 0u};
+  unsigned* d_r = reinterpret_cast<unsigned*>(s->d_red);
+  AC_CUDA(cudaMemcpyAsync(d_r, init, sizeof init, cudaMemcpyHostToDevice, s->stream));
+  AC_CUDA(ac::launch_count_range(&d, d_r, s->stream));
+  AC_CUDA(cudaMemcpyAsync(r, d_r, sizeof r, cudaMemcpyDeviceToHost, s->stream));
+  AC_CUDA(cudaStreamSynchronize(s->stream));
+  const double span = (double)(t_end - s->t_done) / kTicksPerUnit;
+  // a cell commits about `span` arrivals (Poisson); allow a wide margin
+  *fits = (double)(r[1] - r[0]) + 2.0 * span + 64.0 * std::sqrt(span + 1.0) + 64.0 < 30000.0;
+  return AC_OK;
+}
+
+ac_status run_tb(ac_sim* s, long long t_end) {
+  const size_t N = s->ncells();
+  if (!s->key2) {
+    if (cudaMalloc(&s->key2, N * 8) != cudaSuccess || cudaMalloc(&s->cnt2, N * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AC_ERR_OOM, "second state buffer (%zu cells) allocation failed", N);
+    }
+  }
+  const int D = s->cfg.rounds;
+  const int region = ac::tb_region_for(D);
+  int tr = 0, tc = 0;
+  tb_tiling(s->rows, s->cols, region, D, ac::tb_grid(region), &tr, &tc);
+  ac::LatDesc d = s->host_desc(t_end, 0);
+  d.tr = tr;
+  d.tc = tc;
+  const int total = tr * tc;
+  AC_CUDA(cudaMemcpyAsync(s->d_desc, &d, sizeof d, cudaMemcpyHostToDevice, s->stream));
+  AC_CUDA(cudaMemsetAsync(s->d_ctr, 0, sizeof(ac::DevCounters), s->stream));
+  AC_CUDA(cudaEventRecord(s->ev0, s->stream));
+  // about 8.3 synchronous rounds per unit time (Sec. 4), D of them per launch
+  const double span = (double)(t_end - s->t_done) / kTicksPerUnit;
+  int chunk = (int)std::min(4096.0, (9.0 * std::ceil(span) + 16.0) / D + 2.0);
+  int launch_idx = 0;
+  for (;;) {
+    for (int i = 0; i < chunk; ++i) {
+      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, D, launch_idx & 1, launch_idx, s->d_ctr, s->stream));
+      ++launch_idx;
+    }
+    ac::DevCounters cc{};
+    AC_CUDA(cudaMemcpyAsync(&cc, s->d_ctr, sizeof cc, cudaMemcpyDeviceToHost, s->stream));
+    AC_CUDA(cudaStreamSynchronize(s->stream));
+    if (cc.active[(launch_idx - 1) % 3] == 0 || cc.error) break;
+    if ((double)launch_idx * D > 64.0 * (9.0 * std::ceil(span) + 16.0) + 4096.0)
+      return fail(AC_ERR_STALL, "round kernel: no completion after %d launches", launch_idx);
+    chunk = 4;
+  }
+  AC_CUDA(cudaEventRecord(s->ev1, s->stream));
+  ac::DevCounters c{};
+  AC_CUDA(cudaMemcpyAsync(&c, s->d_ctr, sizeof c, cudaMemcpyDeviceToHost, s->stream));
+  AC_CUDA(cudaStreamSynchronize(s->stream));
+  float ms = 0.f;
+  AC_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+  // executed launches form a prefix; launch j wrote the second buffer when j is even.
+  // A launch that hit the count window (safety net, see tb_counts_fit) produced no
+  // consistent output: its input is the state to keep.
+  const unsigned good = (c.error == AC_ERR_STATE) ? c.launched - 1u : c.launched;
+  if (good & 1u) {
+    std::swap(s->key, s->key2);
+    std::swap(s->cnt, s->cnt2);
+  }
+  s->last_grid = std::min(total, ac::tb_grid(region));
+  return accumulate(s, c, ms, true);
+}
+
 ac_status run_round(ac_sim* s, long long t_end) {
+  if (tb_applicable(s)) {
+    bool fits = false;
+    ac_status st = tb_counts_fit(s, t_end, &fits);
+    if (st != AC_OK) return st;
+    if (fits) return run_tb(s, t_end);
+    // counts too uneven for the 16-bit window: one exact synchronous round per launch
+    const int saved = s->cfg.rounds;
+    s->cfg.rounds = 1;
+    st = run_round(s, t_end);
+    s->cfg.rounds = saved;
+    return st;
+  }
   const int total = s->tiles();
   const ac::LatDesc d = s->host_desc(t_end, 0);
   AC_CUDA(cudaMemcpyAsync(s->d_desc, &d, sizeof d, cudaMemcpyHostToDevice, s->stream));

@@ -59,7 +59,14 @@ __device__ __forceinline__ Philox4 philox_event(uint32_t c0, uint32_t c1, uint32
 //   32 steps of: square y (a full 64-bit product), emit the bit that says whether
 //   the square reached 2.0 in Q1.31, and keep the truncated Q1.31 value (halved
 //   when the bit is set);  gap = floor(((33 - k) * 2^32 - f) * ln2 * 2^64 / 2^64) + 1.
-__device__ __forceinline__ unsigned long long exp_ticks(uint32_t x) {
+//
+// `two` must hold 2 at run time but be opaque to the compiler (a kernel argument),
+// so that the step's bookkeeping stays on the FMA pipe (multiply-adds), leaving one
+// funnel shift per step on the integer ALU pipe, the scarcer one on sm_103.  Each
+// step computes amt = 31 + bit = hi32(hi * 2) + 31 with one mad.hi and accumulates
+// f' = 2 f' + amt; since sum_i (31 + b_i) 2^(31-i) = f + 31 (2^32 - 1), the bits are
+// recovered at the end as f = f' + 31 (mod 2^32).
+__device__ __forceinline__ unsigned long long exp_ticks(uint32_t x, uint32_t two) {
   uint32_t k, y;
   if (x & 0x80000000u) {
     k = 32u;
@@ -70,16 +77,18 @@ __device__ __forceinline__ unsigned long long exp_ticks(uint32_t x) {
     k = 31u - lz;
     y = m << lz;
   }
-  uint32_t f = 0u;
+  uint32_t fa = 0u;
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
     const unsigned long long sq = (unsigned long long)y * y;
     const uint32_t hi = (uint32_t)(sq >> 32);
     const uint32_t lo = (uint32_t)sq;
-    const uint32_t bit = hi >> 31;          // square >= 2.0 in Q1.31
-    y = bit ? hi : __funnelshift_l(lo, hi, 1);
-    f = (f << 1) | bit;
+    uint32_t amt;                                        // 32 if the square reached 2.0, else 31
+    asm("mad.hi.u32 %0, %1, %2, 31;" : "=r"(amt) : "r"(hi), "r"(two));
+    y = __funnelshift_rc(lo, hi, amt);                   // square >> (31 + bit), low word
+    fa = fa * two + amt;
   }
+  const uint32_t f = fa + 31u;
   const unsigned long long nl = ((unsigned long long)(33u - k) << 32) - f;
   return __umul64hi(nl, kLn2Q64) + 1ull;
 }

@@ -21,6 +21,8 @@ struct LatDesc {
   unsigned int* cnt;
   unsigned long long* pub;   // edge words, live (blocked kernel) / round input
   unsigned long long* pub2;  // round kernel output edge words (ping-pong)
+  unsigned long long* key2;  // second state buffer (temporal-blocked round kernel, ping-pong)
+  unsigned int* cnt2;
   unsigned long long* events;  // per-lattice committed-arrival counter
   int rows, cols;
   int tr, tc;
@@ -31,7 +33,7 @@ struct LatDesc {
   long long t_end;           // commit arrivals with tick < t_end
   unsigned long long t2;     // 2 * t_end: key < t2  <=>  tick < t_end
   int drop_publish;          // verification hook: suppress edge-word publication
-  int pad_;
+  unsigned int two;          // the constant 2, opaque to the compiler (see exp_ticks)
 };
 
 // Device counters of one run call (zeroed by the host before the call).
@@ -49,6 +51,11 @@ struct DevCounters {
 };
 
 enum KernelKind { kKernelRound = 0, kKernelBlocked = 1 };
+
+// Temporal-blocked round kernel: a shared-memory region of side 96 (two CTAs per
+// SM) or 128 (one) holds a tile and a halo of depth D around it; tile side = region - 2D.
+constexpr int kTbMaxHalo = 16;
+inline int tb_region_for(int halo) { return halo <= 12 ? 96 : 128; }
 
 struct LaunchCfg {
   int kernel;       // KernelKind
@@ -76,10 +83,14 @@ cudaError_t launch_round(const LatDesc* d_desc, int nlat, int total_tiles, const
 cudaError_t launch_blocked(const LatDesc* d_desc, int nlat, int total_tiles, const LaunchCfg& cfg,
                            int grid, unsigned int* tile_done, DevCounters* ctr, cudaStream_t s);
 cudaError_t launch_reduce(const LatDesc* host_desc, unsigned long long* d_out4, cudaStream_t s);
+cudaError_t launch_count_range(const LatDesc* host_desc, unsigned* d_out2, cudaStream_t s);
 cudaError_t launch_unpack(const LatDesc* host_desc, int8_t* s_out, long long* t_out,
                           unsigned int* n_out, cudaStream_t st);
 cudaError_t launch_pack(const LatDesc* host_desc, const int8_t* s_in, const long long* t_in,
                         const unsigned int* n_in, cudaStream_t st);
+cudaError_t launch_tb(const LatDesc* d_desc, int nlat, int total_tiles, int region, int halo, int rounds,
+                      int parity, int launch_idx, DevCounters* ctr, cudaStream_t s);
+int tb_grid(int region);   // resident CTAs of the temporal-blocked kernel
 cudaError_t launch_exp_ticks(const uint32_t* x, unsigned long long* out, long long n, cudaStream_t s);
 cudaError_t launch_philox(unsigned long long seed, const uint32_t* c, const uint32_t* k, uint32_t w2,
                           uint32_t* out4, long long n, cudaStream_t s);

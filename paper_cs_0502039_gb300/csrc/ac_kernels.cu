@@ -41,6 +41,8 @@
 //     number of times and are then left for the CTA's next tile; a
 //     %globaltimer watchdog turns a stall into an error code.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <cstdint>
 
 #include "ac_device.cuh"
@@ -271,7 +273,7 @@ __device__ __forceinline__ void commit_tile(const Smem<LB>& sm, const LatDesc& L
     const unsigned n_old = DIRECT ? L.cnt[gidx] : sm.C[r * LB + c];
     const Philox4 b = philox_event(gidx, n_old + 1u, 0u, L.seed_lo, L.seed_hi);
     const unsigned flip = b.y < sm.thr[j + 5u * sp] ? 1u : 0u;
-    const unsigned long long nk = (key & ~1ull) + (exp_ticks(b.x) << 1) + (sp ^ flip);
+    const unsigned long long nk = (key & ~1ull) + (exp_ticks(b.x, L.two) << 1) + (sp ^ flip);
     *kp = nk;
     if (DIRECT) {
       L.key[gidx] = nk;
@@ -332,7 +334,7 @@ __global__ void init_kernel(LatDesc L, int init_mode) {
     if (init_mode == 1) up = 1u;
     else if (init_mode == 2) up = 0u;
     else up = philox_event((uint32_t)c, 0u, 1u, L.seed_lo, L.seed_hi).x & 1u;
-    L.key[c] = (exp_ticks(b0.x) << 1) | up;
+    L.key[c] = (exp_ticks(b0.x, L.two) << 1) | up;
     L.cnt[c] = 0u;
   }
 }
@@ -480,12 +482,28 @@ __global__ void __launch_bounds__(4 * LB) blocked_kernel(const LatDesc* __restri
         const int n = (int)sm.n_en[cur];
         if (n == 0) {
           if (!any_live) { done = true; break; }
-          if (stuck >= polls) break;
-          ++stuck;
-          ++npolls;
-          __nanosleep(256u << min(stuck, 4));
-          if (hs.src) fill_halo<LB, true>(sm, hs);
-          __syncthreads();
+          // blocked on the halo: poll the neighbours' edge words and rescan only
+          // once one of them has moved (a rescan with an unchanged halo finds nothing)
+          bool moved = false;
+          for (;;) {
+            if (stuck >= polls) break;
+            ++stuck;
+            ++npolls;
+            __nanosleep(256u << min(stuck, 4));
+            bool mine = false;
+            if (hs.src) {
+              const unsigned long long v = ld_relaxed(hs.src) + (unsigned long long)hs.adj;
+              if (v != sm.K[hs.slot]) {
+                sm.K[hs.slot] = v;
+                mine = true;
+              }
+            }
+            if (__syncthreads_or(mine)) {
+              moved = true;
+              break;
+            }
+          }
+          if (!moved) break;
           continue;
         }
         stuck = 0;
@@ -542,6 +560,273 @@ __global__ void __launch_bounds__(4 * LB) blocked_kernel(const LatDesc* __restri
   }
 }
 
+
+// ----------------------------------------------------------------------------
+// (a) Temporal-blocked round kernel.  A CTA loads a 128 x 128 region -- its tile
+// of side 128 - 2D plus a halo of depth D around it, wrapped on the torus -- from
+// the input state buffer, runs R <= D synchronous rounds in shared memory and
+// writes the tile to the output buffer (ping-pong, so every launch reads one
+// consistent state).  Round k scans the region minus its outer k rings: a cell at
+// distance d from the region's edge follows the global synchronous schedule for d
+// rounds, so after R rounds the tile is exactly where R global rounds of Fig. 3.2
+// would put it, while the halo's commits (redundant with the neighbouring tiles)
+// are discarded.  Halo cells that come from across the torus seam carry key + 2
+// (seam above / left of the tile) or key - 2 (below / right): comparisons between
+// two cells on the same side are unchanged, and between the sides they give the
+// (tick, index) order of the seam.  Requires rows, cols >= 4D (the region never
+// overlaps itself).
+template <int RW>
+struct TbCfg {
+  static constexpr int PAIRS = RW / 2;            // a thread scans a column pair ...
+  static constexpr int GROUPS = 8;                // ... in one of 8 row bands
+  static constexpr int ROWS = RW / GROUPS;        // rows per band (12 or 16)
+  static constexpr int NT = PAIRS * GROUPS;       // 384 or 512 threads = 4 * RW
+  // enabled cells form an independent set of the scanned rectangle (at most
+  // (RW-2) x (RW-2) cells): the list holds every one of them, so a round always
+  // commits all enabled cells and every tile advances exactly R synchronous rounds
+  static constexpr int LIST = ((RW - 2) * (RW - 2) + 1) / 2 + 32;
+  static constexpr int MIN_CTAS = (RW <= 96) ? 2 : 1;
+  // keys with one guard row above and two below (the unrolled scan reads neighbours of
+  // masked-out rows), 16-bit counts relative to a per-region base, work list, tables
+  static constexpr size_t kBytes = size_t(RW + 3) * RW * 8;
+  static constexpr size_t cBytes = size_t(RW) * RW * 2;
+  static constexpr size_t lBytes = size_t(LIST) * 2;
+  static constexpr size_t gBytes = size_t(RW) * 4 * 2;
+  static constexpr size_t mBytes = 64;
+  static constexpr size_t bytes = kBytes + cBytes + lBytes + gBytes + mBytes;
+};
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ int wrap_index(int x, int n, int& shift, int up_shift) {
+  // x in [-n, 2n): wrapped index; shift = +up_shift if x came from below 0, -up_shift if >= n
+  if (x < 0) {
+    shift = up_shift;
+    return x + n;
+  }
+  if (x >= n) {
+    shift = -up_shift;
+    return x - n;
+  }
+  shift = 0;
+  return x;
+}
+
+template <int RW>
+__global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
+    tb_kernel(const LatDesc* __restrict__ lats, int nlat, int total_tiles, int D, int R, int parity,
+              int launch_idx, DevCounters* ctr) {
+  using Cfg = TbCfg<RW>;
+  constexpr int NT = Cfg::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned long long* K = reinterpret_cast<unsigned long long*>(smem_raw) + RW;   // row 0
+  unsigned short* C = reinterpret_cast<unsigned short*>(smem_raw + Cfg::kBytes);
+  unsigned short* list = reinterpret_cast<unsigned short*>(smem_raw + Cfg::kBytes + Cfg::cBytes);
+  unsigned int* rowoff = reinterpret_cast<unsigned int*>(smem_raw + Cfg::kBytes + Cfg::cBytes + Cfg::lBytes);
+  unsigned int* colg = rowoff + RW;
+  unsigned int* misc = colg + RW;
+  unsigned int* n_en = misc;          // [2]
+  unsigned int* thr = misc + 2;       // [10]
+  unsigned int* s_over = misc + 12;   // count window overflow in this region
+
+  if (launch_idx > 0) {
+    // nothing left, or an earlier launch of this call hit the count window (its output
+    // is not a consistent state, so no later launch may build on it)
+    if (*(volatile unsigned*)&ctr->active[(launch_idx + 2) % 3] == 0u || *(volatile int*)&ctr->error != 0)
+      return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctr->active[(launch_idx + 1) % 3] = 0u;
+    atomicAdd(&ctr->launched, 1u);
+  }
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int lj = tid % RW, li0 = tid / RW;                 // load / store mapping: column, first row
+  const int pc = (tid % Cfg::PAIRS) * 2;                   // scan mapping: column pair ...
+  const int rbase = 1 + Cfg::ROWS * (tid / Cfg::PAIRS);    // ... and first row of its band
+  unsigned long long scanned = 0, enabled = 0, rounds_done = 0, events_total = 0;
+
+  for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+    const LatDesc& L = lats[find_lattice(lats, nlat, tile)];
+    const Geom g = tile_geom(L, tile - L.tile_base);
+    const unsigned long long* key_in = parity ? L.key2 : L.key;
+    const unsigned int* cnt_in = parity ? L.cnt2 : L.cnt;
+    unsigned long long* key_out = parity ? L.key : L.key2;
+    unsigned int* cnt_out = parity ? L.cnt : L.cnt2;
+    const int RH = g.h + 2 * D, RC = g.w + 2 * D;
+    const bool edge = (g.ti == 0) || (g.ti == L.tr - 1) || (g.tj == 0) || (g.tj == L.tc - 1);
+    // counts are kept as 16-bit offsets from a window start taken at the tile centre
+    const unsigned ccen = __ldg(&cnt_in[(size_t)(g.r0 + g.h / 2) * L.cols + g.c0 + g.w / 2]);
+    const unsigned base = ccen > 32768u ? ccen - 32768u : 0u;
+    const unsigned cap = 65535u - (unsigned)R;
+
+    // ---- load the region: keys by asynchronous copies, counts through registers
+    if (tid == 0) {
+      n_en[0] = 0u;
+      n_en[1] = 0u;
+      s_over[0] = 0u;
+    }
+    int shc;
+    const int gc = wrap_index(g.c0 - D + lj, L.cols, shc, 2);
+    bool over = false;
+    __syncthreads();
+    if (lj < RC) {
+      for (int i = li0; i < RH; i += 4) {
+        int shr;
+        const int gr = wrap_index(g.r0 - D + i, L.rows, shr, 2);
+        const size_t gi = (size_t)gr * L.cols + gc;
+        cp_async8(&K[i * RW + lj], &key_in[gi]);
+        const unsigned cv = cnt_in[gi] - base;
+        over |= cv > cap;
+        C[i * RW + lj] = (unsigned short)cv;
+      }
+    }
+    if (tid < RW) {
+      int sh;
+      rowoff[tid] = (unsigned)wrap_index(min(g.r0 - D + tid, 2 * L.rows - 1), L.rows, sh, 2) * (unsigned)L.cols;
+      colg[tid] = (unsigned)wrap_index(min(g.c0 - D + tid, 2 * L.cols - 1), L.cols, sh, 2);
+    } else if (tid < RW + 10) {
+      thr[tid - RW] = L.thr[tid - RW];
+    }
+    if (over) atomicOr(s_over, 1u);
+    cp_async_wait_all();
+    __syncthreads();
+    if (edge) {   // halo cells from across the torus seam: key +-2 (one tick of tie order)
+      if (lj < RC) {
+        for (int i = li0; i < RH; i += 4) {
+          int shr;
+          wrap_index(g.r0 - D + i, L.rows, shr, 2);
+          if (shr + shc) K[i * RW + lj] += (unsigned long long)(long long)(shr + shc);
+        }
+      }
+      __syncthreads();
+    }
+    if (s_over[0]) {
+      // the counts of this region do not fit the 16-bit window (the host checks the
+      // lattice's count range first, so this is a safety net): flag the launch; the
+      // host then discards its output and keeps the launch's input state
+      if (tid == 0) atomicCAS(&ctr->error, 0, 5 /* AC_ERR_STATE */);
+      __syncthreads();
+      continue;
+    }
+
+    // ---- R synchronous rounds over the shrinking region
+    const unsigned long long t2 = L.t2;
+    const uint32_t two = L.two, seed_lo = L.seed_lo, seed_hi = L.seed_hi;
+    constexpr unsigned kEven = 0x55555555u, kOdd = 0xAAAAAAAAu;
+    int cur = 0;
+    for (int k = 1; k <= R; ++k) {
+      const unsigned colm = ((pc >= k && pc < RC - k) ? kEven : 0u) | ((pc + 1 >= k && pc + 1 < RC - k) ? kOdd : 0u);
+      const int rlo = max(k - rbase, 0), rhi = min(RH - k - rbase, Cfg::ROWS);
+      unsigned rowm = 0u;
+      if (rhi > rlo) {
+        const unsigned hi_bits = (2 * rhi >= 32) ? 0xFFFFFFFFu : ((1u << (2 * rhi)) - 1u);
+        rowm = hi_bits & ~((1u << (2 * rlo)) - 1u);
+      }
+      const unsigned valid = colm & rowm;
+      unsigned mask = 0;
+      if (valid) {
+        const unsigned long long* q = K + rbase * RW + pc;
+        ulonglong2 cv = *reinterpret_cast<const ulonglong2*>(q);
+        const ulonglong2 uv = *reinterpret_cast<const ulonglong2*>(q - RW);
+        bool upa = (cv.x | 1ull) < uv.x, upb = (cv.y | 1ull) < uv.y;
+#pragma unroll
+        for (int i = 0; i < Cfg::ROWS; ++i) {
+          const ulonglong2 dv = *reinterpret_cast<const ulonglong2*>(q + (i + 1) * RW);
+          const unsigned long long left = q[i * RW - 1], right = q[i * RW + 2];
+          const unsigned long long loa = cv.x & ~1ull, lob = cv.y & ~1ull;
+          const bool da = loa <= dv.x, db = lob <= dv.y;
+          const bool ab = loa <= cv.y;   // a before b; its complement is "b before a"
+          const bool ea = (cv.x < t2) & upa & da & ((cv.x | 1ull) < left) & ab;
+          const bool eb = (cv.y < t2) & upb & db & !ab & (lob <= right);
+          mask |= ((unsigned)ea << (2 * i)) | ((unsigned)eb << (2 * i + 1));
+          upa = !da;
+          upb = !db;
+          cv = dv;
+        }
+        mask &= valid;
+        scanned += (unsigned long long)__popc(valid);
+      }
+      const int cnt = __popc(mask);
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+      }
+      int wbase = 0;
+      if (lane == 31 && incl) wbase = (int)atomicAdd(&n_en[cur], (unsigned)incl);
+      wbase = __shfl_sync(kFull, wbase, 31);
+      int off = wbase + incl - cnt;
+      while (mask) {
+        const int b = __ffs(mask) - 1;
+        mask &= mask - 1;
+        if (off < Cfg::LIST) list[off] = (unsigned short)(((rbase + (b >> 1)) << 8) | (pc + (b & 1)));
+        ++off;
+      }
+      __syncthreads();
+      const int n = min((int)n_en[cur], Cfg::LIST);
+      if (n == 0) break;
+      for (int e_i = tid; e_i < n; e_i += NT) {
+        const unsigned e = list[e_i];
+        const int r = (int)(e >> 8), cc = (int)(e & 255u);
+        unsigned long long* kp = K + r * RW + cc;
+        const unsigned long long key = *kp;
+        const unsigned j = ((unsigned)kp[-RW] & 1u) + ((unsigned)kp[RW] & 1u) + ((unsigned)kp[-1] & 1u) +
+                           ((unsigned)kp[1] & 1u);
+        const unsigned sp = (unsigned)key & 1u;
+        const uint32_t gidx = rowoff[r] + colg[cc];
+        const unsigned c16 = C[r * RW + cc];
+        const Philox4 b = philox_event(gidx, base + c16 + 1u, 0u, seed_lo, seed_hi);
+        const unsigned flip = b.y < thr[j + 5u * sp] ? 1u : 0u;
+        *kp = (key & ~1ull) + (exp_ticks(b.x, two) << 1) + (sp ^ flip);
+        C[r * RW + cc] = (unsigned short)(c16 + 1u);
+      }
+      enabled += (unsigned long long)n;
+      ++rounds_done;
+      if (tid == 0) n_en[cur ^ 1] = 0u;
+      __syncthreads();
+      cur ^= 1;
+    }
+
+    // ---- write the tile back; count its arrivals; is anything left before t_end?
+    bool live = false;
+    unsigned long long ev = 0;
+    if (lj >= D && lj < D + g.w) {
+      for (int i = li0; i < g.h; i += 4) {
+        const int si = (i + D) * RW + lj;
+        const size_t gi = (size_t)(g.r0 + i) * L.cols + g.c0 + lj - D;
+        const unsigned long long kk = K[si];
+        const unsigned nn = base + C[si];
+        ev += (unsigned long long)(nn - cnt_in[gi]);
+        key_out[gi] = kk;
+        cnt_out[gi] = nn;
+        live |= kk < t2;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
+    if (lane == 0 && ev) {
+      atomicAdd(L.events, ev);
+      events_total += ev;
+    }
+    const int any_live = __syncthreads_or(live);
+    if (tid == 0 && any_live) atomicAdd(&ctr->active[launch_idx % 3], 1u);
+  }
+  for (int o = 16; o > 0; o >>= 1) scanned += __shfl_down_sync(kFull, scanned, o);
+  if (lane == 0) {
+    if (scanned) atomicAdd(&ctr->scanned, scanned);
+    if (events_total) atomicAdd(&ctr->events, events_total);
+  }
+  if (tid == 0) {
+    atomicAdd(&ctr->enabled, enabled);
+    atomicAdd(&ctr->rounds, rounds_done);
+  }
+}
+
 // ---- observables, packing, device-primitive probes ---------------------------
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
@@ -586,6 +871,25 @@ __global__ void reduce_kernel(LatDesc L, unsigned long long* out) {
   }
 }
 
+// out[0] = min count, out[1] = max count (out initialised to {~0, 0} by the caller)
+__global__ void count_range_kernel(LatDesc L, unsigned* out) {
+  const size_t N = (size_t)L.rows * L.cols;
+  unsigned mn = 0xFFFFFFFFu, mx = 0u;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+    const unsigned v = L.cnt[c];
+    mn = min(mn, v);
+    mx = max(mx, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_down_sync(kFull, mn, o));
+    mx = max(mx, __shfl_down_sync(kFull, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&out[0], mn);
+    atomicMax(&out[1], mx);
+  }
+}
+
 __global__ void unpack_kernel(LatDesc L, int8_t* s, long long* t, unsigned* n) {
   const size_t N = (size_t)L.rows * L.cols;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
@@ -606,10 +910,10 @@ __global__ void pack_kernel(LatDesc L, const int8_t* s, const long long* t, cons
   }
 }
 
-__global__ void exp_ticks_kernel(const uint32_t* x, unsigned long long* out, long long n) {
+__global__ void exp_ticks_kernel(const uint32_t* x, unsigned long long* out, long long n, uint32_t two) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    out[i] = exp_ticks(x[i]);
+    out[i] = exp_ticks(x[i], two);
 }
 
 __global__ void philox_kernel(unsigned long long seed, const uint32_t* c, const uint32_t* k,
@@ -752,6 +1056,12 @@ cudaError_t launch_reduce(const LatDesc* h, unsigned long long* d_out4, cudaStre
   return cudaGetLastError();
 }
 
+cudaError_t launch_count_range(const LatDesc* h, unsigned* d_out2, cudaStream_t st) {
+  const size_t N = (size_t)h->rows * h->cols;
+  count_range_kernel<<<grid_for(N, 256), 256, 0, st>>>(*h, d_out2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_unpack(const LatDesc* h, int8_t* so, long long* to, unsigned* no, cudaStream_t st) {
   const size_t N = (size_t)h->rows * h->cols;
   unpack_kernel<<<grid_for(N, 256), 256, 0, st>>>(*h, so, to, no);
@@ -765,9 +1075,44 @@ cudaError_t launch_pack(const LatDesc* h, const int8_t* si, const long long* ti,
   return cudaGetLastError();
 }
 
+
+template <int RW>
+cudaError_t tb_launch_rw(const LatDesc* d, int nlat, int total, int halo, int rounds, int parity, int launch_idx,
+                         DevCounters* ctr, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TbCfg<RW>::bytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int grid = std::min(total, tb_grid(RW));
+  tb_kernel<RW><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds, parity, launch_idx,
+                                                              ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tb(const LatDesc* d, int nlat, int total, int region, int halo, int rounds, int parity,
+                      int launch_idx, DevCounters* ctr, cudaStream_t s) {
+  if (halo < 1 || rounds < 1 || rounds > halo || 4 * halo >= region) return cudaErrorInvalidValue;
+  switch (region) {
+    case 96: return tb_launch_rw<96>(d, nlat, total, halo, rounds, parity, launch_idx, ctr, s);
+    case 128: return tb_launch_rw<128>(d, nlat, total, halo, rounds, parity, launch_idx, ctr, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int tb_grid(int region) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  return sms * (region <= 96 ? TbCfg<96>::MIN_CTAS : TbCfg<128>::MIN_CTAS);
+}
+
 cudaError_t launch_exp_ticks(const uint32_t* x, unsigned long long* out, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  exp_ticks_kernel<<<grid_for((size_t)n, 256), 256, 0, s>>>(x, out, n);
+  exp_ticks_kernel<<<grid_for((size_t)n, 256), 256, 0, s>>>(x, out, n, 2u);
   return cudaGetLastError();
 }
 

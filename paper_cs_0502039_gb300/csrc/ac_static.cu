@@ -130,6 +130,7 @@ extern "C" ac_status ac_run_blocked_static(int32_t rows, int32_t cols, double be
   d.seed_hi = (unsigned)(seed >> 32);
   d.t_end = t_end;
   d.t2 = 2ull * (unsigned long long)t_end;
+  d.two = 2u;
 
   ac::LaunchCfg cfg{};
   cfg.kernel = ac::kKernelBlocked;

@@ -33,10 +33,14 @@ CASES = [
     (130, 66, 0.2, 0.8, -0.3, 7, 3, 0),
     (2, 200, 0.5, 1.0, 0.0, 8, 4, 0),
     (257, 3, 0.5, 1.0, 0.0, 9, 4, 0),
+    (300, 250, 0.44, 1.0, 0.0, 10, 3, 0),      # several temporal-blocked tiles, seams both ways
+    (64, 520, 0.9, 1.0, -0.05, 12, 3, 1),
 ]
 
+# rounds > 1 selects the temporal-blocked round kernel where rows, cols >= 4 * rounds
 CONFIGS = [
-    (ROUND, 32, 1, 0), (ROUND, 64, 1, 0), (ROUND, 32, 5, 0), (ROUND, 128, 3, 0),
+    (ROUND, 32, 1, 0), (ROUND, 64, 1, 0), (ROUND, 32, 5, 0), (ROUND, 128, 3, 0), (ROUND, 64, 2, 0),
+    (ROUND, 64, 8, 0), (ROUND, 64, 16, 0),
     (BLOCKED, 32, 1, 8), (BLOCKED, 64, 1, 8), (BLOCKED, 128, 1, 8), (BLOCKED, 32, 4, 0),
 ]
 
@@ -142,3 +146,18 @@ def test_invalid_arguments_are_rejected():
         bad_t = np.zeros(256, dtype=np.int64)
         with pytest.raises(ac.ACError):
             sim.load_state(np.ones(256, np.int8), bad_t, np.zeros(256, np.uint32), 0)
+
+
+def test_temporal_blocking_with_uneven_loaded_counts():
+    """Counts too far apart for the temporal-blocked kernel's 16-bit window: the run
+    must finish through the 32-bit-count kernel and stay bit-exact."""
+    rows, cols, seed = 200, 160, 21
+    st = oracle.init(rows, cols, 0, seed)
+    st.n[: rows * cols // 2] += 100000          # half the cells far ahead in their streams
+    ref = st.copy()
+    oracle.run(ref, oracle.thresholds(0.5, 1.0, 0.0), seed, 4 * T32)
+    with ac.Sim(rows, cols, 0.5, 1.0, 0.0, seed, kernel=ROUND, rounds=8) as sim:
+        sim.load_state(st.s, st.t, st.n, 0)
+        sim.run_until(4)
+        s, t, n = sim.read_state()
+    assert_same(ref, s, t, n, "uneven counts")
