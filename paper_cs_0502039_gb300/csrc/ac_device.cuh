@@ -60,12 +60,13 @@ __device__ __forceinline__ Philox4 philox_event(uint32_t c0, uint32_t c1, uint32
 //   the square reached 2.0 in Q1.31, and keep the truncated Q1.31 value (halved
 //   when the bit is set);  gap = floor(((33 - k) * 2^32 - f) * ln2 * 2^64 / 2^64) + 1.
 //
-// `two` must hold 2 at run time but be opaque to the compiler (a kernel argument),
-// so that the step's bookkeeping stays on the FMA pipe (multiply-adds), leaving one
-// funnel shift per step on the integer ALU pipe, the scarcer one on sm_103.  Each
-// step computes amt = 31 + bit = hi32(hi * 2) + 31 with one mad.hi and accumulates
-// f' = 2 f' + amt; since sum_i (31 + b_i) 2^(31-i) = f + 31 (2^32 - 1), the bits are
-// recovered at the end as f = f' + 31 (mod 2^32).
+// Pipe balance (measured with the exp_ticks probe on a GB300): the 32x32->64 square
+// (IMAD.WIDE) occupies the FMA-heavy pipe for several cycles, so the step's other
+// work is split: the shift amount 31 + bit comes from the integer ALU (a shift and
+// an add), the funnel shift is an ALU op, and the accumulation f' = 2 f' + amt is a
+// multiply-add on the FMA pipe -- `two` must hold 2 at run time but be opaque to the
+// compiler (a kernel argument) so that it stays one.  Since
+// sum_i (31 + b_i) 2^(31-i) = f + 31 (2^32 - 1), the bits are f = f' + 31 (mod 2^32).
 __device__ __forceinline__ unsigned long long exp_ticks(uint32_t x, uint32_t two) {
   uint32_t k, y;
   if (x & 0x80000000u) {
@@ -83,8 +84,7 @@ __device__ __forceinline__ unsigned long long exp_ticks(uint32_t x, uint32_t two
     const unsigned long long sq = (unsigned long long)y * y;
     const uint32_t hi = (uint32_t)(sq >> 32);
     const uint32_t lo = (uint32_t)sq;
-    uint32_t amt;                                        // 32 if the square reached 2.0, else 31
-    asm("mad.hi.u32 %0, %1, %2, 31;" : "=r"(amt) : "r"(hi), "r"(two));
+    const uint32_t amt = (hi >> 31) + 31u;               // 32 if the square reached 2.0, else 31
     y = __funnelshift_rc(lo, hi, amt);                   // square >> (31 + bit), low word
     fa = fa * two + amt;
   }

@@ -675,14 +675,29 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     bool over = false;
     __syncthreads();
     if (lj < RC) {
-      for (int i = li0; i < RH; i += 4) {
-        int shr;
-        const int gr = wrap_index(g.r0 - D + i, L.rows, shr, 2);
-        const size_t gi = (size_t)gr * L.cols + gc;
-        cp_async8(&K[i * RW + lj], &key_in[gi]);
-        const unsigned cv = cnt_in[gi] - base;
-        over |= cv > cap;
-        C[i * RW + lj] = (unsigned short)cv;
+      // eight rows per batch: all global loads of a batch are in flight together
+      for (int i0 = li0; i0 < RH; i0 += 32) {
+        unsigned cvs[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int i = i0 + 4 * m;
+          if (i < RH) {
+            int shr;
+            const int gr = wrap_index(g.r0 - D + i, L.rows, shr, 2);
+            const size_t gi = (size_t)gr * L.cols + gc;
+            cp_async8(&K[i * RW + lj], &key_in[gi]);
+            cvs[m] = cnt_in[gi];
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int i = i0 + 4 * m;
+          if (i < RH) {
+            const unsigned cv = cvs[m] - base;
+            over |= cv > cap;
+            C[i * RW + lj] = (unsigned short)cv;
+          }
+        }
       }
     }
     if (tid < RW) {
@@ -771,7 +786,33 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       __syncthreads();
       const int n = min((int)n_en[cur], Cfg::LIST);
       if (n == 0) break;
-      for (int e_i = tid; e_i < n; e_i += NT) {
+      // two commits per iteration: all shared-memory reads first, then two independent
+      // Philox / exp_ticks chains the compiler can interleave, then the writes
+      // (listed cells are pairwise non-adjacent, so the two never touch each other)
+      int e_i = tid;
+      for (; e_i + NT < n; e_i += 2 * NT) {
+        const unsigned ea = list[e_i], eb = list[e_i + NT];
+        const int ra = (int)(ea >> 8), ca = (int)(ea & 255u), rb = (int)(eb >> 8), cb = (int)(eb & 255u);
+        unsigned long long* kpa = K + ra * RW + ca;
+        unsigned long long* kpb = K + rb * RW + cb;
+        const unsigned long long keya = *kpa, keyb = *kpb;
+        const unsigned ja = ((unsigned)kpa[-RW] & 1u) + ((unsigned)kpa[RW] & 1u) + ((unsigned)kpa[-1] & 1u) +
+                            ((unsigned)kpa[1] & 1u);
+        const unsigned jb = ((unsigned)kpb[-RW] & 1u) + ((unsigned)kpb[RW] & 1u) + ((unsigned)kpb[-1] & 1u) +
+                            ((unsigned)kpb[1] & 1u);
+        const unsigned spa = (unsigned)keya & 1u, spb = (unsigned)keyb & 1u;
+        const uint32_t gia = rowoff[ra] + colg[ca], gib = rowoff[rb] + colg[cb];
+        const unsigned c16a = C[ra * RW + ca], c16b = C[rb * RW + cb];
+        const unsigned tha = thr[ja + 5u * spa], thb = thr[jb + 5u * spb];
+        const Philox4 pa = philox_event(gia, base + c16a + 1u, 0u, seed_lo, seed_hi);
+        const Philox4 pb = philox_event(gib, base + c16b + 1u, 0u, seed_lo, seed_hi);
+        const unsigned long long gapa = exp_ticks(pa.x, two), gapb = exp_ticks(pb.x, two);
+        *kpa = (keya & ~1ull) + (gapa << 1) + (spa ^ (pa.y < tha ? 1u : 0u));
+        *kpb = (keyb & ~1ull) + (gapb << 1) + (spb ^ (pb.y < thb ? 1u : 0u));
+        C[ra * RW + ca] = (unsigned short)(c16a + 1u);
+        C[rb * RW + cb] = (unsigned short)(c16b + 1u);
+      }
+      if (e_i < n) {
         const unsigned e = list[e_i];
         const int r = (int)(e >> 8), cc = (int)(e & 255u);
         unsigned long long* kp = K + r * RW + cc;
@@ -797,15 +838,27 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     bool live = false;
     unsigned long long ev = 0;
     if (lj >= D && lj < D + g.w) {
-      for (int i = li0; i < g.h; i += 4) {
-        const int si = (i + D) * RW + lj;
-        const size_t gi = (size_t)(g.r0 + i) * L.cols + g.c0 + lj - D;
-        const unsigned long long kk = K[si];
-        const unsigned nn = base + C[si];
-        ev += (unsigned long long)(nn - cnt_in[gi]);
-        key_out[gi] = kk;
-        cnt_out[gi] = nn;
-        live |= kk < t2;
+      for (int i0 = li0; i0 < g.h; i0 += 32) {
+        unsigned old_n[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int i = i0 + 4 * m;
+          if (i < g.h) old_n[m] = cnt_in[(size_t)(g.r0 + i) * L.cols + g.c0 + lj - D];
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int i = i0 + 4 * m;
+          if (i < g.h) {
+            const int si = (i + D) * RW + lj;
+            const size_t gi = (size_t)(g.r0 + i) * L.cols + g.c0 + lj - D;
+            const unsigned long long kk = K[si];
+            const unsigned nn = base + C[si];
+            ev += (unsigned long long)(nn - old_n[m]);
+            key_out[gi] = kk;
+            cnt_out[gi] = nn;
+            live |= kk < t2;
+          }
+        }
       }
     }
     for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
