@@ -150,6 +150,12 @@ struct BatchRunner {
   cudaGraph_t graph = nullptr;
   ac::LaunchCfg cfg{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // temporal-blocked batches: per-lattice count ranges, a captured chunk of launches
+  bool tb = false;
+  int region = 0, halo = 0, calls = 0;
+  unsigned* d_range = nullptr;
+  cudaGraphExec_t chunk_exec = nullptr;
+  cudaGraph_t chunk_graph = nullptr;
 };
 
 std::mutex g_batch_mu;
@@ -166,6 +172,9 @@ void free_runner(BatchRunner* r) {
   if (r->ev0) cudaEventDestroy(r->ev0);
   if (r->ev1) cudaEventDestroy(r->ev1);
   if (r->own_stream) cudaStreamDestroy(r->own_stream);
+  if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
+  if (r->chunk_graph) cudaGraphDestroy(r->chunk_graph);
+  if (r->d_range) cudaFree(r->d_range);
   delete r;
 }
 
@@ -372,13 +381,14 @@ ac_status run_tb(ac_sim* s, long long t_end) {
   int launch_idx = 0;
   for (;;) {
     for (int i = 0; i < chunk; ++i) {
-      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, D, launch_idx & 1, launch_idx, s->d_ctr, s->stream));
+      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, D, s->d_ctr, s->stream));
       ++launch_idx;
     }
     ac::DevCounters cc{};
     AC_CUDA(cudaMemcpyAsync(&cc, s->d_ctr, sizeof cc, cudaMemcpyDeviceToHost, s->stream));
     AC_CUDA(cudaStreamSynchronize(s->stream));
-    if (cc.active[(launch_idx - 1) % 3] == 0 || cc.error) break;
+    // the last completed launch left nothing, or a later launch found nothing left
+    if (cc.seq < (unsigned)launch_idx || cc.error || (cc.seq > 0 && cc.active[(cc.seq + 2) % 3] == 0)) break;
     if ((double)launch_idx * D > 64.0 * (9.0 * std::ceil(span) + 16.0) + 4096.0)
       return fail(AC_ERR_STALL, "round kernel: no completion after %d launches", launch_idx);
     chunk = 4;
@@ -389,10 +399,10 @@ ac_status run_tb(ac_sim* s, long long t_end) {
   AC_CUDA(cudaStreamSynchronize(s->stream));
   float ms = 0.f;
   AC_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
-  // executed launches form a prefix; launch j wrote the second buffer when j is even.
-  // A launch that hit the count window (safety net, see tb_counts_fit) produced no
-  // consistent output: its input is the state to keep.
-  const unsigned good = (c.error == AC_ERR_STATE) ? c.launched - 1u : c.launched;
+  // c.seq launches completed; launch j wrote the second buffer when j is even.  A launch
+  // that hit the count window (safety net, see tb_counts_fit) produced no consistent
+  // output: its input is the state to keep.
+  const unsigned good = (c.error == AC_ERR_STATE) ? c.seq - 1u : c.seq;
   if (good & 1u) {
     std::swap(s->key, s->key2);
     std::swap(s->cnt, s->cnt2);
@@ -501,6 +511,116 @@ ac_status run_blocked(ac_sim* s, long long t_end) {
 ac_status read_event_counter(ac_sim* s, unsigned long long* v) {
   AC_CUDA(cudaMemcpyAsync(v, s->d_events, 8, cudaMemcpyDeviceToHost, s->stream));
   AC_CUDA(cudaStreamSynchronize(s->stream));
+  return AC_OK;
+}
+
+constexpr int kTbChunk = 8;   // launches per captured chunk
+
+// Batched temporal-blocked rounds: every launch covers the tiles of all handles (one
+// work list), so all lattices advance by the same synchronous rounds per launch.
+ac_status batch_run_tb(int32_t n, ac_sim* const* sims, const int64_t* t_end, BatchRunner* R) {
+  const cudaStream_t stream = R->stream;
+  for (int i = 0; i < n; ++i) {
+    ac_sim* s = sims[i];
+    if (!s->key2) {
+      if (cudaMalloc(&s->key2, s->ncells() * 8) != cudaSuccess || cudaMalloc(&s->cnt2, s->ncells() * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AC_ERR_OOM, "second state buffer allocation failed (handle %d)", i);
+      }
+    }
+  }
+  int base = 0;
+  double span = 0.0;
+  for (int i = 0; i < n; ++i) {
+    int tr = 0, tc = 0;
+    tb_tiling(sims[i]->rows, sims[i]->cols, R->region, R->halo, ac::tb_grid(R->region), &tr, &tc);
+    R->h_desc[i] = sims[i]->host_desc(t_end[i], base);
+    R->h_desc[i].tr = tr;
+    R->h_desc[i].tc = tc;
+    base += tr * tc;
+    span = std::max(span, (double)(t_end[i] - sims[i]->t_done) / kTicksPerUnit);
+  }
+  const int total = base;
+  AC_CUDA(cudaMemcpyAsync(R->d_desc, R->h_desc, sizeof(ac::LatDesc) * n, cudaMemcpyHostToDevice, stream));
+  // the 16-bit count window must hold every region of every lattice for the whole call
+  std::vector<unsigned> range(2 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    range[2 * i] = 0xFFFFFFFFu;
+    range[2 * i + 1] = 0u;
+  }
+  AC_CUDA(cudaMemcpyAsync(R->d_range, range.data(), range.size() * 4, cudaMemcpyHostToDevice, stream));
+  AC_CUDA(ac::launch_count_range_batch(R->d_desc, n, R->d_range, stream));
+  AC_CUDA(cudaMemcpyAsync(range.data(), R->d_range, range.size() * 4, cudaMemcpyDeviceToHost, stream));
+  std::vector<unsigned long long> before(n), after(n);
+  for (int i = 0; i < n; ++i)
+    AC_CUDA(cudaMemcpyAsync(&before[i], sims[i]->d_events, 8, cudaMemcpyDeviceToHost, stream));
+  AC_CUDA(cudaStreamSynchronize(stream));
+  const double margin = 2.0 * span + 64.0 * std::sqrt(span + 1.0) + 64.0;
+  for (int i = 0; i < n; ++i) {
+    if ((double)(range[2 * i + 1] - range[2 * i]) + margin >= 30000.0) {
+      // very uneven counts (loaded states only): run every handle on its own, exactly
+      for (int k = 0; k < n; ++k) {
+        ac_status st = ac_run_until_ticks(sims[k], t_end[k]);
+        if (st != AC_OK) return st;
+      }
+      return AC_OK;
+    }
+  }
+  AC_CUDA(cudaMemsetAsync(R->d_ctr, 0, sizeof(ac::DevCounters), stream));
+  AC_CUDA(cudaEventRecord(R->ev0, stream));
+  const bool use_graph = R->calls++ > 0;   // repeated calls on the same handles replay a captured chunk
+  if (use_graph && !R->chunk_exec) {
+    cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+    for (int i = 0; i < kTbChunk && e == cudaSuccess; ++i)
+      e = ac::launch_tb(R->d_desc, n, total, R->region, R->halo, R->halo, R->d_ctr, stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(stream, &g);
+    if (e == cudaSuccess) e = e2;
+    R->chunk_graph = g;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&R->chunk_exec, g, 0);
+    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "round-kernel graph capture failed: %s", cudaGetErrorString(e));
+  }
+  int issued = 0;
+  for (;;) {
+    if (use_graph) {
+      AC_CUDA(cudaGraphLaunch(R->chunk_exec, stream));
+    } else {
+      for (int i = 0; i < kTbChunk; ++i) AC_CUDA(ac::launch_tb(R->d_desc, n, total, R->region, R->halo, R->halo, R->d_ctr, stream));
+    }
+    issued += kTbChunk;
+    ac::DevCounters cc{};
+    AC_CUDA(cudaMemcpyAsync(&cc, R->d_ctr, sizeof cc, cudaMemcpyDeviceToHost, stream));
+    AC_CUDA(cudaStreamSynchronize(stream));
+    if (cc.seq < (unsigned)issued || cc.error || (cc.seq > 0 && cc.active[(cc.seq + 2) % 3] == 0)) break;
+    if ((double)issued * R->halo > 64.0 * (9.0 * std::ceil(span) + 16.0) + 4096.0)
+      return fail(AC_ERR_STALL, "batched round kernel: no completion after %d launches", issued);
+  }
+  AC_CUDA(cudaEventRecord(R->ev1, stream));
+  ac::DevCounters c{};
+  AC_CUDA(cudaMemcpyAsync(&c, R->d_ctr, sizeof c, cudaMemcpyDeviceToHost, stream));
+  for (int i = 0; i < n; ++i)
+    AC_CUDA(cudaMemcpyAsync(&after[i], sims[i]->d_events, 8, cudaMemcpyDeviceToHost, stream));
+  AC_CUDA(cudaStreamSynchronize(stream));
+  float ms = 0.f;
+  AC_CUDA(cudaEventElapsedTime(&ms, R->ev0, R->ev1));
+  const unsigned good = (c.error == AC_ERR_STATE) ? c.seq - 1u : c.seq;
+  for (int i = 0; i < n; ++i) {
+    ac_sim* s = sims[i];
+    if (good & 1u) {
+      std::swap(s->key, s->key2);
+      std::swap(s->cnt, s->cnt2);
+    }
+    if (c.error) continue;
+    s->events += after[i] - before[i];
+    s->t_done = t_end[i];
+    s->launches += c.launched;
+    s->device_ms += ms;
+    s->last_grid = std::min(total, ac::tb_grid(R->region));
+  }
+  if (c.error) return fail((ac_status)c.error, "batched round kernel: device error %d", c.error);
+  sims[0]->rounds += c.rounds;
+  sims[0]->scanned += c.scanned;
+  sims[0]->enabled += c.enabled;
   return AC_OK;
 }
 
@@ -760,11 +880,53 @@ ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_en
       if (sims[k] == sims[i]) return fail(AC_ERR_ARG, "handle %d appears twice", i);
   }
   std::vector<ac_sim*> keyv(sims, sims + n);
+  bool want_tb = true;
+  for (int i = 0; i < n; ++i)
+    want_tb = want_tb && sims[i]->cfg.kernel == ac::kKernelRound && sims[i]->cfg.rounds == sims[0]->cfg.rounds &&
+              tb_applicable(sims[i]);
   BatchRunner* R = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_batch_mu);
     auto it = g_runners.find(keyv);
-    if (it != g_runners.end()) R = it->second;
+    if (it != g_runners.end()) {
+      if (it->second->tb != want_tb) {
+        free_runner(it->second);
+        g_runners.erase(it);
+      } else {
+        R = it->second;
+      }
+    }
+  }
+  if (want_tb) {
+    if (!R) {
+      R = new BatchRunner();
+      R->sims = keyv;
+      R->tb = true;
+      R->halo = sims[0]->cfg.rounds;
+      R->region = ac::tb_region_for(R->halo);
+      R->lb = sims[0]->cfg.lb;
+      if (sims[0]->stream == nullptr) {
+        if (cudaStreamCreate(&R->own_stream) != cudaSuccess) {
+          free_runner(R);
+          return fail(AC_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        R->stream = R->own_stream;
+      } else {
+        R->stream = sims[0]->stream;
+      }
+      if (cudaHostAlloc(&R->h_desc, sizeof(ac::LatDesc) * n, cudaHostAllocDefault) != cudaSuccess ||
+          cudaMalloc(&R->d_desc, sizeof(ac::LatDesc) * n) != cudaSuccess ||
+          cudaMalloc(&R->d_ctr, sizeof(ac::DevCounters)) != cudaSuccess ||
+          cudaMalloc(&R->d_range, sizeof(unsigned) * 2 * n) != cudaSuccess ||
+          cudaEventCreate(&R->ev0) != cudaSuccess || cudaEventCreate(&R->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        free_runner(R);
+        return fail(AC_ERR_OOM, "batch runner allocation failed");
+      }
+      std::lock_guard<std::mutex> lk(g_batch_mu);
+      g_runners[keyv] = R;
+    }
+    return batch_run_tb(n, sims, t_end, R);
   }
   if (!R) {
     R = new BatchRunner();

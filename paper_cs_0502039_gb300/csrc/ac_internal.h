@@ -48,6 +48,8 @@ struct DevCounters {
   int err_block;
   unsigned int active[3];       // round kernel: tiles with pending arrivals (mod-3 ring)
   unsigned int launched;        // round kernel: launches that did work
+  unsigned int seq;             // temporal-blocked kernel: launches completed in this call
+  unsigned int blocks_done;     // temporal-blocked kernel: CTAs finished in the current launch
 };
 
 enum KernelKind { kKernelRound = 0, kKernelBlocked = 1 };
@@ -88,8 +90,12 @@ cudaError_t launch_unpack(const LatDesc* host_desc, int8_t* s_out, long long* t_
                           unsigned int* n_out, cudaStream_t st);
 cudaError_t launch_pack(const LatDesc* host_desc, const int8_t* s_in, const long long* t_in,
                         const unsigned int* n_in, cudaStream_t st);
+// Launch of the temporal-blocked round kernel.  The launch number (which fixes the
+// ping-pong parity) is kept on the device in ctr->seq, so every launch of a run has
+// the same arguments and a sequence of launches can be captured in a CUDA graph.
 cudaError_t launch_tb(const LatDesc* d_desc, int nlat, int total_tiles, int region, int halo, int rounds,
-                      int parity, int launch_idx, DevCounters* ctr, cudaStream_t s);
+                      DevCounters* ctr, cudaStream_t s);
+cudaError_t launch_count_range_batch(const LatDesc* d_desc, int nlat, unsigned* d_out2n, cudaStream_t s);
 int tb_grid(int region);   // resident CTAs of the temporal-blocked kernel
 cudaError_t launch_exp_ticks(const uint32_t* x, unsigned long long* out, long long n, cudaStream_t s);
 cudaError_t launch_philox(unsigned long long seed, const uint32_t* c, const uint32_t* k, uint32_t w2,

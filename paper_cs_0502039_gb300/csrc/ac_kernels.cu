@@ -618,8 +618,7 @@ __device__ __forceinline__ int wrap_index(int x, int n, int& shift, int up_shift
 
 template <int RW>
 __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
-    tb_kernel(const LatDesc* __restrict__ lats, int nlat, int total_tiles, int D, int R, int parity,
-              int launch_idx, DevCounters* ctr) {
+    tb_kernel(const LatDesc* __restrict__ lats, int nlat, int total_tiles, int D, int R, DevCounters* ctr) {
   using Cfg = TbCfg<RW>;
   constexpr int NT = Cfg::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -633,9 +632,12 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   unsigned int* thr = misc + 2;       // [10]
   unsigned int* s_over = misc + 12;   // count window overflow in this region
 
+  // this launch's number, advanced by the last CTA of the previous launch
+  const unsigned launch_idx = *(volatile unsigned*)&ctr->seq;
+  const int parity = (int)(launch_idx & 1u);
   if (launch_idx > 0) {
     // nothing left, or an earlier launch of this call hit the count window (its output
-    // is not a consistent state, so no later launch may build on it)
+    // is not a consistent state, so no later launch may build on it): uniform exit
     if (*(volatile unsigned*)&ctr->active[(launch_idx + 2) % 3] == 0u || *(volatile int*)&ctr->error != 0)
       return;
   }
@@ -874,9 +876,17 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     if (scanned) atomicAdd(&ctr->scanned, scanned);
     if (events_total) atomicAdd(&ctr->events, events_total);
   }
+  __syncthreads();
   if (tid == 0) {
     atomicAdd(&ctr->enabled, enabled);
     atomicAdd(&ctr->rounds, rounds_done);
+    // the last CTA of this launch advances the launch number for the next one
+    __threadfence();
+    if (atomicAdd(&ctr->blocks_done, 1u) == gridDim.x - 1u) {
+      ctr->blocks_done = 0u;
+      __threadfence();
+      atomicExch(&ctr->seq, launch_idx + 1u);
+    }
   }
 }
 
@@ -940,6 +950,27 @@ __global__ void count_range_kernel(LatDesc L, unsigned* out) {
   if ((threadIdx.x & 31) == 0) {
     atomicMin(&out[0], mn);
     atomicMax(&out[1], mx);
+  }
+}
+
+// out[2i] = min count, out[2i+1] = max count of lattice i (initialised to {~0, 0});
+// blockIdx.y = lattice, blockIdx.x strides over its cells
+__global__ void count_range_batch_kernel(const LatDesc* __restrict__ lats, unsigned* out) {
+  const LatDesc& L = lats[blockIdx.y];
+  const size_t N = (size_t)L.rows * L.cols;
+  unsigned mn = 0xFFFFFFFFu, mx = 0u;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+    const unsigned v = L.cnt[c];
+    mn = min(mn, v);
+    mx = max(mx, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_down_sync(kFull, mn, o));
+    mx = max(mx, __shfl_down_sync(kFull, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&out[2 * blockIdx.y], mn);
+    atomicMax(&out[2 * blockIdx.y + 1], mx);
   }
 }
 
@@ -1115,6 +1146,12 @@ cudaError_t launch_count_range(const LatDesc* h, unsigned* d_out2, cudaStream_t 
   return cudaGetLastError();
 }
 
+cudaError_t launch_count_range_batch(const LatDesc* d, int nlat, unsigned* d_out2n, cudaStream_t st) {
+  if (nlat <= 0) return cudaSuccess;
+  count_range_batch_kernel<<<dim3(8, (unsigned)nlat), 256, 0, st>>>(d, d_out2n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_unpack(const LatDesc* h, int8_t* so, long long* to, unsigned* no, cudaStream_t st) {
   const size_t N = (size_t)h->rows * h->cols;
   unpack_kernel<<<grid_for(N, 256), 256, 0, st>>>(*h, so, to, no);
@@ -1130,8 +1167,8 @@ cudaError_t launch_pack(const LatDesc* h, const int8_t* si, const long long* ti,
 
 
 template <int RW>
-cudaError_t tb_launch_rw(const LatDesc* d, int nlat, int total, int halo, int rounds, int parity, int launch_idx,
-                         DevCounters* ctr, cudaStream_t s) {
+cudaError_t tb_launch_rw(const LatDesc* d, int nlat, int total, int halo, int rounds, DevCounters* ctr,
+                         cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1140,17 +1177,16 @@ cudaError_t tb_launch_rw(const LatDesc* d, int nlat, int total, int halo, int ro
     attr = true;
   }
   const int grid = std::min(total, tb_grid(RW));
-  tb_kernel<RW><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds, parity, launch_idx,
-                                                              ctr);
+  tb_kernel<RW><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds, ctr);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tb(const LatDesc* d, int nlat, int total, int region, int halo, int rounds, int parity,
-                      int launch_idx, DevCounters* ctr, cudaStream_t s) {
+cudaError_t launch_tb(const LatDesc* d, int nlat, int total, int region, int halo, int rounds, DevCounters* ctr,
+                      cudaStream_t s) {
   if (halo < 1 || rounds < 1 || rounds > halo || 4 * halo >= region) return cudaErrorInvalidValue;
   switch (region) {
-    case 96: return tb_launch_rw<96>(d, nlat, total, halo, rounds, parity, launch_idx, ctr, s);
-    case 128: return tb_launch_rw<128>(d, nlat, total, halo, rounds, parity, launch_idx, ctr, s);
+    case 96: return tb_launch_rw<96>(d, nlat, total, halo, rounds, ctr, s);
+    case 128: return tb_launch_rw<128>(d, nlat, total, halo, rounds, ctr, s);
     default: return cudaErrorInvalidValue;
   }
 }
