@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the per-kernel side measurements")
+    ap.add_argument("--workload", default="ising4096", choices=["ising4096", "batch", "serve"],
+                    help="ising4096: the headline step; batch: the 512-lattice batch only; serve: the request stream")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the replayed request stream")
     ap.add_argument("--single", action="store_true",
                     help="one lattice, one kernel configuration (the profiling case); prints one JSON line")
     ap.add_argument("--rows", type=int, default=4096)
@@ -234,6 +237,16 @@ def main():
         return run_reference(args)
     if args.single:
         return run_single(args)
+    if args.workload in ("batch", "serve"):
+        import torch
+        torch.cuda.set_device(0)
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_cs_0502039_gb300 as ac
+        res = batch_measurement(ac, args.rounds, args.lb) if args.workload == "batch" else \
+            serve_measurement(ac, args.serve_seconds, args.rounds, args.lb)
+        print(json.dumps({"workload": args.workload, **res}), flush=True)
+        return 0
 
     import numpy as np
     import torch
@@ -378,9 +391,11 @@ def main():
                "d2h_bytes_per_step": 12 * N * len(sims), "steps": e_steps,
                "path": "ac_load_state(host) + run + ac_read_state(host) per lattice"}
 
-    extra = {}
+    extra, batch, served = {}, None, None
     if rank == 0 and not args.no_extra:
         extra = side_measurements(ac, w, seed)
+        batch = batch_measurement(ac)
+        served = serve_measurement(ac, seconds=args.serve_seconds)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -402,13 +417,85 @@ def main():
                           "parallelism": f"replicas x{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(),
-               "blocked_stats": {k: stats0[k] for k in ("visits", "polls", "rounds", "scanned", "enabled",
-                                                        "grid", "ctas_per_sm")},
-               "kernels": extra}
+               "kernel_stats": {k: stats0[k] for k in ("visits", "polls", "rounds", "scanned", "enabled",
+                                                       "grid", "ctas_per_sm")},
+               "kernels": extra, "batch": batch, "serve": served}
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def batch_measurement(ac, rounds=8, lb=64):
+    """512 independent lattices (L log-uniform in [32, 1024], beta ~ U[0.3, 0.6], seeds 0..511) run
+    to T = 100: one batched call (one work list of all tiles, launches replayed from a captured
+    graph) against 512 plain per-lattice run calls on the same GPU."""
+    from paper_cs_0502039_gb300 import workloads
+    ws = workloads.batch_workload()
+    handles = ac.ac_batch_create([(w["rows"], w["cols"], w["init"]) for w in ws], [w["beta"] for w in ws],
+                                 [w["J"] for w in ws], [w["h"] for w in ws], [w["seed"] for w in ws])
+    sims = [ac.Sim(w["rows"], w["cols"], w["beta"], w["J"], w["h"], w["seed"], handle=h) for w, h in zip(ws, handles)]
+    for s in sims:
+        s.configure(ac.AC_KERNEL_ROUND, lb, rounds, 8)
+    t_end = [int(w["T"] * T32) for w in ws]
+    import torch
+
+    def reset_all():
+        for w, s in zip(ws, sims):
+            s.reset(w["seed"], w["init"])
+
+    out = {"lattices": len(ws), "cells": sum(w["rows"] * w["cols"] for w in ws), "T": ws[0]["T"]}
+    for mode in ("batched", "plain"):
+        times = []
+        for rep in range(3):          # rep 0 warms up (and, for batched, captures the graph)
+            reset_all()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if mode == "batched":
+                ac.ac_batch_run_until([s.handle for s in sims], t_end)
+            else:
+                for s, te in zip(sims, t_end):
+                    s.run_until_ticks(te)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        ev = sum(s.stats()["events"] for s in sims)
+        out[mode] = {"events": ev, "seconds": min(times[1:]), "events_per_s": ev / min(times[1:])}
+    out["batched_over_plain"] = out["batched"]["events_per_s"] / out["plain"]["events_per_s"]
+    for s in sims:
+        s.close()
+    return out
+
+
+def serve_measurement(ac, seconds=10.0, rounds=8, lb=64):
+    """Continuous batching: a Poisson request stream (200 requests/s, L log-uniform in [64, 2048],
+    beta ~ U[0.25, 0.7], T ~ U[10, 200], seed = request id) replayed in real time; latency is
+    request arrival -> result ready.  Baseline: the same requests run one after another, each
+    with a plain run call (its own launches), on the same GPU."""
+    from paper_cs_0502039_gb300 import serve as srv_mod
+    from paper_cs_0502039_gb300 import workloads
+    reqs = workloads.serve_requests(rate=200.0, duration=seconds)
+    results, wall, server = srv_mod.serve(reqs, budget_bytes=64 << 30, slice_T=10.0, rounds=rounds, Lb=lb,
+                                          realtime=True)
+    lat = sorted(r.latency for r in results)
+    ev = sum(r.events for r in results)
+    span = max(r.finished for r in results) - min(r.arrival for r in results)
+    out = {"requests": len(reqs), "completed": len(results), "wall_s": wall, "events": ev,
+           "events_per_s": ev / span, "p50_latency_s": lat[len(lat) // 2],
+           "p99_latency_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "steps": server.steps,
+           "offered_events_per_s": sum(r["rows"] * r["cols"] * r["T"] for r in reqs) / seconds}
+    # serial per-request baseline on a sample (first 100 requests, timed end to end)
+    sample = reqs[:100]
+    t0 = time.perf_counter()
+    sev = 0
+    for r in sample:
+        with ac.Sim(r["rows"], r["cols"], r["beta"], r["J"], r["h"], r["seed"], init=r["init"],
+                    kernel=ac.AC_KERNEL_ROUND, Lb=lb, rounds=rounds) as s:
+            s.run_until(r["T"])
+            sev += s.stats()["events"]
+    dt = time.perf_counter() - t0
+    out["serial_sample"] = {"requests": len(sample), "events_per_s": sev / dt, "seconds": dt}
+    out["served_over_serial"] = out["events_per_s"] / out["serial_sample"]["events_per_s"]
+    return out
 
 
 def side_measurements(ac, w, seed):
