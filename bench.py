@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--rounds", type=int, default=8,
                     help="round kernel: synchronous rounds per launch (>1: temporal blocking); blocked: refresh")
     ap.add_argument("--polls", type=int, default=8)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use --kernel/--lb/--rounds/--polls as given instead of the autotuned configuration")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the per-kernel side measurements")
@@ -60,10 +62,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_cs_0502039_gb300.dist import rank_env
+    return rank_env()
 
 
 class ClockSampler:
@@ -268,8 +268,15 @@ def main():
 
     w = WORKLOAD
     kern = ac.AC_KERNEL_BLOCKED if args.kernel == "blocked" else ac.AC_KERNEL_ROUND
+    tuned = None
+    if not args.no_autotune:
+        from paper_cs_0502039_gb300 import autotune
+        tuned = autotune.tune(w["rows"], w["cols"], T=4.0)
+        kern, args.lb, args.rounds, args.polls = tuned["kernel"], tuned["Lb"], tuned["rounds"], tuned["polls"]
+        args.kernel = "blocked" if kern == ac.AC_KERNEL_BLOCKED else "round"
     # weak scaling: every rank runs its own replica batch (seed offset by rank)
-    seed = w["seed"] + 1000 * rank
+    from paper_cs_0502039_gb300.dist import replica_seed
+    seed = replica_seed(w["seed"], rank)
     sims = [ac.Sim(w["rows"], w["cols"], b, w["J"], w["h"], seed, init=w["init"], kernel=kern, Lb=args.lb,
                    rounds=args.rounds, polls=args.polls) for b in w["betas"]]
     handles = [s.handle for s in sims]
@@ -412,6 +419,8 @@ def main():
                "config": {"workload": w["name"], "rows": w["rows"], "cols": w["cols"], "betas": w["betas"],
                           "J": w["J"], "h": w["h"], "seed": w["seed"], "T": w["T"], "init": "random",
                           "kernel": kname, "Lb": args.lb, "polls": args.polls, "rounds": args.rounds,
+                          "autotuned": None if tuned is None else {k: tuned[k] for k in ("kernel", "Lb", "rounds",
+                                                                                       "polls", "events_per_s")},
                           "events_per_step": ev_all / args.steps,
                           "l2": "state 3 x 201 MB > 129 MB L2 (no flush)",
                           "parallelism": f"replicas x{world}"},

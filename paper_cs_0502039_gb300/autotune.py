@@ -1,0 +1,91 @@
+"""Autotuner: pick the kernel and its tuning per lattice size class by timing them.
+
+For a (rows, cols) class -- each side rounded up to a power of two -- every candidate
+configuration runs the same short trajectory (a lattice of the class's size, seed 1,
+beta 0.44) and the one with the highest committed-arrival rate (device time of the
+run calls) wins.  The trajectory is the same for every candidate (Sec. 3: it does not
+depend on the partition or the schedule), so the tuner changes speed only; it also
+checks that every candidate ends in the same state fingerprint.  Results are cached
+in a JSON file keyed by GPU name and size class.
+
+Candidates: the round kernel with R in {4, 6, 8, 10, 12, 16} rounds per launch
+(temporal blocking, where the lattice is large enough) and the blocked persistent
+kernel with tile side 32, 64 or 128 and 2 or 8 halo polls.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import ac as _ac
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_cs_0502039_gb300", "autotune.json")
+
+CANDIDATES = ([dict(kernel=_ac.AC_KERNEL_ROUND, Lb=64, rounds=r, polls=0) for r in (4, 6, 8, 10, 12, 16)] +
+              [dict(kernel=_ac.AC_KERNEL_BLOCKED, Lb=lb, rounds=1, polls=p) for lb in (32, 64, 128) for p in (2, 8)])
+
+
+def _bucket(n: int) -> int:
+    b = 1
+    while b < n:
+        b *= 2
+    return b
+
+
+def _gpu_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name(0)
+    except Exception:
+        return "unknown"
+
+
+def class_key(rows: int, cols: int) -> str:
+    return f"{_gpu_name()}|{_bucket(rows)}x{_bucket(cols)}"
+
+
+def _load(path: str) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def measure(rows: int, cols: int, cfg: dict, T: float = 2.0) -> dict:
+    with _ac.Sim(rows, cols, 0.44, 1.0, 0.0, 1, kernel=cfg["kernel"], Lb=cfg["Lb"], rounds=cfg["rounds"],
+                 polls=cfg["polls"]) as sim:
+        sim.run_until(T)                 # warm-up (module load, graph, allocation of the second buffer)
+        sim.reset(1)
+        sim.run_until(T)
+        st = sim.stats()
+    return dict(cfg, events=st["events"], device_ms=st["device_ms"],
+                events_per_s=st["events"] / max(st["device_ms"], 1e-6) * 1e3, checksum=st["checksum"])
+
+
+def tune(rows: int, cols: int, T: float = 2.0, cache_path: str | None = None, force: bool = False) -> dict:
+    """Best configuration for the size class of (rows, cols); cached."""
+    path = cache_path or os.environ.get("AC_AUTOTUNE_CACHE", DEFAULT_CACHE)
+    cache = _load(path)
+    key = class_key(rows, cols)
+    if key in cache and not force:
+        return cache[key]
+    R, C = _bucket(rows), _bucket(cols)
+    results = [measure(R, C, cfg, T) for cfg in CANDIDATES]
+    sums = {r["checksum"] for r in results}
+    if len(sums) != 1:
+        raise RuntimeError(f"autotune: candidates disagree on the trajectory ({len(sums)} fingerprints)")
+    best = max(results, key=lambda r: r["events_per_s"])
+    entry = {k: best[k] for k in ("kernel", "Lb", "rounds", "polls", "events_per_s")}
+    entry["measured"] = [{k: r[k] for k in ("kernel", "Lb", "rounds", "polls", "events_per_s")} for r in results]
+    cache[key] = entry
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, path)
+    return entry
+
+
+def apply(sim: "_ac.Sim", entry: dict) -> None:
+    sim.configure(entry["kernel"], entry["Lb"], entry["rounds"], entry["polls"])
