@@ -81,8 +81,9 @@ struct ac_sim {
 
   unsigned long long* key = nullptr;
   unsigned int* cnt = nullptr;
-  unsigned long long* key2 = nullptr;       // second state buffer (temporal-blocked rounds)
-  unsigned int* cnt2 = nullptr;
+  unsigned long long* key2 = nullptr;       // second state buffer (temporal-blocked rounds);
+  unsigned int* cnt2 = nullptr;             // between run calls also the staging of state transfers
+  int8_t* stage8 = nullptr;                 // spin staging of state transfers
   unsigned long long* pub = nullptr;
   unsigned long long* pub2 = nullptr;
   size_t pub_words = 0;
@@ -219,6 +220,7 @@ void free_sim(ac_sim* s) {
   cudaFree(s->cnt);
   cudaFree(s->key2);
   cudaFree(s->cnt2);
+  cudaFree(s->stage8);
   cudaFree(s->pub);
   cudaFree(s->pub2);
   cudaFree(s->d_events);
@@ -698,28 +700,42 @@ ac_status ac_run_until(ac_sim* sim, double T) {
   return ac_run_until_ticks(sim, (int64_t)ticks);
 }
 
-ac_status ac_read_state(const ac_sim* sim, int8_t* s, int64_t* t, uint32_t* n) {
-  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+}  // extern "C"
+
+namespace {
+// Device staging for state transfers: the second state buffers (free between run calls)
+// and a byte array for the spins.
+ac_status ensure_staging(ac_sim* s) {
+  const size_t N = s->ncells();
+  if (!s->key2 && (cudaMalloc(&s->key2, N * 8) != cudaSuccess || cudaMalloc(&s->cnt2, N * 4) != cudaSuccess)) {
+    cudaGetLastError();
+    return fail(AC_ERR_OOM, "state staging allocation failed");
+  }
+  if (!s->stage8 && cudaMalloc(&s->stage8, N) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AC_ERR_OOM, "state staging allocation failed");
+  }
+  return AC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ac_status ac_read_state(const ac_sim* csim, int8_t* s, int64_t* t, uint32_t* n) {
+  if (!csim) return fail(AC_ERR_ARG, "sim is NULL");
+  ac_sim* sim = const_cast<ac_sim*>(csim);   // staging buffers only; the state is not modified
   const size_t N = sim->ncells();
   if (s || t) {
-    std::vector<int64_t> tmp;
-    int64_t* kbuf = t;
-    if (!kbuf) {
-      tmp.resize(N);
-      kbuf = tmp.data();
-    }
-    AC_CUDA(cudaMemcpyAsync(kbuf, sim->key, N * 8, cudaMemcpyDeviceToHost, sim->stream));
-    AC_CUDA(cudaStreamSynchronize(sim->stream));
-    for (size_t c = 0; c < N; ++c) {
-      const uint64_t k = (uint64_t)kbuf[c];
-      if (s) s[c] = (k & 1u) ? 1 : -1;
-      if (t) t[c] = (int64_t)(k >> 1);
-    }
+    ac_status st = ensure_staging(sim);
+    if (st != AC_OK) return st;
+    const ac::LatDesc d = sim->host_desc(sim->t_done, 0);
+    AC_CUDA(ac::launch_unpack(&d, s ? sim->stage8 : nullptr, t ? (long long*)sim->key2 : nullptr, nullptr,
+                              sim->stream));
+    if (s) AC_CUDA(cudaMemcpyAsync(s, sim->stage8, N, cudaMemcpyDeviceToHost, sim->stream));
+    if (t) AC_CUDA(cudaMemcpyAsync(t, sim->key2, N * 8, cudaMemcpyDeviceToHost, sim->stream));
   }
-  if (n) {
-    AC_CUDA(cudaMemcpyAsync(n, sim->cnt, N * 4, cudaMemcpyDeviceToHost, sim->stream));
-    AC_CUDA(cudaStreamSynchronize(sim->stream));
-  }
+  if (n) AC_CUDA(cudaMemcpyAsync(n, sim->cnt, N * 4, cudaMemcpyDeviceToHost, sim->stream));
+  AC_CUDA(cudaStreamSynchronize(sim->stream));
   return AC_OK;
 }
 
@@ -737,16 +753,24 @@ ac_status ac_load_state(ac_sim* sim, const int8_t* s, const int64_t* t, const ui
   if (!s || !t || !n) return fail(AC_ERR_ARG, "s, t and n are required");
   if (t_done < 0 || t_done >= kTickLimit) return fail(AC_ERR_ARG, "t_done out of range");
   const size_t N = sim->ncells();
-  std::vector<uint64_t> packed(N);
+  ac_status st = ensure_staging(sim);
+  if (st != AC_OK) return st;
+  // copy into staging, validate on the device, and only then replace the state
+  AC_CUDA(cudaMemcpyAsync(sim->stage8, s, N, cudaMemcpyHostToDevice, sim->stream));
+  AC_CUDA(cudaMemcpyAsync(sim->key2, t, N * 8, cudaMemcpyHostToDevice, sim->stream));
+  AC_CUDA(cudaMemcpyAsync(sim->cnt2, n, N * 4, cudaMemcpyHostToDevice, sim->stream));
   const long long tmin = std::max<long long>(t_done, 1);
-  for (size_t c = 0; c < N; ++c) {
-    if (s[c] != 1 && s[c] != -1) return fail(AC_ERR_ARG, "spin of cell %zu is %d (must be +-1)", c, s[c]);
-    if (t[c] < tmin || t[c] >= kTickLimit)
-      return fail(AC_ERR_ARG, "tick of cell %zu is %lld, outside [%lld, 2^61)", c, (long long)t[c], tmin);
-    packed[c] = ((uint64_t)t[c] << 1) | (s[c] > 0 ? 1u : 0u);
-  }
-  AC_CUDA(cudaMemcpyAsync(sim->key, packed.data(), N * 8, cudaMemcpyHostToDevice, sim->stream));
-  AC_CUDA(cudaMemcpyAsync(sim->cnt, n, N * 4, cudaMemcpyHostToDevice, sim->stream));
+  unsigned long long bad = ~0ull;
+  AC_CUDA(cudaMemcpyAsync(sim->d_red, &bad, 8, cudaMemcpyHostToDevice, sim->stream));
+  AC_CUDA(ac::launch_validate(sim->stage8, (const long long*)sim->key2, N, tmin, kTickLimit, sim->d_red,
+                              sim->stream));
+  AC_CUDA(cudaMemcpyAsync(&bad, sim->d_red, 8, cudaMemcpyDeviceToHost, sim->stream));
+  AC_CUDA(cudaStreamSynchronize(sim->stream));
+  if (bad != ~0ull)
+    return fail(AC_ERR_ARG, "cell %llu: spin %d / tick %lld (spins must be +-1, ticks in [%lld, 2^61))",
+                bad, (int)s[bad], (long long)t[bad], tmin);
+  const ac::LatDesc d = sim->host_desc(t_done, 0);
+  AC_CUDA(ac::launch_pack(&d, sim->stage8, (const long long*)sim->key2, sim->cnt2, sim->stream));
   AC_CUDA(cudaStreamSynchronize(sim->stream));
   sim->t_done = t_done;
   return AC_OK;

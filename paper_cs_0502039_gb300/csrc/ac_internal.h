@@ -97,6 +97,8 @@ cudaError_t launch_tb(const LatDesc* d_desc, int nlat, int total_tiles, int regi
                       DevCounters* ctr, cudaStream_t s);
 cudaError_t launch_count_range_batch(const LatDesc* d_desc, int nlat, unsigned* d_out2n, cudaStream_t s);
 int tb_grid(int region);   // resident CTAs of the temporal-blocked kernel
+cudaError_t launch_validate(const int8_t* s_in, const long long* t_in, size_t N, long long tmin, long long tmax,
+                            unsigned long long* d_first_bad, cudaStream_t st);
 cudaError_t launch_exp_ticks(const uint32_t* x, unsigned long long* out, long long n, cudaStream_t s);
 cudaError_t launch_philox(unsigned long long seed, const uint32_t* c, const uint32_t* k, uint32_t w2,
                           uint32_t* out4, long long n, cudaStream_t s);

@@ -994,6 +994,15 @@ __global__ void pack_kernel(LatDesc L, const int8_t* s, const long long* t, cons
   }
 }
 
+// first cell (lowest index) whose spin is not +-1 or whose tick is outside [tmin, tmax)
+__global__ void validate_kernel(const int8_t* s, const long long* t, size_t N, long long tmin, long long tmax,
+                                unsigned long long* first_bad) {
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+    const bool ok = (s[c] == 1 || s[c] == -1) && t[c] >= tmin && t[c] < tmax;
+    if (!ok) atomicMin(first_bad, (unsigned long long)c);
+  }
+}
+
 __global__ void exp_ticks_kernel(const uint32_t* x, unsigned long long* out, long long n, uint32_t two) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -1197,6 +1206,12 @@ int tb_grid(int region) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms <= 0) sms = 1;
   return sms * (region <= 96 ? TbCfg<96>::MIN_CTAS : TbCfg<128>::MIN_CTAS);
+}
+
+cudaError_t launch_validate(const int8_t* s_in, const long long* t_in, size_t N, long long tmin, long long tmax,
+                            unsigned long long* d_first_bad, cudaStream_t st) {
+  validate_kernel<<<grid_for(N, 256), 256, 0, st>>>(s_in, t_in, N, tmin, tmax, d_first_bad);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_exp_ticks(const uint32_t* x, unsigned long long* out, long long n, cudaStream_t s) {
