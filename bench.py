@@ -394,8 +394,9 @@ def main():
             e = torch.tensor([float(e_ev)], device="cuda", dtype=torch.float64)
             dist.all_reduce(e)
             e_ev = e.item()
-        e2e = {"value": e_ev / e_dt, "unit": "events/s", "h2d_bytes_per_step": 12 * N * len(sims),
-               "d2h_bytes_per_step": 12 * N * len(sims), "steps": e_steps,
+        # per lattice and direction: spins int8 + ticks int64 + counts uint32 = 13 bytes per cell
+        e2e = {"value": e_ev / e_dt, "unit": "events/s", "h2d_bytes_per_step": 13 * N * len(sims),
+               "d2h_bytes_per_step": 13 * N * len(sims), "steps": e_steps,
                "path": "ac_load_state(host) + run + ac_read_state(host) per lattice"}
 
     extra, batch, served = {}, None, None
