@@ -581,6 +581,7 @@ struct TbCfg {
   static constexpr int GROUPS = 8;                // ... in one of 8 row bands
   static constexpr int ROWS = RW / GROUPS;        // rows per band (12 or 16)
   static constexpr int NT = PAIRS * GROUPS;       // 384 or 512 threads = 4 * RW
+  static constexpr int LSTRIDE = NT / RW;         // load / store mapping: rows per column sweep
   // enabled cells form an independent set of the scanned rectangle (at most
   // (RW-2) x (RW-2) cells): the list holds every one of them, so a round always
   // commits all enabled cells and every tile advances exactly R synchronous rounds
@@ -676,29 +677,33 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     const int gc = wrap_index(g.c0 - D + lj, L.cols, shc, 2);
     bool over = false;
     __syncthreads();
+    // the thread's own-tile cells' count offsets at load (the write-back uses the same
+    // column and rows, so its difference is the tile's committed arrivals)
+    unsigned own_before = 0;
+    const bool own_col = lj >= D && lj < D + g.w;
     if (lj < RC) {
-      // eight rows per batch: all global loads of a batch are in flight together
-      for (int i0 = li0; i0 < RH; i0 += 32) {
-        unsigned cvs[8];
+      // all of the thread's global loads are in flight together (one batch)
+      constexpr int MROWS = RW / Cfg::LSTRIDE;
+      unsigned cvs[MROWS];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int i = i0 + 4 * m;
-          if (i < RH) {
-            int shr;
-            const int gr = wrap_index(g.r0 - D + i, L.rows, shr, 2);
-            const size_t gi = (size_t)gr * L.cols + gc;
-            cp_async8(&K[i * RW + lj], &key_in[gi]);
-            cvs[m] = cnt_in[gi];
-          }
+      for (int m = 0; m < MROWS; ++m) {
+        const int i = li0 + Cfg::LSTRIDE * m;
+        if (i < RH) {
+          int shr;
+          const int gr = wrap_index(g.r0 - D + i, L.rows, shr, 2);
+          const size_t gi = (size_t)gr * L.cols + gc;
+          cp_async8(&K[i * RW + lj], &key_in[gi]);
+          cvs[m] = cnt_in[gi];
         }
+      }
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int i = i0 + 4 * m;
-          if (i < RH) {
-            const unsigned cv = cvs[m] - base;
-            over |= cv > cap;
-            C[i * RW + lj] = (unsigned short)cv;
-          }
+      for (int m = 0; m < MROWS; ++m) {
+        const int i = li0 + Cfg::LSTRIDE * m;
+        if (i < RH) {
+          const unsigned cv = cvs[m] - base;
+          over |= cv > cap;
+          C[i * RW + lj] = (unsigned short)cv;
+          if (own_col && i >= D && i < D + g.h) own_before += cv;
         }
       }
     }
@@ -714,7 +719,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     __syncthreads();
     if (edge) {   // halo cells from across the torus seam: key +-2 (one tick of tie order)
       if (lj < RC) {
-        for (int i = li0; i < RH; i += 4) {
+        for (int i = li0; i < RH; i += Cfg::LSTRIDE) {
           int shr;
           wrap_index(g.r0 - D + i, L.rows, shr, 2);
           if (shr + shc) K[i * RW + lj] += (unsigned long long)(long long)(shr + shc);
@@ -768,17 +773,20 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         mask &= valid;
         scanned += (unsigned long long)__popc(valid);
       }
+      // exclusive prefix of the per-lane counts (< 32) from five independent ballots
       const int cnt = __popc(mask);
-      int incl = cnt;
+      const unsigned lt = (1u << lane) - 1u;
+      int excl = 0, total = 0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += v;
+      for (int b = 0; b < 5; ++b) {
+        const unsigned bal = __ballot_sync(kFull, (cnt >> b) & 1);
+        excl += __popc(bal & lt) << b;
+        total += __popc(bal) << b;
       }
       int wbase = 0;
-      if (lane == 31 && incl) wbase = (int)atomicAdd(&n_en[cur], (unsigned)incl);
-      wbase = __shfl_sync(kFull, wbase, 31);
-      int off = wbase + incl - cnt;
+      if (lane == 0 && total) wbase = (int)atomicAdd(&n_en[cur], (unsigned)total);
+      wbase = __shfl_sync(kFull, wbase, 0);
+      int off = wbase + excl;
       while (mask) {
         const int b = __ffs(mask) - 1;
         mask &= mask - 1;
@@ -839,29 +847,23 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     // ---- write the tile back; count its arrivals; is anything left before t_end?
     bool live = false;
     unsigned long long ev = 0;
-    if (lj >= D && lj < D + g.w) {
-      for (int i0 = li0; i0 < g.h; i0 += 32) {
-        unsigned old_n[8];
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int i = i0 + 4 * m;
-          if (i < g.h) old_n[m] = cnt_in[(size_t)(g.r0 + i) * L.cols + g.c0 + lj - D];
-        }
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int i = i0 + 4 * m;
-          if (i < g.h) {
-            const int si = (i + D) * RW + lj;
-            const size_t gi = (size_t)(g.r0 + i) * L.cols + g.c0 + lj - D;
-            const unsigned long long kk = K[si];
-            const unsigned nn = base + C[si];
-            ev += (unsigned long long)(nn - old_n[m]);
-            key_out[gi] = kk;
-            cnt_out[gi] = nn;
-            live |= kk < t2;
-          }
-        }
+    if (own_col) {
+      // own rows i = li0 + 4m - D for region rows li0 + 4m in [D, D + h): the same cells
+      // whose offsets own_before summed at load
+      unsigned own_after = 0;
+      for (int ri = li0; ri < D + g.h; ri += Cfg::LSTRIDE) {
+        if (ri < D) continue;
+        const int i = ri - D;
+        const int si = ri * RW + lj;
+        const size_t gi = (size_t)(g.r0 + i) * L.cols + g.c0 + lj - D;
+        const unsigned long long kk = K[si];
+        const unsigned c16 = C[si];
+        own_after += c16;
+        key_out[gi] = kk;
+        cnt_out[gi] = base + c16;
+        live |= kk < t2;
       }
+      ev = (unsigned long long)(own_after - own_before);
     }
     for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
     if (lane == 0 && ev) {
