@@ -348,7 +348,7 @@ def main():
     if kern == ac.AC_KERNEL_BLOCKED:
         kname = f"blocked_kernel<{args.lb}>"
     elif args.rounds > 1:
-        kname = f"tb_kernel<{96 if args.rounds <= 12 else 128}>"
+        kname = f"tb_kernel<{96 if args.rounds <= 12 else 128}> rounds={args.rounds}"
     else:
         kname = f"round_kernel<{args.lb}>"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
