@@ -6,9 +6,13 @@ Workload (one step): the 4096 x 4096 periodic Ising torus at beta = 0.30,
 0.4407 and 0.60 (J = 1, h = 0, random +-1 initial spins from seed 7, Poisson
 rate 1 per cell, 2^32 ticks per unit time), each initialised on the device and
 run to T = 50 -- about 2.5e9 committed arrivals per step, all bit-exact against
-the serial oracle (tests/).  The three lattices run in one graph-captured
-launch of the blocked persistent kernel.  The state (3 x 201 MB) is larger than
-the 129 MB L2, so no flush is needed between steps.
+the serial oracle (tests/).  The kernel and its tuning are picked by the
+autotuner (on a GB300: the temporal-blocked round kernel).  The state
+(3 x 201 MB) is larger than the 129 MB L2, so no flush is needed between steps.
+
+Other workloads (--workload): batch (512 lattices, batched against plain calls),
+serve (a replayed request stream) and frames (snapshot frames at K dt, B slots,
+against the same run without frames).
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
 host cores on a bounded prefix of the same workload.
@@ -49,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the per-kernel side measurements")
-    ap.add_argument("--workload", default="ising4096", choices=["ising4096", "batch", "serve"],
+    ap.add_argument("--workload", default="ising4096", choices=["ising4096", "batch", "serve", "frames"],
                     help="ising4096: the headline step; batch: the 512-lattice batch only; serve: the request stream")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the replayed request stream")
     ap.add_argument("--single", action="store_true",
@@ -237,14 +241,18 @@ def main():
         return run_reference(args)
     if args.single:
         return run_single(args)
-    if args.workload in ("batch", "serve"):
+    if args.workload in ("batch", "serve", "frames"):
         import torch
         torch.cuda.set_device(0)
         import __graft_entry__
         __graft_entry__.build()
         import paper_cs_0502039_gb300 as ac
-        res = batch_measurement(ac, args.rounds, args.lb) if args.workload == "batch" else \
-            serve_measurement(ac, args.serve_seconds, args.rounds, args.lb)
+        if args.workload == "batch":
+            res = batch_measurement(ac, args.rounds, args.lb)
+        elif args.workload == "serve":
+            res = serve_measurement(ac, args.serve_seconds, args.rounds, args.lb)
+        else:
+            res = frames_measurement(ac, args.rounds, args.lb)
         print(json.dumps({"workload": args.workload, **res}), flush=True)
         return 0
 
@@ -505,6 +513,54 @@ def serve_measurement(ac, seconds=10.0, rounds=8, lb=64):
     dt = time.perf_counter() - t0
     out["serial_sample"] = {"requests": len(sample), "events_per_s": sev / dt, "seconds": dt}
     out["served_over_serial"] = out["events_per_s"] / out["serial_sample"]["events_per_s"]
+    return out
+
+
+def frames_measurement(ac, rounds=6, lb=64):
+    """Snapshot frames (Fig. 3.7) on the 4096^2 beta = 0.4407 lattice to T = 50: arrivals per second
+    of the run with frames every dt time units in B slots (frames written by the kernels and dropped,
+    or copied to the host), against the same run without frames.  The trajectory is the same in
+    every case (tests/test_gpu_frames.py); what changes is the lag bound of B dt time units."""
+    import torch
+    w = WORKLOAD
+    out = {"lattice": f"{w['rows']}x{w['cols']}", "beta": 0.4407, "T": w["T"], "rounds": rounds, "cases": []}
+    with ac.Sim(w["rows"], w["cols"], 0.4407, w["J"], w["h"], w["seed"], init=w["init"], kernel=ac.AC_KERNEL_ROUND,
+                Lb=lb, rounds=rounds) as sim:
+        def timed(dt_units, B, mode):
+            best, ev = None, 0
+            for _ in range(2):           # the first pass warms up
+                sim.reset(w["seed"], w["init"])
+                if B:
+                    sim.configure_frames(int(dt_units * T32), 0, B)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if not B:
+                    sim.run_until(w["T"])
+                elif mode == "host":
+                    got = [0]
+
+                    def fn(K, ptr, n):
+                        got[0] += 1
+                    ac.ac_run_until_frames(sim.handle, w["T"] * T32, fn, on_host=True)
+                else:
+                    ac.ac_run_until_frames(sim.handle, w["T"] * T32, None)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                ev = sim.stats()["events"]
+                best = dt if best is None else min(best, dt)
+            return ev, best
+
+        ev0, t0 = timed(0, 0, None)
+        out["no_frames"] = {"events": ev0, "seconds": t0, "events_per_s": ev0 / t0}
+        # the lag bound B dt (in mean interarrival times), as in the paper's bounded-lag experiment
+        for lag, B, mode in [(0.3, 1, "drop"), (1.0, 1, "drop"), (2.0, 1, "drop"), (4.0, 1, "drop"),
+                             (8.0, 1, "drop"), (16.0, 1, "drop"), (1.0, 4, "drop"), (4.0, 4, "drop"),
+                             (16.0, 4, "drop"), (16.0, 16, "drop"), (4.0, 4, "host")]:
+            dt_units = lag / B
+            ev, t = timed(dt_units, B, mode)
+            assert ev == ev0
+            out["cases"].append({"lag": lag, "dt": dt_units, "B": B, "frames": int(w["T"] / dt_units), "mode": mode,
+                                 "seconds": t, "events_per_s": ev / t, "relative": t0 / t})
     return out
 
 

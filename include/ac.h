@@ -42,6 +42,7 @@
 #ifndef AC_H
 #define AC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -171,6 +172,42 @@ ac_status ac_round_history(const ac_sim* sim, uint64_t* counts, int32_t cap, int
  * the trajectory restart).  No allocation.  Errors: AC_ERR_ARG, AC_ERR_CUDA.
  */
 ac_status ac_reset(ac_sim* sim, uint64_t seed, int32_t init);
+
+/*
+ * Snapshot frames at regular times K * dt (Sec. 3, "Generating the output",
+ * Fig. 3.7).  Frame K is the array of all spins (int8 +-1, row-major) after every
+ * arrival with tick <= K * dt_ticks has been committed and none later -- the
+ * figure stores a subarray's image before it processes its first event later
+ * than K dt.  (With ac_run_until's convention, frame K is the state after
+ * ac_run_until_ticks(K * dt_ticks + 1).)  Frames are written by the kernels'
+ * commits while the run proceeds; the library keeps B frame slots (the figure's
+ * output buffer of B frames, B * rows * cols bytes of device memory) and never
+ * lets a cell get further ahead than the B frames after the oldest one not yet
+ * handed out (the figure's lag bound, between (B-1) dt and B dt).  Works with
+ * every kernel and tuning; the trajectory and the final state do not change.
+ *
+ * ac_frames_configure: frames K0, K0+1, ... every dt_ticks ticks, B slots in
+ *   [1, AC_MAX_FRAMES]; B = 0 turns frames off and frees the slots.  Needs
+ *   dt_ticks >= 1, (B + 1) * dt_ticks <= 2^60, K0 * dt_ticks <= 2^60 and frame K0
+ *   not before the state (K0 * dt_ticks + 1 >= the last t_end).  Replaces an
+ *   earlier configuration.  ac_reset and ac_load_state turn frames off.
+ *   Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
+ * ac_run_until_frames: as ac_run_until_ticks, and calls fn(user, K, frame, n)
+ *   on the calling thread, in increasing K, once for every frame K with
+ *   K * dt_ticks < t_end that was not handed out before.  `frame` points to
+ *   n = rows * cols spins: device memory when on_host == 0 (the stream is
+ *   synchronised before the call; the slot is reused after fn returns, so work
+ *   that reads it must finish inside fn), else a library-owned pinned host buffer
+ *   valid until fn returns.  fn may be NULL (frames are dropped).  While frames
+ *   are configured, ac_run_until and ac_run_until_ticks behave as this call with
+ *   fn = NULL, and ac_batch_run_until refuses the handle (AC_ERR_ARG).
+ * ac_frames_status: next frame to be handed out, B and dt_ticks (B = 0: off).
+ */
+#define AC_MAX_FRAMES 64
+typedef void (*ac_frame_fn)(void* user, int64_t K, const int8_t* frame, size_t n);
+ac_status ac_frames_configure(ac_sim* sim, int64_t dt_ticks, int64_t K0, int32_t B);
+ac_status ac_run_until_frames(ac_sim* sim, int64_t t_end, ac_frame_fn fn, void* user, int32_t on_host);
+ac_status ac_frames_status(const ac_sim* sim, int64_t* next_K, int32_t* B, int64_t* dt_ticks);
 
 /* Tuning and verification options (ac_set_option):
  *   AC_OPT_WATCHDOG_NS   blocked kernel: no-progress limit in ns before the run

@@ -25,6 +25,8 @@ Pins (tests/test_oracle_*.py, all CPU):
                      transient P0 exp(QT)), Poisson(T) counts, beta = 0
                      closed form, Onsager energy and magnetisation.
   time_rounds     -- round-1 fraction 1/5, long-run fraction ~0.121 (Sec. 4).
+  frames          -- per-cell spin histories of the brute-force simulator read
+                     at each frame time, including an arrival exactly at K dt.
   observables, checksum -- brute-force recomputation in numpy.
 """
 from __future__ import annotations
@@ -169,6 +171,22 @@ def run(state: State, thr: np.ndarray, seed: int, t_end: int) -> int:
     if ev < 0:
         raise MemoryError("oracle heap allocation failed")
     return int(ev)
+
+
+def frames(state: State, thr: np.ndarray, seed: int, dt_ticks: int, K0: int, count: int) -> np.ndarray:
+    """Snapshot frames K0 .. K0+count-1 (Sec. 3, "Generating the output", Fig. 3.7).
+
+    Frame K is every cell's spin after all of its arrivals with tick <= K * dt_ticks:
+    the figure stores a subarray's image before it processes the first event later
+    than K dt (reading R10).  With ``run``'s strict end (tick < t_end) that is the
+    state after ``run(.., K * dt_ticks + 1)``.  ``state`` must not be past frame K0
+    (it was last run to a t_end <= K0 * dt_ticks + 1).  Advances ``state`` in place
+    to the last frame; returns an int8 array of shape (count, rows * cols)."""
+    out = np.zeros((count, state.rows * state.cols), dtype=np.int8)
+    for i in range(count):
+        run(state, thr, seed, (K0 + i) * dt_ticks + 1)
+        out[i] = state.s
+    return out
 
 
 def simulate(rows: int, cols: int, beta: float, J: float, h: float, seed: int, T: float,

@@ -53,7 +53,12 @@ class ac_stats_t(ctypes.Structure):
 EXPORTS = ["ac_create", "ac_set_stream", "ac_configure", "ac_run_until", "ac_run_until_ticks",
            "ac_read_state", "ac_read_state_device", "ac_load_state", "ac_stats", "ac_round_history",
            "ac_destroy", "ac_last_error", "ac_thresholds", "ac_reset", "ac_set_option", "ac_batch_create", "ac_batch_run_until",
-           "ac_dev_exp_ticks", "ac_dev_philox", "ac_run_blocked_static"]
+           "ac_dev_exp_ticks", "ac_dev_philox", "ac_run_blocked_static", "ac_frames_configure",
+           "ac_run_until_frames", "ac_frames_status"]
+
+AC_MAX_FRAMES = 64
+# void (*ac_frame_fn)(void* user, int64_t K, const int8_t* frame, size_t n)
+FRAME_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t)
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -83,6 +88,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ac_dev_exp_ticks": ([P, P, I64], I32),
         "ac_dev_philox": ([U64, P, P, ctypes.c_uint32, P, I64], I32),
         "ac_run_blocked_static": ([I32, I32, D, D, D, U64, P, P, I64, P], I32),
+        "ac_frames_configure": ([P, I64, I64, I32], I32),
+        "ac_run_until_frames": ([P, I64, FRAME_FN, P, I32], I32),
+        "ac_frames_status": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -211,6 +219,36 @@ def ac_run_blocked_static(rows: int, cols: int, beta: float, J: float, h: float,
                                       int(t_end), stream))
 
 
+def ac_frames_configure(sim: int, dt_ticks: int, K0: int, B: int) -> None:
+    _check(_lib.ac_frames_configure(sim, int(dt_ticks), int(K0), int(B)))
+
+
+def ac_run_until_frames(sim: int, t_end: int, fn=None, on_host: bool = True) -> None:
+    """fn(K, ptr, n) is called for every completed frame; ptr is a host address (on_host) or a
+    device address valid only during the call.  Exceptions raised by fn are re-raised here."""
+    errors = []
+
+    def _tramp(user, K, ptr, n):
+        if errors:
+            return
+        try:
+            fn(int(K), int(ptr), int(n))
+        except BaseException as e:  # noqa: BLE001 -- re-raised after the C call returns
+            errors.append(e)
+
+    cb = FRAME_FN(_tramp) if fn is not None else FRAME_FN()
+    status = _lib.ac_run_until_frames(sim, int(t_end), cb, None, 1 if on_host else 0)
+    if errors:
+        raise errors[0]
+    _check(status)
+
+
+def ac_frames_status(sim: int) -> tuple[int, int, int]:
+    K, B, dt = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+    _check(_lib.ac_frames_status(sim, ctypes.byref(K), ctypes.byref(B), ctypes.byref(dt)))
+    return K.value, B.value, dt.value
+
+
 # --------------------------------------------------------------- convenience
 class Sim:
     """One lattice handle (owns its device memory; freed on close / GC)."""
@@ -263,6 +301,30 @@ class Sim:
 
     def round_history(self) -> np.ndarray:
         return ac_round_history(self.handle)
+
+    def configure_frames(self, dt_ticks: int, K0: int = 0, B: int = 4) -> None:
+        """Snapshot frames K0, K0+1, ... at ticks K * dt_ticks, B frame slots (0 = off)."""
+        ac_frames_configure(self.handle, dt_ticks, K0, B)
+
+    def run_until_frames(self, t_end: int, on_frame=None) -> list:
+        """Run to tick t_end.  Each completed frame K is passed as (K, int8 array of rows*cols
+        spins) to on_frame, or collected and returned when on_frame is None."""
+        got = []
+        n_cells = self.rows * self.cols
+
+        def _fn(K, ptr, n):
+            assert n == n_cells
+            frame = np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctypes.c_int8)), shape=(n,)).copy()
+            if on_frame is None:
+                got.append((K, frame))
+            else:
+                on_frame(K, frame)
+
+        ac_run_until_frames(self.handle, t_end, _fn, on_host=True)
+        return got
+
+    def frames_status(self) -> tuple[int, int, int]:
+        return ac_frames_status(self.handle)
 
     def close(self) -> None:
         if self.handle:

@@ -98,6 +98,11 @@ struct ac_sim {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   long long t_done = 0;
+  // snapshot frames (Fig. 3.7): f_B slots of ncells() spins; frames [f_K, f_K + f_B) open
+  int8_t* frames = nullptr;
+  int8_t* frame_host = nullptr;             // pinned copy handed to host callbacks
+  int f_B = 0;
+  long long f_dt = 0, f_K = 0;
   // accumulated statistics
   unsigned long long events = 0, rounds = 0, launches = 0, scanned = 0, enabled = 0, visits = 0,
                      polls = 0, global_rounds = 0, enabled_r1 = 0;
@@ -130,6 +135,14 @@ struct ac_sim {
     d.t_end = t_end;
     d.t2 = 2ull * (unsigned long long)t_end;
     d.drop_publish = drop_publish;
+    if (f_B > 0) {
+      d.frames = reinterpret_cast<signed char*>(frames);
+      d.f_t0 = f_K * f_dt;
+      d.f_dt = f_dt;
+      d.f_open = f_B;
+      d.f_slot0 = (int)(f_K % f_B);
+      d.f_B = f_B;
+    }
     return d;
   }
 };
@@ -229,6 +242,8 @@ void free_sim(ac_sim* s) {
   cudaFree(s->d_tile_done);
   cudaFree(s->d_hist);
   cudaFree(s->d_red);
+  cudaFree(s->frames);
+  if (s->frame_host) cudaFreeHost(s->frame_host);
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
   delete s;
@@ -383,7 +398,7 @@ ac_status run_tb(ac_sim* s, long long t_end) {
   int launch_idx = 0;
   for (;;) {
     for (int i = 0; i < chunk; ++i) {
-      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, D, s->d_ctr, s->stream));
+      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, D, s->d_ctr, s->stream, s->f_B > 0));
       ++launch_idx;
     }
     ac::DevCounters cc{};
@@ -626,6 +641,76 @@ ac_status batch_run_tb(int32_t n, ac_sim* const* sims, const int64_t* t_end, Bat
   return AC_OK;
 }
 
+ac_status run_core(ac_sim* sim, long long t_end) {
+  unsigned long long before = 0, after = 0;
+  ac_status st = read_event_counter(sim, &before);
+  if (st != AC_OK) return st;
+  st = (sim->cfg.kernel == ac::kKernelRound) ? run_round(sim, t_end) : run_blocked(sim, t_end);
+  if (st != AC_OK) return st;
+  st = read_event_counter(sim, &after);
+  if (st != AC_OK) return st;
+  sim->events += after - before;
+  sim->t_done = t_end;
+  return AC_OK;
+}
+
+void frames_off(ac_sim* s) {
+  if (s->frames) cudaFree(s->frames);
+  s->frames = nullptr;
+  s->f_B = 0;
+  s->f_dt = 0;
+  s->f_K = 0;
+}
+
+// Snapshot frames (Fig. 3.7).  Frames [f_K, f_K + B) are open.  Commits are capped at
+// tick <= (f_K + B) dt -- the figure's lag bound: no cell gets more than B frames ahead
+// of the oldest frame not yet handed out -- so every frame a commit must write is
+// open.  After the capped run the open frames are complete (all arrivals <= K dt
+// committed); each is handed to fn in order, its slot is reopened for frame K + B and
+// filled where no later commit will write it.
+ac_status run_frames(ac_sim* s, long long t_end, ac_frame_fn fn, void* user, int on_host) {
+  const size_t N = s->ncells();
+  if (fn && on_host && !s->frame_host) {
+    if (cudaMallocHost(&s->frame_host, N) != cudaSuccess) {
+      cudaGetLastError();
+      s->frame_host = nullptr;
+      return fail(AC_ERR_OOM, "pinned frame buffer (%zu bytes) allocation failed", N);
+    }
+  }
+  for (;;) {
+    const long long W = s->f_K + s->f_B;
+    const long long cap = std::min<long long>(t_end, W * s->f_dt + 1);
+    if (cap > s->t_done) {
+      ac_status st = run_core(s, cap);
+      if (st != AC_OK) return st;
+    }
+    const long long first = s->f_K;
+    while (s->f_K < W && s->f_K * s->f_dt + 1 <= s->t_done) {
+      const int8_t* slot = s->frames + (size_t)(s->f_K % s->f_B) * N;
+      if (fn) {
+        if (on_host) {
+          AC_CUDA(cudaMemcpyAsync(s->frame_host, slot, N, cudaMemcpyDeviceToHost, s->stream));
+          AC_CUDA(cudaStreamSynchronize(s->stream));
+          fn(user, s->f_K, s->frame_host, N);
+        } else {
+          AC_CUDA(cudaStreamSynchronize(s->stream));
+          fn(user, s->f_K, slot, N);
+        }
+      }
+      ++s->f_K;
+    }
+    if (s->f_K > first) {
+      const ac::LatDesc d = s->host_desc(s->t_done, 0);
+      AC_CUDA(ac::launch_frames_fill(&d, W, (int)(s->f_K - first), s->stream));
+    }
+    // done when the run reached t_end and the next frame is not complete (a frame just
+    // reopened and already complete -- every cell past its tick -- is handed out first)
+    if (s->t_done >= t_end && s->f_K * s->f_dt + 1 > s->t_done) break;
+  }
+  AC_CUDA(cudaStreamSynchronize(s->stream));
+  return AC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -680,15 +765,52 @@ ac_status ac_run_until_ticks(ac_sim* sim, int64_t t_end) {
   if (t_end < sim->t_done) return fail(AC_ERR_ARG, "t_end %lld is below the previous t_end %lld",
                                        (long long)t_end, sim->t_done);
   if (t_end >= kTickLimit) return fail(AC_ERR_ARG, "t_end must be < 2^61");
-  unsigned long long before = 0, after = 0;
-  ac_status st = read_event_counter(sim, &before);
-  if (st != AC_OK) return st;
-  st = (sim->cfg.kernel == ac::kKernelRound) ? run_round(sim, t_end) : run_blocked(sim, t_end);
-  if (st != AC_OK) return st;
-  st = read_event_counter(sim, &after);
-  if (st != AC_OK) return st;
-  sim->events += after - before;
-  sim->t_done = t_end;
+  if (sim->f_B > 0) return run_frames(sim, t_end, nullptr, nullptr, 0);
+  return run_core(sim, t_end);
+}
+
+ac_status ac_frames_configure(ac_sim* sim, int64_t dt_ticks, int64_t K0, int32_t B) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  if (B == 0) {
+    frames_off(sim);
+    return AC_OK;
+  }
+  if (B < 1 || B > AC_MAX_FRAMES) return fail(AC_ERR_ARG, "B must be in [1, %d] (or 0 to turn frames off)", AC_MAX_FRAMES);
+  if (dt_ticks < 1 || dt_ticks > (kTickLimit / 2) / (B + 1)) return fail(AC_ERR_ARG, "dt_ticks must be in [1, 2^60 / (B + 1)]");
+  if (K0 < 0 || K0 > (kTickLimit / 2) / dt_ticks) return fail(AC_ERR_ARG, "K0 must be >= 0 and K0 * dt_ticks < 2^60");
+  if (K0 * dt_ticks + 1 < sim->t_done)
+    return fail(AC_ERR_ARG, "frame K0 = %lld (tick %lld) is before the state's time %lld", (long long)K0,
+                (long long)(K0 * dt_ticks), sim->t_done);
+  frames_off(sim);
+  const size_t N = sim->ncells();
+  if (cudaMalloc(&sim->frames, (size_t)B * N) != cudaSuccess) {
+    cudaGetLastError();
+    sim->frames = nullptr;
+    return fail(AC_ERR_OOM, "%d frames of %zu cells: allocation failed", B, N);
+  }
+  sim->f_B = B;
+  sim->f_dt = dt_ticks;
+  sim->f_K = K0;
+  const ac::LatDesc d = sim->host_desc(sim->t_done, 0);
+  AC_CUDA(ac::launch_frames_fill(&d, K0, B, sim->stream));
+  AC_CUDA(cudaStreamSynchronize(sim->stream));
+  return AC_OK;
+}
+
+ac_status ac_run_until_frames(ac_sim* sim, int64_t t_end, ac_frame_fn fn, void* user, int32_t on_host) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  if (sim->f_B <= 0) return fail(AC_ERR_ARG, "no frames configured (ac_frames_configure)");
+  if (t_end < sim->t_done) return fail(AC_ERR_ARG, "t_end %lld is below the previous t_end %lld",
+                                       (long long)t_end, sim->t_done);
+  if (t_end >= kTickLimit) return fail(AC_ERR_ARG, "t_end must be < 2^61");
+  return run_frames(sim, t_end, fn, user, on_host);
+}
+
+ac_status ac_frames_status(const ac_sim* sim, int64_t* next_K, int32_t* B, int64_t* dt_ticks) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  if (next_K) *next_K = sim->f_K;
+  if (B) *B = sim->f_B;
+  if (dt_ticks) *dt_ticks = sim->f_dt;
   return AC_OK;
 }
 
@@ -773,6 +895,7 @@ ac_status ac_load_state(ac_sim* sim, const int8_t* s, const int64_t* t, const ui
   AC_CUDA(ac::launch_pack(&d, sim->stage8, (const long long*)sim->key2, sim->cnt2, sim->stream));
   AC_CUDA(cudaStreamSynchronize(sim->stream));
   sim->t_done = t_done;
+  frames_off(sim);
   return AC_OK;
 }
 
@@ -835,6 +958,7 @@ ac_status ac_reset(ac_sim* sim, uint64_t seed, int32_t init) {
   if (sim->d_hist) AC_CUDA(cudaMemsetAsync(sim->d_hist, 0, (size_t)sim->hist_cap * 8, sim->stream));
   AC_CUDA(cudaStreamSynchronize(sim->stream));
   sim->t_done = 0;
+  frames_off(sim);
   sim->events = sim->rounds = sim->launches = sim->scanned = sim->enabled = sim->visits = sim->polls = 0;
   sim->global_rounds = sim->enabled_r1 = 0;
   sim->device_ms = 0.0;
@@ -896,6 +1020,7 @@ ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_en
   if (n <= 0 || !sims || !t_end) return fail(AC_ERR_ARG, "n > 0, sims and t_end are required");
   for (int i = 0; i < n; ++i) {
     if (!sims[i]) return fail(AC_ERR_ARG, "sims[%d] is NULL", i);
+    if (sims[i]->f_B > 0) return fail(AC_ERR_ARG, "sims[%d] has snapshot frames: run it with ac_run_until_frames", i);
     if (sims[i]->cfg.lb != sims[0]->cfg.lb) return fail(AC_ERR_ARG, "all handles must share a tile side");
     if (sims[i]->stream != sims[0]->stream) return fail(AC_ERR_ARG, "all handles must share a stream");
     if (t_end[i] < sims[i]->t_done) return fail(AC_ERR_ARG, "t_end[%d] is below its previous t_end", i);

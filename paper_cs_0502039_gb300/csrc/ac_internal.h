@@ -34,6 +34,13 @@ struct LatDesc {
   unsigned long long t2;     // 2 * t_end: key < t2  <=>  tick < t_end
   int drop_publish;          // verification hook: suppress edge-word publication
   unsigned int two;          // the constant 2, opaque to the compiler (see exp_ticks)
+  // Snapshot frames (Fig. 3.7): f_open frames are open, the f-th at tick f_t0 + f * f_dt
+  // in slot (f_slot0 + f) % f_B of `frames` (f_B slots of rows * cols int8 spins).
+  // A commit of an arrival at tick ta whose next arrival is at tick tn writes the new
+  // spin into every open frame whose tick T satisfies ta <= T < tn.  f_open = 0: off.
+  signed char* frames;
+  long long f_t0, f_dt;
+  int f_open, f_slot0, f_B;
 };
 
 // Device counters of one run call (zeroed by the host before the call).
@@ -93,8 +100,12 @@ cudaError_t launch_pack(const LatDesc* host_desc, const int8_t* s_in, const long
 // Launch of the temporal-blocked round kernel.  The launch number (which fixes the
 // ping-pong parity) is kept on the device in ctr->seq, so every launch of a run has
 // the same arguments and a sequence of launches can be captured in a CUDA graph.
+// frames: the lattices have open snapshot frames (the kernel variant that writes them).
 cudaError_t launch_tb(const LatDesc* d_desc, int nlat, int total_tiles, int region, int halo, int rounds,
-                      DevCounters* ctr, cudaStream_t s);
+                      DevCounters* ctr, cudaStream_t s, bool frames = false);
+// Frames [K, K + count) were just opened: write each cell's spin into those whose tick
+// lies before the cell's next arrival (later commits write the others).
+cudaError_t launch_frames_fill(const LatDesc* host_desc, long long K, int count, cudaStream_t s);
 cudaError_t launch_count_range_batch(const LatDesc* d_desc, int nlat, unsigned* d_out2n, cudaStream_t s);
 int tb_grid(int region);   // resident CTAs of the temporal-blocked kernel
 cudaError_t launch_validate(const int8_t* s_in, const long long* t_in, size_t N, long long tmin, long long tmax,

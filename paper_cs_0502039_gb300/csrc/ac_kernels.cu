@@ -70,6 +70,54 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// Snapshot frames (Fig. 3.7).  Frame K holds every cell's spin after all of its
+// arrivals with tick <= K dt (the figure stores the image before it processes the
+// first event later than K dt).  The commit of an arrival at tick ta, whose next
+// arrival is at tick tn, is therefore the last one <= T for every frame tick T in
+// [ta, tn): it writes the new spin there.  The open frames are evenly spaced.
+struct FrameView {
+  signed char* frames;
+  unsigned long long t0, dt, t_last;   // ticks of the first and the last open frame
+  unsigned long long N;                // cells per frame slot
+  float inv_dt;
+  int open, slot0, B;
+};
+
+__device__ __forceinline__ FrameView frame_view(const LatDesc& L) {
+  FrameView F;
+  F.frames = L.frames;
+  F.t0 = (unsigned long long)L.f_t0;
+  F.dt = (unsigned long long)L.f_dt;
+  F.t_last = F.t0 + (unsigned long long)(L.f_open - 1) * F.dt;
+  F.N = (unsigned long long)L.rows * (unsigned long long)L.cols;
+  F.inv_dt = 1.0f / (float)F.dt;
+  F.open = L.f_open;
+  F.slot0 = L.f_slot0;
+  F.B = L.f_B;
+  return F;
+}
+
+__device__ __forceinline__ void write_frames(const FrameView& F, size_t gi, unsigned long long ta,
+                                             unsigned long long tn, unsigned up) {
+  if (tn <= F.t0 || ta > F.t_last) return;        // no open frame tick in [ta, tn)
+  unsigned f = 0;
+  if (ta > F.t0) {
+    // first frame with t0 + f dt >= ta: a float estimate (f <= 64), then exact steps
+    const unsigned long long d = ta - F.t0;
+    f = (unsigned)((float)d * F.inv_dt);
+    while ((unsigned long long)f * F.dt < d) ++f;
+    while (f > 0 && (unsigned long long)(f - 1) * F.dt >= d) --f;
+  }
+  unsigned long long T = F.t0 + (unsigned long long)f * F.dt;
+  int slot = F.slot0 + (int)f;
+  if (slot >= F.B) slot -= F.B;
+  for (; (int)f < F.open && T < tn; ++f) {
+    F.frames[(size_t)slot * F.N + gi] = up ? (signed char)1 : (signed char)-1;
+    T += F.dt;
+    if (++slot == F.B) slot = 0;
+  }
+}
+
 struct Geom {
   int ti, tj, r0, h, c0, w;
 };
@@ -275,6 +323,7 @@ __device__ __forceinline__ void commit_tile(const Smem<LB>& sm, const LatDesc& L
     const unsigned flip = b.y < sm.thr[j + 5u * sp] ? 1u : 0u;
     const unsigned long long nk = (key & ~1ull) + (exp_ticks(b.x, L.two) << 1) + (sp ^ flip);
     *kp = nk;
+    if (L.f_open) write_frames(frame_view(L), gidx, key >> 1, nk >> 1, (unsigned)nk & 1u);
     if (DIRECT) {
       L.key[gidx] = nk;
       L.cnt[gidx] = n_old + 1u;
@@ -594,7 +643,9 @@ struct TbCfg {
   static constexpr size_t lBytes = size_t(LIST) * 2;
   static constexpr size_t gBytes = size_t(RW) * 4 * 2;
   static constexpr size_t mBytes = 64;
-  static constexpr size_t bytes = kBytes + cBytes + lBytes + gBytes + mBytes;
+  static constexpr size_t fBytes = 64;            // snapshot-frame view (frame variant), 16-byte aligned
+  static constexpr size_t fOff = (kBytes + cBytes + lBytes + gBytes + mBytes + 15) / 16 * 16;
+  static constexpr size_t bytes = fOff + fBytes;
 };
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
@@ -617,7 +668,8 @@ __device__ __forceinline__ int wrap_index(int x, int n, int& shift, int up_shift
   return x;
 }
 
-template <int RW>
+// FR: snapshot frames are open (write_frames for the tile's own cells).
+template <int RW, bool FR>
 __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     tb_kernel(const LatDesc* __restrict__ lats, int nlat, int total_tiles, int D, int R, DevCounters* ctr) {
   using Cfg = TbCfg<RW>;
@@ -632,6 +684,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   unsigned int* n_en = misc;          // [2]
   unsigned int* thr = misc + 2;       // [10]
   unsigned int* s_over = misc + 12;   // count window overflow in this region
+  FrameView* fv = reinterpret_cast<FrameView*>(smem_raw + Cfg::fOff);
+  static_assert(sizeof(FrameView) <= Cfg::fBytes, "frame view does not fit");
 
   // this launch's number, advanced by the last CTA of the previous launch
   const unsigned launch_idx = *(volatile unsigned*)&ctr->seq;
@@ -672,6 +726,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       n_en[0] = 0u;
       n_en[1] = 0u;
       s_over[0] = 0u;
+      if (FR) *fv = frame_view(L);
     }
     int shc;
     const int gc = wrap_index(g.c0 - D + lj, L.cols, shc, 2);
@@ -817,10 +872,18 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const Philox4 pa = philox_event(gia, base + c16a + 1u, 0u, seed_lo, seed_hi);
         const Philox4 pb = philox_event(gib, base + c16b + 1u, 0u, seed_lo, seed_hi);
         const unsigned long long gapa = exp_ticks(pa.x, two), gapb = exp_ticks(pb.x, two);
-        *kpa = (keya & ~1ull) + (gapa << 1) + (spa ^ (pa.y < tha ? 1u : 0u));
-        *kpb = (keyb & ~1ull) + (gapb << 1) + (spb ^ (pb.y < thb ? 1u : 0u));
+        const unsigned long long nka = (keya & ~1ull) + (gapa << 1) + (spa ^ (pa.y < tha ? 1u : 0u));
+        const unsigned long long nkb = (keyb & ~1ull) + (gapb << 1) + (spb ^ (pb.y < thb ? 1u : 0u));
+        *kpa = nka;
+        *kpb = nkb;
         C[ra * RW + ca] = (unsigned short)(c16a + 1u);
         C[rb * RW + cb] = (unsigned short)(c16b + 1u);
+        if (FR) {   // own cells only: halo commits are repeated by the owning tile
+          if (ra >= D && ra < D + g.h && ca >= D && ca < D + g.w)
+            write_frames(*fv, gia, keya >> 1, nka >> 1, (unsigned)nka & 1u);
+          if (rb >= D && rb < D + g.h && cb >= D && cb < D + g.w)
+            write_frames(*fv, gib, keyb >> 1, nkb >> 1, (unsigned)nkb & 1u);
+        }
       }
       if (e_i < n) {
         const unsigned e = list[e_i];
@@ -834,8 +897,11 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const unsigned c16 = C[r * RW + cc];
         const Philox4 b = philox_event(gidx, base + c16 + 1u, 0u, seed_lo, seed_hi);
         const unsigned flip = b.y < thr[j + 5u * sp] ? 1u : 0u;
-        *kp = (key & ~1ull) + (exp_ticks(b.x, two) << 1) + (sp ^ flip);
+        const unsigned long long nk = (key & ~1ull) + (exp_ticks(b.x, two) << 1) + (sp ^ flip);
+        *kp = nk;
         C[r * RW + cc] = (unsigned short)(c16 + 1u);
+        if (FR && r >= D && r < D + g.h && cc >= D && cc < D + g.w)
+          write_frames(*fv, gidx, key >> 1, nk >> 1, (unsigned)nk & 1u);
       }
       enabled += (unsigned long long)n;
       ++rounds_done;
@@ -1177,29 +1243,52 @@ cudaError_t launch_pack(const LatDesc* h, const int8_t* si, const long long* ti,
 }
 
 
-template <int RW>
+template <int RW, bool FR>
 cudaError_t tb_launch_rw(const LatDesc* d, int nlat, int total, int halo, int rounds, DevCounters* ctr,
                          cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW, FR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)TbCfg<RW>::bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int grid = std::min(total, tb_grid(RW));
-  tb_kernel<RW><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds, ctr);
+  tb_kernel<RW, FR><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds, ctr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tb(const LatDesc* d, int nlat, int total, int region, int halo, int rounds, DevCounters* ctr,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool frames) {
   if (halo < 1 || rounds < 1 || rounds > halo || 4 * halo >= region) return cudaErrorInvalidValue;
   switch (region) {
-    case 96: return tb_launch_rw<96>(d, nlat, total, halo, rounds, ctr, s);
-    case 128: return tb_launch_rw<128>(d, nlat, total, halo, rounds, ctr, s);
+    case 96:
+      return frames ? tb_launch_rw<96, true>(d, nlat, total, halo, rounds, ctr, s)
+                    : tb_launch_rw<96, false>(d, nlat, total, halo, rounds, ctr, s);
+    case 128:
+      return frames ? tb_launch_rw<128, true>(d, nlat, total, halo, rounds, ctr, s)
+                    : tb_launch_rw<128, false>(d, nlat, total, halo, rounds, ctr, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+__global__ void frames_fill_kernel(LatDesc L, long long K, int count) {
+  const size_t N = (size_t)L.rows * L.cols;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = L.key[c];
+    const signed char v = (k & 1ull) ? (signed char)1 : (signed char)-1;
+    for (int f = 0; f < count; ++f) {
+      const unsigned long long T = (unsigned long long)((K + f) * L.f_dt);
+      if (T < (k >> 1)) L.frames[(size_t)((K + f) % L.f_B) * N + c] = v;
+    }
+  }
+}
+
+cudaError_t launch_frames_fill(const LatDesc* h, long long K, int count, cudaStream_t s) {
+  const size_t N = (size_t)h->rows * h->cols;
+  if (count <= 0) return cudaSuccess;
+  frames_fill_kernel<<<grid_for(N, 256), 256, 0, s>>>(*h, K, count);
+  return cudaGetLastError();
 }
 
 int tb_grid(int region) {
