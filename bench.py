@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the per-kernel side measurements")
-    ap.add_argument("--workload", default="ising4096", choices=["ising4096", "batch", "serve", "frames"],
+    ap.add_argument("--workload", default="ising4096", choices=["ising4096", "batch", "serve", "frames", "configs"],
                     help="ising4096: the headline step; batch: the 512-lattice batch only; serve: the request stream")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the replayed request stream")
     ap.add_argument("--single", action="store_true",
@@ -241,6 +241,10 @@ def main():
         return run_reference(args)
     if args.single:
         return run_single(args)
+    if args.workload == "configs":
+        res = configs_measurement()
+        print(json.dumps({"workload": args.workload, **res}), flush=True)
+        return 0
     if args.workload in ("batch", "serve", "frames"):
         import torch
         torch.cuda.set_device(0)
@@ -561,6 +565,85 @@ def frames_measurement(ac, rounds=6, lb=64):
             assert ev == ev0
             out["cases"].append({"lag": lag, "dt": dt_units, "B": B, "frames": int(w["T"] / dt_units), "mode": mode,
                                  "seconds": t, "events_per_s": ev / t, "relative": t0 / t})
+    return out
+
+
+def _oracle_batch_prefix(items):
+    """CPU-baseline worker: oracle runs of a list of (rows, cols, init, seed, beta, t_end)."""
+    import oracle
+    ev = 0
+    for rows, cols, init, seed, beta, t_end in items:
+        st = oracle.init(rows, cols, init, seed)
+        ev += oracle.run(st, oracle.thresholds(beta), seed, t_end)
+    return ev
+
+
+def configs_measurement():
+    """Numbers for the smaller and larger configurations beside the main workload.
+    C1: 64x64, random init from seed 1, beta 0.44, T = 10 (every kernel; the oracle's full run).
+    C3: 16384x16384, all up, seed 3, beta 1.0, h 0.05, T = 20 (the autotuned kernel and each tile side
+        of the blocked kernel; the oracle on the prefix [0, 0.05)).
+    C4: the oracle over the 512-lattice batch on all host cores, prefix [0, 1) of every lattice
+        (the GPU numbers of C4 and C5 come from --workload batch / serve).
+    The oracle's process pool is started before the first GPU call."""
+    import multiprocessing as mp
+    import __graft_entry__
+    __graft_entry__.build()          # compiles and loads the library; no GPU call yet
+    import oracle
+    from paper_cs_0502039_gb300 import workloads
+    ws = workloads.batch_workload()
+    cores = os.cpu_count() or 1
+    items = [(w["rows"], w["cols"], w["init"], w["seed"], w["beta"], T32) for w in ws]
+    chunks = [items[i::cores] for i in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        t0 = time.perf_counter()
+        ev = sum(pool.map(_oracle_batch_prefix, chunks))
+        dt = time.perf_counter() - t0
+    out = {"c4_oracle": {"events": ev, "seconds": dt, "events_per_s": ev / dt, "cores": cores,
+                         "sample": "all 512 lattices, arrivals in [0, 1), one process per core"}}
+
+    st = oracle.init(64, 64, 0, 1)
+    t0 = time.perf_counter()
+    ev = oracle.run(st, oracle.thresholds(0.44), 1, 10 * T32)
+    dt = time.perf_counter() - t0
+    out["c1_oracle"] = {"events": ev, "seconds": dt, "events_per_s": ev / dt, "cores": 1}
+    st = oracle.init(16384, 16384, 1, 3)
+    t0 = time.perf_counter()
+    ev = oracle.run(st, oracle.thresholds(1.0, 1.0, 0.05), 3, int(0.05 * T32))
+    dt = time.perf_counter() - t0
+    out["c3_oracle"] = {"events": ev, "seconds": dt, "events_per_s": ev / dt, "cores": 1,
+                        "sample": "arrivals in [0, 0.05)"}
+    del st
+
+    import torch
+    torch.cuda.set_device(0)
+    import paper_cs_0502039_gb300 as ac
+    from paper_cs_0502039_gb300 import autotune
+    R, B = ac.AC_KERNEL_ROUND, ac.AC_KERNEL_BLOCKED
+
+    def measure(rows, cols, init, seed, beta, h, T, kern, lb, rounds, polls, warm_T):
+        with ac.Sim(rows, cols, beta, 1.0, h, seed, init=init, kernel=kern, Lb=lb, rounds=rounds, polls=polls) as s:
+            s.run_until(warm_T)
+            s.reset(seed, init)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.run_until(T)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            st = s.stats()
+        return {"kernel": "blocked" if kern == B else "round", "Lb": lb, "rounds": rounds, "polls": polls,
+                "events": st["events"], "device_ms": st["device_ms"], "wall_ms": 1000 * wall,
+                "events_per_s": st["events"] / (st["device_ms"] / 1000.0),
+                "hbm_frac_effective": BYTES_PER_EVENT * st["events"] / (st["device_ms"] / 1000.0) / 1e9
+                / measured_peaks()[0]}
+
+    out["c1"] = [measure(64, 64, 0, 1, 0.44, 0.0, 10, k, lb, r, p, 10)
+                 for k, lb, r, p in [(R, 32, 1, 0), (R, 64, 4, 0), (B, 32, 1, 8), (B, 64, 1, 8)]]
+    tuned = autotune.tune(16384, 16384, T=2.0)
+    cfgs = [(tuned["kernel"], tuned["Lb"], tuned["rounds"], tuned["polls"]), (R, 64, 6, 0),
+            (B, 32, 1, 8), (B, 64, 1, 8), (B, 128, 1, 8)]
+    out["c3"] = [measure(16384, 16384, 1, 3, 1.0, 0.05, 20, k, lb, r, p, 1) for k, lb, r, p in cfgs]
+    out["c3_autotuned"] = {k: tuned[k] for k in ("kernel", "Lb", "rounds", "polls")}
     return out
 
 
