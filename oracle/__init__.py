@@ -25,6 +25,9 @@ Pins (tests/test_oracle_*.py, all CPU):
                      transient P0 exp(QT)), Poisson(T) counts, beta = 0
                      closed form, Onsager energy and magnetisation.
   time_rounds     -- round-1 fraction 1/5, long-run fraction ~0.121 (Sec. 4).
+  gap, time_model -- laws: closed form, binary64 r^(1/8); brute-force rounds in
+                     1, 2 and 3 dimensions; first-round fractions 1/3, 1/5, 1/7;
+                     2D exponential equal to time_rounds; the paper's limits.
   frames          -- per-cell spin histories of the brute-force simulator read
                      at each frame time, including an arrival exactly at K dt.
   observables, checksum -- brute-force recomputation in numpy.
@@ -93,6 +96,11 @@ def _bind(lib):
     lib.aco_exp_ticks_many.restype = None
     lib.aco_philox_blocks.argtypes = [ctypes.c_uint64, P, P, ctypes.c_uint32, P, ctypes.c_int64]
     lib.aco_philox_blocks.restype = None
+    lib.aco_gap.argtypes = [ctypes.c_int32, ctypes.c_uint32]
+    lib.aco_gap.restype = ctypes.c_uint64
+    lib.aco_time_model.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                   ctypes.c_int64, ctypes.c_int64, P, P, P]
+    lib.aco_time_model.restype = ctypes.c_int64
     return lib
 
 
@@ -208,6 +216,31 @@ def time_rounds(state: State, seed: int, t_end: int, max_rounds: int = 1 << 20):
     if r < 0:
         raise MemoryError("oracle allocation failed")
     return buf[:min(r, max_rounds)].copy()
+
+
+LAW_EXP, LAW_UNIFORM, LAW_ROOT8 = 0, 1, 2
+
+
+def gap(law: int, x: int) -> int:
+    """Increment in ticks for the 32-bit word x under law 0 (exponential), 1 (uniform on (0, 1])
+    or 2 (r^(1/8)) of the time-only model (reading R11)."""
+    return int(_load().aco_gap(int(law), int(x) & 0xFFFFFFFF))
+
+
+def time_model(dims: int, n: int, law: int, seed: int, t_end: int, max_rounds: int):
+    """Time-only round model of Sec. 4 on an n-cell circle (dims 1), n x n torus (2) or n^3
+    periodic array (3): returns (advancing cells per round, final ticks, final counts)."""
+    N = n ** dims
+    en = np.zeros(max(1, max_rounds), dtype=np.int64)
+    t = np.zeros(N, dtype=np.int64)
+    cnt = np.zeros(N, dtype=np.uint32)
+    r = _load().aco_time_model(int(dims), int(n), int(law), int(seed) & (2**64 - 1), int(t_end),
+                               int(max_rounds), _ptr(en), _ptr(t), _ptr(cnt))
+    if r == -1:
+        raise MemoryError("oracle allocation failed")
+    if r < 0:
+        raise ValueError("dims must be 1..3, n >= 2, law 0..2")
+    return en[:r].copy(), t, cnt
 
 
 def observables(state: State):

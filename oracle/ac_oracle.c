@@ -47,6 +47,9 @@
  *              neighbours, as in the appendix's prob[10].
  *   R7 nbrs    4 nearest neighbours on the periodic torus, counted with
  *              multiplicity (on a 2-wide torus both sides are one cell).
+ *   R11 laws   time-only model of Sec. 4: exponential (R5), uniform on
+ *              (0, 1] as x + 1 ticks, and r^(1/8) as three nested integer
+ *              square roots (see aco_gap below).
  *
  * Build: plain C99 + libm, -O2 -ffp-contract=off (no fused multiply-add, so
  * the binary64 table is the same on every host).
@@ -278,6 +281,113 @@ int64_t aco_time_rounds(int32_t rows, int32_t cols, uint64_t seed, int64_t *t, u
         ++rounds;
     }
     free(en);
+    return rounds;
+}
+
+/* ------------------------------------------------------------------ */
+/* Time-only round model in one, two and three dimensions (Sec. 4: the  */
+/* six experiments behind the one-cell-per-PE efficiency figure -- an   */
+/* n-cell circle, an n x n torus and an n x n x n periodic array, with  */
+/* exponential or uniform increments, and the r^(1/8) increments of the */
+/* same section).  Times only: a cell advances in a round iff its key   */
+/* (t, index) is below the keys of all its 2*dims neighbours (R1) and   */
+/* t < t_end; advancing cells draw their next increment afterwards.     */
+/*                                                                      */
+/* Increment laws (reading R11), from the 32-bit word x = B(c, k).x:    */
+/*   0  exponential: exp_ticks(x) (R5)                                  */
+/*   1  uniform on (0, 1]: x + 1 ticks                                  */
+/*   2  r^(1/8), r = (2x+1)/2^33 uniform on (0, 1): three nested        */
+/*      integer square roots, s1 = isqrt((2x+1) 2^31) = floor(2^32 r^   */
+/*      (1/2)), s2 = isqrt(s1 2^32), gap = isqrt(s2 2^32)               */
+/* Initial times t0 = gap(B(c, 0).x) as in R3; cell c's k-th advance     */
+/* draws B(c, k).x.  Cell index: row-major, ((z n) + y) n + x.          */
+/* ------------------------------------------------------------------ */
+
+/* floor(sqrt(v)), the digit-by-digit (base 4) method */
+static uint64_t isqrt64(uint64_t v)
+{
+    uint64_t res = 0, bit = 1ull << 62;
+    while (bit > v) bit >>= 2;
+    while (bit) {
+        if (v >= res + bit) {
+            v -= res + bit;
+            res = (res >> 1) + bit;
+        } else {
+            res >>= 1;
+        }
+        bit >>= 2;
+    }
+    return res;
+}
+
+uint64_t aco_gap(int32_t law, uint32_t x)
+{
+    if (law == 0) return aco_exp_ticks(x);
+    if (law == 1) return (uint64_t)x + 1ull;
+    uint64_t s1 = isqrt64((2ull * (uint64_t)x + 1ull) << 31);
+    uint64_t s2 = isqrt64(s1 << 32);
+    return isqrt64(s2 << 32);
+}
+
+static void neighbours_nd(int32_t dims, int64_t n, uint64_t c, uint64_t nb[6])
+{
+    int64_t coord[3] = {0, 0, 0}, stride[3] = {1, n, n * n};
+    uint64_t rest = c;
+    for (int a = 0; a < dims; ++a) {
+        coord[a] = (int64_t)(rest % (uint64_t)n);
+        rest /= (uint64_t)n;
+    }
+    for (int a = 0; a < dims; ++a) {
+        int64_t lo = (coord[a] - 1 + n) % n, hi = (coord[a] + 1) % n;
+        nb[2 * a] = c - (uint64_t)(coord[a] * stride[a]) + (uint64_t)(lo * stride[a]);
+        nb[2 * a + 1] = c - (uint64_t)(coord[a] * stride[a]) + (uint64_t)(hi * stride[a]);
+    }
+}
+
+int64_t aco_time_model(int32_t dims, int64_t n, int32_t law, uint64_t seed, int64_t t_end,
+                       int64_t max_rounds, int64_t *enabled, int64_t *t_out, uint32_t *n_out)
+{
+    if (dims < 1 || dims > 3 || n < 2 || law < 0 || law > 2) return -2;
+    uint64_t N = (uint64_t)n;
+    for (int a = 1; a < dims; ++a) N *= (uint64_t)n;
+    int64_t *t = (int64_t *)malloc(N * sizeof(int64_t));
+    uint32_t *cnt = (uint32_t *)calloc(N, sizeof(uint32_t));
+    uint8_t *en = (uint8_t *)malloc(N);
+    if (!t || !cnt || !en) {
+        free(t); free(cnt); free(en);
+        return -1;
+    }
+    for (uint64_t c = 0; c < N; ++c) {
+        uint32_t b[4];
+        philox_block(seed, (uint32_t)c, 0u, 0u, b);
+        t[c] = (int64_t)aco_gap(law, b[0]);
+    }
+    int64_t rounds = 0;
+    while (rounds < max_rounds) {
+        int64_t nen = 0;
+        for (uint64_t c = 0; c < N; ++c) {
+            uint64_t nb[6];
+            neighbours_nd(dims, n, c, nb);
+            int ok = t[c] < t_end;
+            for (int d = 0; d < 2 * dims && ok; ++d)
+                if (nb[d] != c && !key_less(t, (uint32_t)c, (uint32_t)nb[d])) ok = 0;
+            en[c] = (uint8_t)ok;
+            nen += ok;
+        }
+        if (nen == 0) break;
+        for (uint64_t c = 0; c < N; ++c) {
+            if (!en[c]) continue;
+            uint32_t b[4];
+            philox_block(seed, (uint32_t)c, cnt[c] + 1u, 0u, b);
+            t[c] += (int64_t)aco_gap(law, b[0]);
+            cnt[c] += 1u;
+        }
+        enabled[rounds] = nen;
+        ++rounds;
+    }
+    if (t_out) memcpy(t_out, t, N * sizeof(int64_t));
+    if (n_out) memcpy(n_out, cnt, N * sizeof(uint32_t));
+    free(t); free(cnt); free(en);
     return rounds;
 }
 
