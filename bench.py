@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the per-kernel side measurements")
-    ap.add_argument("--workload", default="ising4096", choices=["ising4096", "batch", "serve", "frames", "configs"],
+    ap.add_argument("--workload", default="ising4096",
+                    choices=["ising4096", "batch", "serve", "frames", "configs", "efficiency"],
                     help="ising4096: the headline step; batch: the 512-lattice batch only; serve: the request stream")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the replayed request stream")
     ap.add_argument("--single", action="store_true",
@@ -244,6 +245,14 @@ def main():
     if args.workload == "configs":
         res = configs_measurement()
         print(json.dumps({"workload": args.workload, **res}), flush=True)
+        return 0
+    if args.workload == "efficiency":
+        import torch
+        torch.cuda.set_device(0)
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_cs_0502039_gb300 as ac
+        print(json.dumps({"workload": args.workload, **efficiency_measurement(ac)}), flush=True)
         return 0
     if args.workload in ("batch", "serve", "frames"):
         import torch
@@ -565,6 +574,26 @@ def frames_measurement(ac, rounds=6, lb=64):
             assert ev == ev0
             out["cases"].append({"lag": lag, "dt": dt_units, "B": B, "frames": int(w["T"] / dt_units), "mode": mode,
                                  "seconds": t, "events_per_s": ev / t, "relative": t0 / t})
+    return out
+
+
+def efficiency_measurement(ac, rounds=2000):
+    """Sec. 4's time-only round model at large sizes: the fraction of cells that advance per
+    round (mean over the second half of `rounds` rounds), for a 2^24-cell circle, a 4096^2 torus
+    and a 256^3 periodic array, each with exponential, uniform and r^(1/8) increments, beside the
+    limits the paper reports; and the rate of cell advances on the GPU."""
+    import numpy as np
+    paper = {(1, 0): 0.247, (1, 1): 0.271, (1, 2): 0.3388, (2, 0): 0.121, (2, 1): 0.132}
+    out = {"rounds": rounds, "cases": []}
+    for dims, n in [(1, 1 << 24), (2, 4096), (3, 256)]:
+        for law, name in [(ac.AC_LAW_EXP, "exponential"), (ac.AC_LAW_UNIFORM, "uniform"), (ac.AC_LAW_ROOT8, "r^(1/8)")]:
+            en, _, _, ms = ac.ac_time_model(dims, n, law, 11, 2**61 - 1, rounds)
+            N = n ** dims
+            frac = en.astype(np.float64) / N
+            out["cases"].append({"dims": dims, "n": n, "law": name, "efficiency": float(frac[rounds // 2:].mean()),
+                                 "efficiency_first_round": float(frac[0]), "paper": paper.get((dims, law)),
+                                 "advances": int(en.sum()), "device_ms": ms,
+                                 "advances_per_s": float(en.sum()) / (ms / 1000.0)})
     return out
 
 

@@ -203,6 +203,32 @@ ac_status ac_reset(ac_sim* sim, uint64_t seed, int32_t init);
  *   fn = NULL, and ac_batch_run_until refuses the handle (AC_ERR_ARG).
  * ac_frames_status: next frame to be handed out, B and dt_ticks (B = 0: off).
  */
+/*
+ * Time-only round model (Sec. 4, the model behind the one-cell-per-PE efficiency
+ * figure).  Cells carry only local times on an n-cell circle (dims = 1), an n x n
+ * torus (2) or an n x n x n periodic array (3), row-major index
+ * ((z n) + y) n + x.  Cell c starts at t = gap(B(c, 0).x); in each synchronous
+ * round a cell advances iff t < t_end and (t, index) is below the keys of all
+ * its 2 dims neighbours (reading R1), drawing its k-th increment from
+ * B(c, k).x, where B(c, k) is Philox4x32-10 of {c, k, 0, 0} under the key
+ * (seed lo, seed hi).  Increment laws:
+ *   AC_LAW_EXP     exponential: the integer logarithm gap of ac_run_until
+ *   AC_LAW_UNIFORM uniform on (0, 1]: x + 1 ticks
+ *   AC_LAW_ROOT8   r^(1/8), r = (2x+1)/2^33: s1 = isqrt((2x+1) 2^31),
+ *                  s2 = isqrt(s1 2^32), gap = isqrt(s2 2^32)
+ * Runs until a round advances no cell or max_rounds rounds have run.  Writes the
+ * number of advancing cells of each round to enabled[0 .. *rounds_out) (a host
+ * array of max_rounds entries), and, when not NULL, the final times and advance
+ * counts to host arrays t_out, n_out of n^dims entries and the device time of
+ * the rounds to *device_ms.  Allocates and frees its own device memory.  Needs
+ * n >= 2, n^dims < 2^32, t_end >= 0, max_rounds >= 1.
+ * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
+ */
+enum { AC_LAW_EXP = 0, AC_LAW_UNIFORM = 1, AC_LAW_ROOT8 = 2 };
+ac_status ac_time_model(int32_t dims, int64_t n, int32_t law, uint64_t seed, int64_t t_end, int32_t max_rounds,
+                        uint64_t* enabled, int32_t* rounds_out, int64_t* t_out, uint32_t* n_out,
+                        double* device_ms);
+
 #define AC_MAX_FRAMES 64
 typedef void (*ac_frame_fn)(void* user, int64_t K, const int8_t* frame, size_t n);
 ac_status ac_frames_configure(ac_sim* sim, int64_t dt_ticks, int64_t K0, int32_t B);

@@ -54,7 +54,9 @@ EXPORTS = ["ac_create", "ac_set_stream", "ac_configure", "ac_run_until", "ac_run
            "ac_read_state", "ac_read_state_device", "ac_load_state", "ac_stats", "ac_round_history",
            "ac_destroy", "ac_last_error", "ac_thresholds", "ac_reset", "ac_set_option", "ac_batch_create", "ac_batch_run_until",
            "ac_dev_exp_ticks", "ac_dev_philox", "ac_run_blocked_static", "ac_frames_configure",
-           "ac_run_until_frames", "ac_frames_status"]
+           "ac_run_until_frames", "ac_frames_status", "ac_time_model"]
+
+AC_LAW_EXP, AC_LAW_UNIFORM, AC_LAW_ROOT8 = 0, 1, 2
 
 AC_MAX_FRAMES = 64
 # void (*ac_frame_fn)(void* user, int64_t K, const int8_t* frame, size_t n)
@@ -91,6 +93,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ac_frames_configure": ([P, I64, I64, I32], I32),
         "ac_run_until_frames": ([P, I64, FRAME_FN, P, I32], I32),
         "ac_frames_status": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)], I32),
+        "ac_time_model": ([I32, I64, I32, U64, I64, I32, P, ctypes.POINTER(I32), P, P,
+                           ctypes.POINTER(ctypes.c_double)], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -247,6 +251,22 @@ def ac_frames_status(sim: int) -> tuple[int, int, int]:
     K, B, dt = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
     _check(_lib.ac_frames_status(sim, ctypes.byref(K), ctypes.byref(B), ctypes.byref(dt)))
     return K.value, B.value, dt.value
+
+
+def ac_time_model(dims: int, n: int, law: int, seed: int, t_end: int, max_rounds: int, want_state: bool = False):
+    """Time-only round model of Sec. 4 on the GPU: returns (advancing cells per round, final ticks or
+    None, final counts or None, device milliseconds)."""
+    en = np.zeros(max_rounds, dtype=np.uint64)
+    rounds = ctypes.c_int32()
+    ms = ctypes.c_double()
+    N = n ** dims
+    t = np.empty(N, dtype=np.int64) if want_state else None
+    cnt = np.empty(N, dtype=np.uint32) if want_state else None
+    _check(_lib.ac_time_model(int(dims), int(n), int(law), int(seed) & (2**64 - 1), int(t_end), int(max_rounds),
+                              _np_ptr(en, np.uint64), ctypes.byref(rounds),
+                              None if t is None else _np_ptr(t, np.int64),
+                              None if cnt is None else _np_ptr(cnt, np.uint32), ctypes.byref(ms)))
+    return en[:rounds.value].copy(), t, cnt, ms.value
 
 
 # --------------------------------------------------------------- convenience

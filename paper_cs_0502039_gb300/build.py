@@ -13,7 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libac.so")
-SOURCES = ["ac_kernels.cu", "ac_api.cu", "ac_static.cu"]
+SOURCES = ["ac_kernels.cu", "ac_api.cu", "ac_static.cu", "ac_time.cu"]
 HEADERS = ["ac_device.cuh", "ac_internal.h"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
