@@ -25,6 +25,8 @@ Pins (tests/test_oracle_*.py, all CPU):
                      transient P0 exp(QT)), Poisson(T) counts, beta = 0
                      closed form, Onsager energy and magnetisation.
   time_rounds     -- round-1 fraction 1/5, long-run fraction ~0.121 (Sec. 4).
+  life_init, life_run -- brute-force linear scan, the rule on hand-built
+                     neighbourhoods, still lifes, ticks equal to the Ising run's.
   gap, time_model -- laws: closed form, binary64 r^(1/8); brute-force rounds in
                      1, 2 and 3 dimensions; first-round fractions 1/3, 1/5, 1/7;
                      2D exponential equal to time_rounds; the paper's limits.
@@ -96,6 +98,12 @@ def _bind(lib):
     lib.aco_exp_ticks_many.restype = None
     lib.aco_philox_blocks.argtypes = [ctypes.c_uint64, P, P, ctypes.c_uint32, P, ctypes.c_int64]
     lib.aco_philox_blocks.restype = None
+    lib.aco_life_init.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
+                                  ctypes.c_uint64, P, P, P]
+    lib.aco_life_init.restype = None
+    lib.aco_life_run.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
+                                 ctypes.c_uint64, P, P, P, ctypes.c_int64]
+    lib.aco_life_run.restype = ctypes.c_int64
     lib.aco_gap.argtypes = [ctypes.c_int32, ctypes.c_uint32]
     lib.aco_gap.restype = ctypes.c_uint64
     lib.aco_time_model.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
@@ -216,6 +224,33 @@ def time_rounds(state: State, seed: int, t_end: int, max_rounds: int = 1 << 20):
     if r < 0:
         raise MemoryError("oracle allocation failed")
     return buf[:min(r, max_rounds)].copy()
+
+
+CONWAY_BIRTH, CONWAY_SURVIVE = 1 << 3, (1 << 2) | (1 << 3)
+
+
+def life_init(rows: int, cols: int, init_mode: int, density: int, seed: int) -> State:
+    """Initial Life state (reading R12): alive (+1) iff I(c).x < density for init 0, all alive for 1,
+    all dead for 2; first arrivals as for the Ising array."""
+    if rows < 3 or cols < 3:
+        raise ValueError("rows and cols must be >= 3")
+    N = rows * cols
+    s = np.zeros(N, dtype=np.int8)
+    t = np.zeros(N, dtype=np.int64)
+    n = np.zeros(N, dtype=np.uint32)
+    _load().aco_life_init(rows, cols, int(init_mode), int(density) & 0xFFFFFFFF, int(seed) & (2**64 - 1),
+                          _ptr(s), _ptr(t), _ptr(n))
+    return State(rows, cols, s, t, n)
+
+
+def life_run(state: State, birth: int, survive: int, seed: int, t_end: int) -> int:
+    """Advance a Life state in place: every arrival with tick < t_end, in (tick, index) order, sets the
+    cell to bit k of `survive` (alive) or `birth` (dead), k = live Moore neighbours just before it."""
+    ev = _load().aco_life_run(state.rows, state.cols, int(birth), int(survive), int(seed) & (2**64 - 1),
+                              _ptr(state.s), _ptr(state.t), _ptr(state.n), int(t_end))
+    if ev < 0:
+        raise MemoryError("oracle heap allocation failed")
+    return int(ev)
 
 
 LAW_EXP, LAW_UNIFORM, LAW_ROOT8 = 0, 1, 2

@@ -47,6 +47,8 @@
  *              neighbours, as in the appendix's prob[10].
  *   R7 nbrs    4 nearest neighbours on the periodic torus, counted with
  *              multiplicity (on a 2-wide torus both sides are one cell).
+ *   R12 life   Life-like rules: Moore neighbourhood, birth / survival masks
+ *              over the live-neighbour count (see aco_life_run below).
  *   R11 laws   time-only model of Sec. 4: exponential (R5), uniform on
  *              (0, 1] as x + 1 ticks, and r^(1/8) as three nested integer
  *              square roots (see aco_gap below).
@@ -234,6 +236,73 @@ int64_t aco_run(int32_t rows, int32_t cols, const uint32_t thr[10], uint64_t see
         philox_block(seed, c, n[c] + 1u, 0u, b);
         if (b[1] < thr[up + 5 * (s[c] > 0)]) s[c] = (int8_t)(-s[c]);  /* Eq. (1) */
         t[c] += (int64_t)aco_exp_ticks(b[0]);                          /* Eq. (5) */
+        n[c] += 1u;
+        sift_down(heap, N, 0, t);
+        ++events;
+    }
+    free(heap);
+    return events;
+}
+
+/* ------------------------------------------------------------------ */
+/* Asynchronous Life-like automaton (Sec. 3: the deterministic update   */
+/* under Poisson asynchrony, with Conway's Game of Life as the example  */
+/* of a rule that leaves most cells unchanged).  Reading R12: the       */
+/* neighbourhood is the 8-cell Moore neighbourhood on the torus; at an  */
+/* arrival a cell with k live neighbours becomes                        */
+/*   alive ? bit k of `survive` : bit k of `birth`                      */
+/* (Conway: birth = 1<<3, survive = 1<<2 | 1<<3), from the states just  */
+/* before the arrival; arrivals are the same Poisson process as for the */
+/* Ising array (R3-R5: first gap from B(c,0).x, the commit of arrival n */
+/* advances by exp_ticks(B(c,n+1).x)).  Initial state: alive iff        */
+/* I(c).x < density (init 0), all alive (1), all dead (2).  Alive is    */
+/* s = +1, dead s = -1.  Needs rows, cols >= 3 (8 distinct neighbours). */
+/* ------------------------------------------------------------------ */
+void aco_life_init(int32_t rows, int32_t cols, int32_t init, uint32_t density, uint64_t seed,
+                   int8_t *s, int64_t *t, uint32_t *n)
+{
+    uint64_t N = (uint64_t)rows * (uint64_t)cols;
+    for (uint64_t c = 0; c < N; ++c) {
+        uint32_t b0[4], ib[4];
+        philox_block(seed, (uint32_t)c, 0u, 0u, b0);
+        if (init == 1)
+            s[c] = 1;
+        else if (init == 2)
+            s[c] = -1;
+        else {
+            philox_block(seed, (uint32_t)c, 0u, 1u, ib);
+            s[c] = (ib[0] < density) ? 1 : -1;
+        }
+        t[c] = (int64_t)aco_exp_ticks(b0[0]);
+        n[c] = 0u;
+    }
+}
+
+int64_t aco_life_run(int32_t rows, int32_t cols, uint32_t birth, uint32_t survive, uint64_t seed,
+                     int8_t *s, int64_t *t, uint32_t *n, int64_t t_end)
+{
+    uint64_t N = (uint64_t)rows * (uint64_t)cols;
+    uint32_t *heap = (uint32_t *)malloc(N * sizeof(uint32_t));
+    if (!heap) return -1;
+    for (uint64_t c = 0; c < N; ++c) heap[c] = (uint32_t)c;
+    for (uint64_t i = N / 2; i-- > 0;) sift_down(heap, N, i, t);
+
+    int64_t events = 0;
+    while (t[heap[0]] < t_end) {
+        uint32_t c = heap[0];
+        int64_t r = (int64_t)(c / (uint32_t)cols), q = (int64_t)(c % (uint32_t)cols);
+        int k = 0;                                    /* live Moore neighbours */
+        for (int dr = -1; dr <= 1; ++dr)
+            for (int dq = -1; dq <= 1; ++dq) {
+                if (dr == 0 && dq == 0) continue;
+                int64_t rr = (r + dr + rows) % rows, qq = (q + dq + cols) % cols;
+                k += (s[rr * cols + qq] > 0);
+            }
+        uint32_t mask = (s[c] > 0) ? survive : birth;
+        s[c] = ((mask >> k) & 1u) ? 1 : -1;
+        uint32_t b[4];
+        philox_block(seed, c, n[c] + 1u, 0u, b);
+        t[c] += (int64_t)aco_exp_ticks(b[0]);
         n[c] += 1u;
         sift_down(heap, N, 0, t);
         ++events;
