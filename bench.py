@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the per-kernel side measurements")
     ap.add_argument("--workload", default="ising4096",
-                    choices=["ising4096", "batch", "serve", "frames", "configs", "efficiency"],
+                    choices=["ising4096", "batch", "serve", "frames", "configs", "efficiency", "life"],
                     help="ising4096: the headline step; batch: the 512-lattice batch only; serve: the request stream")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the replayed request stream")
     ap.add_argument("--single", action="store_true",
@@ -245,6 +245,14 @@ def main():
     if args.workload == "configs":
         res = configs_measurement()
         print(json.dumps({"workload": args.workload, **res}), flush=True)
+        return 0
+    if args.workload == "life":
+        import torch
+        torch.cuda.set_device(0)
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_cs_0502039_gb300 as ac
+        print(json.dumps({"workload": args.workload, **life_measurement(ac)}), flush=True)
         return 0
     if args.workload == "efficiency":
         import torch
@@ -574,6 +582,27 @@ def frames_measurement(ac, rounds=6, lb=64):
             assert ev == ev0
             out["cases"].append({"lag": lag, "dt": dt_units, "B": B, "frames": int(w["T"] / dt_units), "mode": mode,
                                  "seconds": t, "events_per_s": ev / t, "relative": t0 / t})
+    return out
+
+
+def life_measurement(ac):
+    """Asynchronous Conway Life (B3/S23, Moore neighbourhood) on a 4096^2 torus, half the cells
+    alive at the start (seed 7), run to T = 50 with the temporal-blocked kernel: committed arrivals
+    per second for several rounds per launch, beside the Ising array on the same kernel."""
+    import torch
+    w = WORKLOAD
+    out = {"lattice": f"{w['rows']}x{w['cols']}", "rule": "B3/S23", "density": 0.5, "T": w["T"], "cases": []}
+    for rounds in (4, 6, 8):
+        with ac.life(w["rows"], w["cols"], w["seed"], 0.5, rounds=rounds) as sim:
+            sim.run_until(w["T"])
+            sim.reset(w["seed"], 0)
+            torch.cuda.synchronize()
+            sim.run_until(w["T"])
+            st = sim.stats()
+            s, _, _ = sim.read_state()
+        out["cases"].append({"rounds": rounds, "events": st["events"], "device_ms": st["device_ms"],
+                             "events_per_s": st["events"] / (st["device_ms"] / 1000.0),
+                             "alive_fraction_at_T": float((s > 0).mean())})
     return out
 
 

@@ -82,6 +82,28 @@ typedef struct {
  */
 ac_status ac_create(ac_lattice lat, double beta, double J, double h, uint64_t seed, ac_sim** out);
 
+/*
+ * Create an asynchronous Life-like automaton instead of the Ising array: the
+ * deterministic update of Sec. 3 (Conway's Game of Life is the paper's example)
+ * under the same Poisson asynchrony, arrivals and random streams.  At an arrival
+ * a cell with k live cells among its 8 Moore neighbours (states just before the
+ * arrival) becomes alive iff bit k of `survive` (if alive) or of `birth` (if
+ * dead) is set; Conway's rule is birth = AC_LIFE_CONWAY_BIRTH, survive =
+ * AC_LIFE_CONWAY_SURVIVE.  A cell may commit once its (tick, index) key is below
+ * those of all 8 Moore neighbours.  Initial state (lat.init): AC_INIT_RANDOM =
+ * alive iff the word x of Philox block {c, 0, 1, 0} is < density (a 32-bit
+ * fraction), AC_INIT_UP = all alive, AC_INIT_DOWN = all dead.  The state reads
+ * and loads as for the Ising array with s = +1 alive, -1 dead; ticks and counts
+ * are those of the Ising array with the same seed.  Needs rows, cols >= 4 and
+ * 9-bit masks.  Runs on the round kernel only (temporal blocking with rounds per
+ * launch capped at min(rows, cols) / 4, default 6); not in batches.
+ * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
+ */
+#define AC_LIFE_CONWAY_BIRTH (1u << 3)
+#define AC_LIFE_CONWAY_SURVIVE ((1u << 2) | (1u << 3))
+ac_status ac_create_life(ac_lattice lat, uint32_t density, uint32_t birth, uint32_t survive, uint64_t seed,
+                         ac_sim** out);
+
 /* Use `cuda_stream` (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
  * for all later device work of this handle.  NULL selects the legacy default stream. */
 ac_status ac_set_stream(ac_sim* sim, void* cuda_stream);

@@ -54,7 +54,9 @@ EXPORTS = ["ac_create", "ac_set_stream", "ac_configure", "ac_run_until", "ac_run
            "ac_read_state", "ac_read_state_device", "ac_load_state", "ac_stats", "ac_round_history",
            "ac_destroy", "ac_last_error", "ac_thresholds", "ac_reset", "ac_set_option", "ac_batch_create", "ac_batch_run_until",
            "ac_dev_exp_ticks", "ac_dev_philox", "ac_run_blocked_static", "ac_frames_configure",
-           "ac_run_until_frames", "ac_frames_status", "ac_time_model"]
+           "ac_run_until_frames", "ac_frames_status", "ac_time_model", "ac_create_life"]
+
+AC_LIFE_CONWAY_BIRTH, AC_LIFE_CONWAY_SURVIVE = 1 << 3, (1 << 2) | (1 << 3)
 
 AC_LAW_EXP, AC_LAW_UNIFORM, AC_LAW_ROOT8 = 0, 1, 2
 
@@ -93,6 +95,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ac_frames_configure": ([P, I64, I64, I32], I32),
         "ac_run_until_frames": ([P, I64, FRAME_FN, P, I32], I32),
         "ac_frames_status": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)], I32),
+        "ac_create_life": ([ac_lattice, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, U64,
+                            ctypes.POINTER(P)], I32),
         "ac_time_model": ([I32, I64, I32, U64, I64, I32, P, ctypes.POINTER(I32), P, P,
                            ctypes.POINTER(ctypes.c_double)], I32),
     }
@@ -121,6 +125,13 @@ def _np_ptr(a: np.ndarray, dtype) -> ctypes.c_void_p:
 def ac_create(rows: int, cols: int, init: int, beta: float, J: float, h: float, seed: int) -> int:
     out = ctypes.c_void_p()
     _check(_lib.ac_create(ac_lattice(rows, cols, init), beta, J, h, seed & (2**64 - 1), ctypes.byref(out)))
+    return out.value
+
+
+def ac_create_life(rows: int, cols: int, init: int, density: int, birth: int, survive: int, seed: int) -> int:
+    out = ctypes.c_void_p()
+    _check(_lib.ac_create_life(ac_lattice(rows, cols, init), int(density) & 0xFFFFFFFF, int(birth), int(survive),
+                               seed & (2**64 - 1), ctypes.byref(out)))
     return out.value
 
 
@@ -270,6 +281,17 @@ def ac_time_model(dims: int, n: int, law: int, seed: int, t_end: int, max_rounds
 
 
 # --------------------------------------------------------------- convenience
+def life(rows: int, cols: int, seed: int = 0, density: float = 0.5, birth: int = AC_LIFE_CONWAY_BIRTH,
+         survive: int = AC_LIFE_CONWAY_SURVIVE, init: int = 0, rounds: int = 6) -> "Sim":
+    """A Sim handle holding an asynchronous Life-like automaton (alive = +1); density is the fraction
+    of live cells of a random start (quantised to 32 bits)."""
+    d = min(int(density * 2**32), 2**32 - 1) if density < 1.0 else 2**32 - 1
+    h = ac_create_life(rows, cols, init, d, birth, survive, seed)
+    sim = Sim(rows, cols, 0.0, 0.0, 0.0, seed, init=init, handle=h)
+    sim.configure(AC_KERNEL_ROUND, 64, rounds, 0)
+    return sim
+
+
 class Sim:
     """One lattice handle (owns its device memory; freed on close / GC)."""
 

@@ -99,6 +99,9 @@ struct ac_sim {
 
   long long t_done = 0;
   // snapshot frames (Fig. 3.7): f_B slots of ncells() spins; frames [f_K, f_K + f_B) open
+  // model: 0 = Ising heat bath, 1 = Life-like automaton (birth / survival masks, density)
+  int model = 0;
+  uint32_t life_birth = 0, life_survive = 0, life_density = 0;
   int8_t* frames = nullptr;
   int8_t* frame_host = nullptr;             // pinned copy handed to host callbacks
   int f_B = 0;
@@ -135,6 +138,12 @@ struct ac_sim {
     d.t_end = t_end;
     d.t2 = 2ull * (unsigned long long)t_end;
     d.drop_publish = drop_publish;
+    d.model = model;
+    d.life_density = life_density;
+    if (model == 1) {
+      d.thr[0] = life_birth;
+      d.thr[1] = life_survive;
+    }
     if (f_B > 0) {
       d.frames = reinterpret_cast<signed char*>(frames);
       d.f_t0 = f_K * f_dt;
@@ -373,7 +382,7 @@ ac_status tb_counts_fit(ac_sim* s, long long t_end, bool* fits) {
   return AC_OK;
 }
 
-ac_status run_tb(ac_sim* s, long long t_end) {
+ac_status run_tb(ac_sim* s, long long t_end, int D) {
   const size_t N = s->ncells();
   if (!s->key2) {
     if (cudaMalloc(&s->key2, N * 8) != cudaSuccess || cudaMalloc(&s->cnt2, N * 4) != cudaSuccess) {
@@ -381,7 +390,6 @@ ac_status run_tb(ac_sim* s, long long t_end) {
       return fail(AC_ERR_OOM, "second state buffer (%zu cells) allocation failed", N);
     }
   }
-  const int D = s->cfg.rounds;
   const int region = ac::tb_region_for(D);
   int tr = 0, tc = 0;
   tb_tiling(s->rows, s->cols, region, D, ac::tb_grid(region), &tr, &tc);
@@ -398,7 +406,7 @@ ac_status run_tb(ac_sim* s, long long t_end) {
   int launch_idx = 0;
   for (;;) {
     for (int i = 0; i < chunk; ++i) {
-      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, D, s->d_ctr, s->stream, s->f_B > 0));
+      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, D, s->d_ctr, s->stream, s->f_B > 0, s->model == 1));
       ++launch_idx;
     }
     ac::DevCounters cc{};
@@ -429,11 +437,21 @@ ac_status run_tb(ac_sim* s, long long t_end) {
 }
 
 ac_status run_round(ac_sim* s, long long t_end) {
+  if (s->model == 1) {
+    // the Life automaton runs on the temporal-blocked kernel only (its enable test needs
+    // the diagonal neighbours, which the region holds): halo depth capped by the lattice
+    const int D = std::max(1, std::min(s->cfg.rounds, std::min(s->rows, s->cols) / 4));
+    bool fits = false;
+    ac_status st = tb_counts_fit(s, t_end, &fits);
+    if (st != AC_OK) return st;
+    if (!fits) return fail(AC_ERR_STATE, "Life: event counts too uneven for the temporal-blocked kernel");
+    return run_tb(s, t_end, D);
+  }
   if (tb_applicable(s)) {
     bool fits = false;
     ac_status st = tb_counts_fit(s, t_end, &fits);
     if (st != AC_OK) return st;
-    if (fits) return run_tb(s, t_end);
+    if (fits) return run_tb(s, t_end, s->cfg.rounds);
     // counts too uneven for the 16-bit window: one exact synchronous round per launch
     const int saved = s->cfg.rounds;
     s->cfg.rounds = 1;
@@ -733,6 +751,34 @@ ac_status ac_create(ac_lattice lat, double beta, double J, double h, uint64_t se
   return create_one(lat, beta, J, h, seed, out);
 }
 
+ac_status ac_create_life(ac_lattice lat, uint32_t density, uint32_t birth, uint32_t survive, uint64_t seed,
+                         ac_sim** out) {
+  if (!out) return fail(AC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (lat.rows < 4 || lat.cols < 4) return fail(AC_ERR_ARG, "Life needs rows, cols >= 4 (got %d x %d)", lat.rows, lat.cols);
+  if (birth > 0x1FFu || survive > 0x1FFu) return fail(AC_ERR_ARG, "birth and survive are 9-bit masks (bits 0..8)");
+  ac_status st = check_params(lat, 0.0, 0.0, 0.0);
+  if (st != AC_OK) return st;
+  st = create_one(lat, 0.0, 0.0, 0.0, seed, out);
+  if (st != AC_OK) return st;
+  ac_sim* s = *out;
+  s->model = 1;
+  s->life_birth = birth;
+  s->life_survive = survive;
+  s->life_density = density;
+  s->cfg.kernel = ac::kKernelRound;
+  s->cfg.rounds = 6;
+  const ac::LatDesc d = s->host_desc(0, 0);
+  cudaError_t e = ac::launch_init(&d, lat.init, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    free_sim(s);
+    *out = nullptr;
+    return fail(AC_ERR_CUDA, "Life initialisation failed: %s", cudaGetErrorString(e));
+  }
+  return AC_OK;
+}
+
 ac_status ac_set_stream(ac_sim* sim, void* stream) {
   if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
   sim->stream = (cudaStream_t)stream;
@@ -747,6 +793,8 @@ ac_status ac_configure(ac_sim* sim, int32_t kernel, int32_t Lb, int32_t rounds, 
   if (Lb != 32 && Lb != 64 && Lb != 128) return fail(AC_ERR_ARG, "Lb must be 32, 64 or 128");
   if (rounds < 1 || rounds > 1 << 20) return fail(AC_ERR_ARG, "rounds must be in [1, 2^20]");
   if (polls < 0 || polls > 1 << 20) return fail(AC_ERR_ARG, "polls must be in [0, 2^20]");
+  if (sim->model == 1 && kernel != AC_KERNEL_ROUND)
+    return fail(AC_ERR_ARG, "the Life automaton runs on the round kernel (AC_KERNEL_ROUND) only");
   sim->cfg.kernel = kernel;
   sim->cfg.lb = Lb;
   sim->cfg.threads = 4 * Lb;
@@ -1021,6 +1069,7 @@ ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_en
   for (int i = 0; i < n; ++i) {
     if (!sims[i]) return fail(AC_ERR_ARG, "sims[%d] is NULL", i);
     if (sims[i]->f_B > 0) return fail(AC_ERR_ARG, "sims[%d] has snapshot frames: run it with ac_run_until_frames", i);
+    if (sims[i]->model != 0) return fail(AC_ERR_ARG, "sims[%d] is a Life automaton: batches hold Ising lattices", i);
     if (sims[i]->cfg.lb != sims[0]->cfg.lb) return fail(AC_ERR_ARG, "all handles must share a tile side");
     if (sims[i]->stream != sims[0]->stream) return fail(AC_ERR_ARG, "all handles must share a stream");
     if (t_end[i] < sims[i]->t_done) return fail(AC_ERR_ARG, "t_end[%d] is below its previous t_end", i);

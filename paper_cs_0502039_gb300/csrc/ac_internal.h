@@ -41,6 +41,11 @@ struct LatDesc {
   signed char* frames;
   long long f_t0, f_dt;
   int f_open, f_slot0, f_B;
+  // model: 0 = Ising heat bath (thr = flip thresholds); 1 = Life-like automaton on the
+  // Moore neighbourhood (thr[0] = birth mask, thr[1] = survival mask over the number of
+  // live neighbours; a random initial cell is alive iff its init word < life_density)
+  int model;
+  unsigned life_density;
 };
 
 // Device counters of one run call (zeroed by the host before the call).
@@ -100,9 +105,10 @@ cudaError_t launch_pack(const LatDesc* host_desc, const int8_t* s_in, const long
 // Launch of the temporal-blocked round kernel.  The launch number (which fixes the
 // ping-pong parity) is kept on the device in ctr->seq, so every launch of a run has
 // the same arguments and a sequence of launches can be captured in a CUDA graph.
-// frames: the lattices have open snapshot frames (the kernel variant that writes them).
+// frames: the lattices have open snapshot frames (the kernel variant that writes them);
+// life: the lattices hold the Life-like automaton (all lattices of a launch share the model).
 cudaError_t launch_tb(const LatDesc* d_desc, int nlat, int total_tiles, int region, int halo, int rounds,
-                      DevCounters* ctr, cudaStream_t s, bool frames = false);
+                      DevCounters* ctr, cudaStream_t s, bool frames = false, bool life = false);
 // Frames [K, K + count) were just opened: write each cell's spin into those whose tick
 // lies before the cell's next arrival (later commits write the others).
 cudaError_t launch_frames_fill(const LatDesc* host_desc, long long K, int count, cudaStream_t s);

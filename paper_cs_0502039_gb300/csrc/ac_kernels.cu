@@ -382,7 +382,10 @@ __global__ void init_kernel(LatDesc L, int init_mode) {
     unsigned up;
     if (init_mode == 1) up = 1u;
     else if (init_mode == 2) up = 0u;
-    else up = philox_event((uint32_t)c, 0u, 1u, L.seed_lo, L.seed_hi).x & 1u;
+    else {
+      const uint32_t x = philox_event((uint32_t)c, 0u, 1u, L.seed_lo, L.seed_hi).x;
+      up = L.model ? (x < L.life_density ? 1u : 0u) : (x & 1u);   // Life: alive with the given density
+    }
     L.key[c] = (exp_ticks(b0.x, L.two) << 1) | up;
     L.cnt[c] = 0u;
   }
@@ -668,8 +671,101 @@ __device__ __forceinline__ int wrap_index(int x, int n, int& shift, int up_shift
   return x;
 }
 
+// ---- Life-like automaton on the Moore neighbourhood (the deterministic update of
+// Sec. 3, e.g. Conway's Game of Life): a cell may commit once its key is below the
+// keys of all 8 Moore neighbours (its update reads all of them), so enabled cells
+// are pairwise at Chebyshev distance >= 2 and the same shrinking-region argument as
+// for the 4-neighbour array holds.
+
+// live cells among the 8 Moore neighbours of the region cell at kp
+template <int RW>
+__device__ __forceinline__ unsigned moore_live(const unsigned long long* kp) {
+  return ((unsigned)kp[-RW - 1] & 1u) + ((unsigned)kp[-RW] & 1u) + ((unsigned)kp[-RW + 1] & 1u) +
+         ((unsigned)kp[-1] & 1u) + ((unsigned)kp[1] & 1u) + ((unsigned)kp[RW - 1] & 1u) +
+         ((unsigned)kp[RW] & 1u) + ((unsigned)kp[RW + 1] & 1u);
+}
+
+// Enable test of a thread's column pair (pc, pc + 1) over ROWS region rows from rbase,
+// for a region that does not wrap: region row-major order is the index order, so a
+// neighbour in the row above or to the left needs tick_c < tick_n ((key_c | 1) < key_n)
+// and one below or to the right tick_c <= tick_n ((key_c & ~1) <= key_n).  The relations
+// between a row and the row below are carried to the next row (complemented).
+template <int RW, int ROWS>
+__device__ __forceinline__ unsigned life_scan(const unsigned long long* K, int rbase, int pc,
+                                              unsigned long long t2) {
+  const unsigned long long* q = K + rbase * RW + pc;
+  ulonglong2 mv = *reinterpret_cast<const ulonglong2*>(q);
+  unsigned long long m0 = q[-1], m3 = q[2];
+  // up-row relations of the first row
+  const ulonglong2 uv = *reinterpret_cast<const ulonglong2*>(q - RW);
+  const unsigned long long u0 = q[-RW - 1], u3 = q[-RW + 2];
+  bool a_u1 = (mv.x | 1ull) < uv.x, a_u2 = (mv.x | 1ull) < uv.y;   // a before its up, up-right
+  bool b_u1 = (mv.y | 1ull) < uv.x, b_u2 = (mv.y | 1ull) < uv.y;   // b before its up-left, up
+  bool a_u0 = (mv.x | 1ull) < u0, b_u3 = (mv.y | 1ull) < u3;
+  unsigned mask = 0;
+#pragma unroll
+  for (int i = 0; i < ROWS; ++i) {
+    const unsigned long long* qd = q + (i + 1) * RW;
+    const ulonglong2 dv = *reinterpret_cast<const ulonglong2*>(qd);
+    const unsigned long long d0 = qd[-1], d3 = qd[2];
+    const unsigned long long loa = mv.x & ~1ull, lob = mv.y & ~1ull;
+    const unsigned long long hia = mv.x | 1ull, hib = mv.y | 1ull;
+    const bool a_d0 = loa <= d0, a_d1 = loa <= dv.x, a_d2 = loa <= dv.y;
+    const bool b_d1 = lob <= dv.x, b_d2 = lob <= dv.y, b_d3 = lob <= d3;
+    const bool ab = loa <= mv.y;
+    const bool ea = (mv.x < t2) & a_u0 & a_u1 & a_u2 & (hia < m0) & ab & a_d0 & a_d1 & a_d2;
+    const bool eb = (mv.y < t2) & b_u1 & b_u2 & b_u3 & !ab & (lob <= m3) & b_d1 & b_d2 & b_d3;
+    mask |= ((unsigned)ea << (2 * i)) | ((unsigned)eb << (2 * i + 1));
+    // next row: its a sits below a, its b below b; up-left of a and up-right of b are new
+    const ulonglong2 nv = dv;
+    a_u1 = !a_d1;
+    a_u2 = !b_d1;
+    b_u1 = !a_d2;
+    b_u2 = !b_d2;
+    a_u0 = (nv.x | 1ull) < m0;
+    b_u3 = (nv.y | 1ull) < m3;
+    mv = nv;
+    m0 = d0;
+    m3 = d3;
+  }
+  return mask;
+}
+
+// The same test for a region that wraps across the torus seam: ticks compared
+// directly, equal ticks ordered by the cells' lattice indices.
+template <int RW, int ROWS>
+__device__ __forceinline__ unsigned life_scan_exact(const unsigned long long* K, const unsigned* rowoff,
+                                                    const unsigned* colg, int rbase, int pc,
+                                                    unsigned long long t2) {
+  unsigned mask = 0;
+  for (int i = 0; i < ROWS; ++i) {
+    const int r = rbase + i;
+    for (int e = 0; e < 2; ++e) {
+      const int c = pc + e;
+      if (r > RW - 1 || c < 1 || c > RW - 2) continue;   // never a valid cell (masked by the caller)
+      const unsigned long long kc = K[r * RW + c];
+      const unsigned long long tc = kc >> 1;
+      const unsigned gc = rowoff[r] + colg[c];
+      bool ok = kc < t2;
+#pragma unroll
+      for (int dr = -1; dr <= 1; ++dr)
+#pragma unroll
+        for (int dc = -1; dc <= 1; ++dc) {
+          if (dr == 0 && dc == 0) continue;
+          const unsigned long long tn = K[(r + dr) * RW + c + dc] >> 1;
+          const unsigned gn = rowoff[r + dr] + colg[c + dc];
+          ok &= (tc < tn) || (tc == tn && gc < gn);
+        }
+      mask |= (unsigned)ok << (2 * i + e);
+    }
+  }
+  return mask;
+}
+
 // FR: snapshot frames are open (write_frames for the tile's own cells).
-template <int RW, bool FR>
+// LIFE: the Life-like automaton (Moore neighbourhood, birth / survival masks in
+// thr[0] / thr[1]) instead of the Ising heat bath.
+template <int RW, bool FR, bool LIFE>
 __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     tb_kernel(const LatDesc* __restrict__ lats, int nlat, int total_tiles, int D, int R, DevCounters* ctr) {
   using Cfg = TbCfg<RW>;
@@ -715,7 +811,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     unsigned long long* key_out = parity ? L.key : L.key2;
     unsigned int* cnt_out = parity ? L.cnt : L.cnt2;
     const int RH = g.h + 2 * D, RC = g.w + 2 * D;
-    const bool edge = (g.ti == 0) || (g.ti == L.tr - 1) || (g.tj == 0) || (g.tj == L.tc - 1);
+    // the region wraps across the torus seam (small tiles of interior positions can too)
+    const bool edge = (g.r0 < D) || (g.r0 + g.h + D > L.rows) || (g.c0 < D) || (g.c0 + g.w + D > L.cols);
     // counts are kept as 16-bit offsets from a window start taken at the tile centre
     const unsigned ccen = __ldg(&cnt_in[(size_t)(g.r0 + g.h / 2) * L.cols + g.c0 + g.w / 2]);
     const unsigned base = ccen > 32768u ? ccen - 32768u : 0u;
@@ -772,7 +869,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     if (over) atomicOr(s_over, 1u);
     cp_async_wait_all();
     __syncthreads();
-    if (edge) {   // halo cells from across the torus seam: key +-2 (one tick of tie order)
+    if (edge && !LIFE) {   // halo cells from across the torus seam: key +-2 (one tick of tie order)
       if (lj < RC) {
         for (int i = li0; i < RH; i += Cfg::LSTRIDE) {
           int shr;
@@ -806,7 +903,12 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       }
       const unsigned valid = colm & rowm;
       unsigned mask = 0;
-      if (valid) {
+      if (LIFE && valid) {
+        mask = edge ? life_scan_exact<RW, Cfg::ROWS>(K, rowoff, colg, rbase, pc, t2)
+                    : life_scan<RW, Cfg::ROWS>(K, rbase, pc, t2);
+        mask &= valid;
+        scanned += (unsigned long long)__popc(valid);
+      } else if (valid) {
         const unsigned long long* q = K + rbase * RW + pc;
         ulonglong2 cv = *reinterpret_cast<const ulonglong2*>(q);
         const ulonglong2 uv = *reinterpret_cast<const ulonglong2*>(q - RW);
@@ -861,19 +963,28 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         unsigned long long* kpa = K + ra * RW + ca;
         unsigned long long* kpb = K + rb * RW + cb;
         const unsigned long long keya = *kpa, keyb = *kpb;
-        const unsigned ja = ((unsigned)kpa[-RW] & 1u) + ((unsigned)kpa[RW] & 1u) + ((unsigned)kpa[-1] & 1u) +
-                            ((unsigned)kpa[1] & 1u);
-        const unsigned jb = ((unsigned)kpb[-RW] & 1u) + ((unsigned)kpb[RW] & 1u) + ((unsigned)kpb[-1] & 1u) +
-                            ((unsigned)kpb[1] & 1u);
         const unsigned spa = (unsigned)keya & 1u, spb = (unsigned)keyb & 1u;
         const uint32_t gia = rowoff[ra] + colg[ca], gib = rowoff[rb] + colg[cb];
         const unsigned c16a = C[ra * RW + ca], c16b = C[rb * RW + cb];
-        const unsigned tha = thr[ja + 5u * spa], thb = thr[jb + 5u * spb];
+        unsigned tha, thb;
+        if (LIFE) {   // rule mask of the current state; the new state is its bit k
+          tha = thr[spa];
+          thb = thr[spb];
+        } else {
+          const unsigned ja = ((unsigned)kpa[-RW] & 1u) + ((unsigned)kpa[RW] & 1u) + ((unsigned)kpa[-1] & 1u) +
+                              ((unsigned)kpa[1] & 1u);
+          const unsigned jb = ((unsigned)kpb[-RW] & 1u) + ((unsigned)kpb[RW] & 1u) + ((unsigned)kpb[-1] & 1u) +
+                              ((unsigned)kpb[1] & 1u);
+          tha = thr[ja + 5u * spa];
+          thb = thr[jb + 5u * spb];
+        }
         const Philox4 pa = philox_event(gia, base + c16a + 1u, 0u, seed_lo, seed_hi);
         const Philox4 pb = philox_event(gib, base + c16b + 1u, 0u, seed_lo, seed_hi);
         const unsigned long long gapa = exp_ticks(pa.x, two), gapb = exp_ticks(pb.x, two);
-        const unsigned long long nka = (keya & ~1ull) + (gapa << 1) + (spa ^ (pa.y < tha ? 1u : 0u));
-        const unsigned long long nkb = (keyb & ~1ull) + (gapb << 1) + (spb ^ (pb.y < thb ? 1u : 0u));
+        const unsigned nsa = LIFE ? (tha >> moore_live<RW>(kpa)) & 1u : spa ^ (pa.y < tha ? 1u : 0u);
+        const unsigned nsb = LIFE ? (thb >> moore_live<RW>(kpb)) & 1u : spb ^ (pb.y < thb ? 1u : 0u);
+        const unsigned long long nka = (keya & ~1ull) + (gapa << 1) + nsa;
+        const unsigned long long nkb = (keyb & ~1ull) + (gapb << 1) + nsb;
         *kpa = nka;
         *kpb = nkb;
         C[ra * RW + ca] = (unsigned short)(c16a + 1u);
@@ -890,14 +1001,19 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const int r = (int)(e >> 8), cc = (int)(e & 255u);
         unsigned long long* kp = K + r * RW + cc;
         const unsigned long long key = *kp;
-        const unsigned j = ((unsigned)kp[-RW] & 1u) + ((unsigned)kp[RW] & 1u) + ((unsigned)kp[-1] & 1u) +
-                           ((unsigned)kp[1] & 1u);
         const unsigned sp = (unsigned)key & 1u;
         const uint32_t gidx = rowoff[r] + colg[cc];
         const unsigned c16 = C[r * RW + cc];
         const Philox4 b = philox_event(gidx, base + c16 + 1u, 0u, seed_lo, seed_hi);
-        const unsigned flip = b.y < thr[j + 5u * sp] ? 1u : 0u;
-        const unsigned long long nk = (key & ~1ull) + (exp_ticks(b.x, two) << 1) + (sp ^ flip);
+        unsigned ns;
+        if (LIFE) {
+          ns = (thr[sp] >> moore_live<RW>(kp)) & 1u;
+        } else {
+          const unsigned j = ((unsigned)kp[-RW] & 1u) + ((unsigned)kp[RW] & 1u) + ((unsigned)kp[-1] & 1u) +
+                             ((unsigned)kp[1] & 1u);
+          ns = sp ^ (b.y < thr[j + 5u * sp] ? 1u : 0u);
+        }
+        const unsigned long long nk = (key & ~1ull) + (exp_ticks(b.x, two) << 1) + ns;
         *kp = nk;
         C[r * RW + cc] = (unsigned short)(c16 + 1u);
         if (FR && r >= D && r < D + g.h && cc >= D && cc < D + g.w)
@@ -1243,31 +1359,37 @@ cudaError_t launch_pack(const LatDesc* h, const int8_t* si, const long long* ti,
 }
 
 
-template <int RW, bool FR>
+template <int RW, bool FR, bool LIFE>
 cudaError_t tb_launch_rw(const LatDesc* d, int nlat, int total, int halo, int rounds, DevCounters* ctr,
                          cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW, FR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW, FR, LIFE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)TbCfg<RW>::bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int grid = std::min(total, tb_grid(RW));
-  tb_kernel<RW, FR><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds, ctr);
+  tb_kernel<RW, FR, LIFE><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds, ctr);
   return cudaGetLastError();
 }
 
+template <int RW>
+cudaError_t tb_launch_model(const LatDesc* d, int nlat, int total, int halo, int rounds, DevCounters* ctr,
+                            cudaStream_t s, bool frames, bool life) {
+  if (life)
+    return frames ? tb_launch_rw<RW, true, true>(d, nlat, total, halo, rounds, ctr, s)
+                  : tb_launch_rw<RW, false, true>(d, nlat, total, halo, rounds, ctr, s);
+  return frames ? tb_launch_rw<RW, true, false>(d, nlat, total, halo, rounds, ctr, s)
+                : tb_launch_rw<RW, false, false>(d, nlat, total, halo, rounds, ctr, s);
+}
+
 cudaError_t launch_tb(const LatDesc* d, int nlat, int total, int region, int halo, int rounds, DevCounters* ctr,
-                      cudaStream_t s, bool frames) {
+                      cudaStream_t s, bool frames, bool life) {
   if (halo < 1 || rounds < 1 || rounds > halo || 4 * halo >= region) return cudaErrorInvalidValue;
   switch (region) {
-    case 96:
-      return frames ? tb_launch_rw<96, true>(d, nlat, total, halo, rounds, ctr, s)
-                    : tb_launch_rw<96, false>(d, nlat, total, halo, rounds, ctr, s);
-    case 128:
-      return frames ? tb_launch_rw<128, true>(d, nlat, total, halo, rounds, ctr, s)
-                    : tb_launch_rw<128, false>(d, nlat, total, halo, rounds, ctr, s);
+    case 96: return tb_launch_model<96>(d, nlat, total, halo, rounds, ctr, s, frames, life);
+    case 128: return tb_launch_model<128>(d, nlat, total, halo, rounds, ctr, s, frames, life);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -40,8 +40,8 @@ MUTANTS = {
                              "uint32_t n0 = (uint32_t)(p1 >> 32) ^ c3 ^ k0;",
                              lambda: phx.test_philox_matches_triton(7)),
     "log_bit_dropped": ("f |= 1ull;", "f |= 0ull;", ext.test_exp_ticks_error_bound_and_positivity),
-    "first_gap_from_init_block": ("philox_block(seed, (uint32_t)c, 0u, 0u, b0);",
-                                  "philox_block(seed, (uint32_t)c, 0u, 1u, b0);",
+    "first_gap_from_init_block": ("philox_block(seed, (uint32_t)c, 0u, 0u, b0);\n        if (init == 1)\n            s[c] = 1;\n        else if (init == 2)\n            s[c] = -1;\n        else {\n            philox_block(seed, (uint32_t)c, 0u, 1u, ib);\n            s[c] = (ib[0] & 1u)",
+                                  "philox_block(seed, (uint32_t)c, 0u, 1u, b0);\n        if (init == 1)\n            s[c] = 1;\n        else if (init == 2)\n            s[c] = -1;\n        else {\n            philox_block(seed, (uint32_t)c, 0u, 1u, ib);\n            s[c] = (ib[0] & 1u)",
                                   lambda: dyn.test_heap_equals_linear_scan(2, 3, 2, 0.7, 0.2, 6)),
 }
 
