@@ -7,7 +7,14 @@
 // smaller row-major index goes first); the result is the unique trajectory of
 // the standard serial procedure (Sec. 1) whatever the execution schedule.
 //
-// Shared-memory tile engine (used by both kernels).  A CTA holds one tile of at
+// Kernels: the round kernel (a), one synchronous round per launch or, with
+// temporal blocking, R rounds per launch (the path the throughput figures use);
+// the blocked persistent kernel (b); the initialisation, statistics and
+// state-transfer kernels; the frame fill; device-primitive probes.  The
+// temporal-blocked kernel also runs the Life-like automaton (Moore neighbourhood)
+// and writes snapshot frames (Fig. 3.7) when they are open.
+//
+// Shared-memory tile engine (used by the one-round and blocked kernels).  A CTA holds one tile of at
 // most LB x LB cells: the packed keys with a one-cell halo ring, the event
 // counts and a compacted work list.  One tile round is
 //   scan    every thread walks a column segment and tests its cells against
@@ -614,19 +621,21 @@ __global__ void __launch_bounds__(4 * LB) blocked_kernel(const LatDesc* __restri
 
 
 // ----------------------------------------------------------------------------
-// (a) Temporal-blocked round kernel.  A CTA loads a 128 x 128 region -- its tile
-// of side 128 - 2D plus a halo of depth D around it, wrapped on the torus -- from
-// the input state buffer, runs R <= D synchronous rounds in shared memory and
-// writes the tile to the output buffer (ping-pong, so every launch reads one
-// consistent state).  Round k scans the region minus its outer k rings: a cell at
-// distance d from the region's edge follows the global synchronous schedule for d
-// rounds, so after R rounds the tile is exactly where R global rounds of Fig. 3.2
-// would put it, while the halo's commits (redundant with the neighbouring tiles)
-// are discarded.  Halo cells that come from across the torus seam carry key + 2
-// (seam above / left of the tile) or key - 2 (below / right): comparisons between
-// two cells on the same side are unchanged, and between the sides they give the
-// (tick, index) order of the seam.  Requires rows, cols >= 4D (the region never
-// overlaps itself).
+// (a) Temporal-blocked round kernel.  A CTA loads an RW x RW region (RW = 96, two
+// CTAs per SM, or 128, one) -- its tile of side at most RW - 2D plus a halo of depth
+// D around it, wrapped on the torus -- from the input state buffer, runs R <= D
+// synchronous rounds in shared memory and writes the tile to the output buffer
+// (ping-pong, so every launch reads one consistent state).  Round k scans the
+// region minus its outer k rings: a cell at distance d from the region's edge
+// follows the global synchronous schedule for d rounds, so after R rounds the tile
+// is exactly where R global rounds of Fig. 3.2 would put it, while the halo's
+// commits (redundant with the neighbouring tiles) are discarded.  In a region that
+// wraps, halo cells from across the torus seam carry key + 2 (seam above / left of
+// the tile) or key - 2 (below / right): comparisons between two cells on the same
+// side are unchanged, and between the sides they give the (tick, index) order of
+// the seam (the Life variant compares lattice indices there instead).  Counts are
+// held as 16-bit offsets from the tile centre's count.  Requires rows, cols >= 4D
+// (the region never overlaps itself).
 template <int RW>
 struct TbCfg {
   static constexpr int PAIRS = RW / 2;            // a thread scans a column pair ...
