@@ -360,6 +360,16 @@ void tb_tiling(int rows, int cols, int region, int halo, int sms, int* tr, int* 
     }
 }
 
+// Tile grid of a lattice inside a batch: the fewest tiles (side <= region - 2D, at
+// least 2 per dimension).  Every tile visit costs a region load, R rounds and a store
+// whatever the tile's size, and the whole batch's tile list fills the waves, so the
+// tile count, not one lattice's wave balance, sets the time.
+void tb_tiling_batch(int rows, int cols, int region, int halo, int* tr, int* tc) {
+  const int own = region - 2 * halo;
+  *tr = std::max(2, ceil_div(rows, own));
+  *tc = std::max(2, ceil_div(cols, own));
+}
+
 bool tb_applicable(const ac_sim* s) {
   const int D = s->cfg.rounds;
   return s->cfg.rounds > 1 && D <= ac::kTbMaxHalo && s->rows >= 4 * D && s->cols >= 4 * D;
@@ -568,7 +578,7 @@ ac_status batch_run_tb(int32_t n, ac_sim* const* sims, const int64_t* t_end, Bat
   double span = 0.0;
   for (int i = 0; i < n; ++i) {
     int tr = 0, tc = 0;
-    tb_tiling(sims[i]->rows, sims[i]->cols, R->region, R->halo, ac::tb_grid(R->region), &tr, &tc);
+    tb_tiling_batch(sims[i]->rows, sims[i]->cols, R->region, R->halo, &tr, &tc);
     R->h_desc[i] = sims[i]->host_desc(t_end[i], base);
     R->h_desc[i].tr = tr;
     R->h_desc[i].tc = tc;
