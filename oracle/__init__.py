@@ -106,8 +106,8 @@ def _bind(lib):
     lib.aco_life_run.restype = ctypes.c_int64
     lib.aco_gap.argtypes = [ctypes.c_int32, ctypes.c_uint32]
     lib.aco_gap.restype = ctypes.c_uint64
-    lib.aco_time_model.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
-                                   ctypes.c_int64, ctypes.c_int64, P, P, P]
+    lib.aco_time_model.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, P, P, P]
     lib.aco_time_model.restype = ctypes.c_int64
     return lib
 
@@ -262,19 +262,21 @@ def gap(law: int, x: int) -> int:
     return int(_load().aco_gap(int(law), int(x) & 0xFFFFFFFF))
 
 
-def time_model(dims: int, n: int, law: int, seed: int, t_end: int, max_rounds: int):
+def time_model(dims: int, n: int, law: int, seed: int, t_end: int, max_rounds: int, q: int = 1):
     """Time-only round model of Sec. 4 on an n-cell circle (dims 1), n x n torus (2) or n^3
-    periodic array (3): returns (advancing cells per round, final ticks, final counts)."""
+    periodic array (3), with the q-th degree neighbourhood of Sec. 3 (every cell within
+    Manhattan distance q; q = 1 is the nearest neighbours): returns (advancing cells per
+    round, final ticks, final counts)."""
     N = n ** dims
     en = np.zeros(max(1, max_rounds), dtype=np.int64)
     t = np.zeros(N, dtype=np.int64)
     cnt = np.zeros(N, dtype=np.uint32)
-    r = _load().aco_time_model(int(dims), int(n), int(law), int(seed) & (2**64 - 1), int(t_end),
+    r = _load().aco_time_model(int(dims), int(n), int(q), int(law), int(seed) & (2**64 - 1), int(t_end),
                                int(max_rounds), _ptr(en), _ptr(t), _ptr(cnt))
     if r == -1:
         raise MemoryError("oracle allocation failed")
     if r < 0:
-        raise ValueError("dims must be 1..3, n >= 2, law 0..2")
+        raise ValueError("dims must be 1..3, n >= 2, law 0..2, q in 1..8 with n >= 2q+1")
     return en[:r].copy(), t, cnt
 
 

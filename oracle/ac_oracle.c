@@ -359,8 +359,10 @@ int64_t aco_time_rounds(int32_t rows, int32_t cols, uint64_t seed, int64_t *t, u
 /* n-cell circle, an n x n torus and an n x n x n periodic array, with  */
 /* exponential or uniform increments, and the r^(1/8) increments of the */
 /* same section).  Times only: a cell advances in a round iff its key   */
-/* (t, index) is below the keys of all its 2*dims neighbours (R1) and   */
-/* t < t_end; advancing cells draw their next increment afterwards.     */
+/* (t, index) is below the keys of all its neighbours -- the 2*dims     */
+/* nearest ones, or every cell within Manhattan distance q for the q-th */
+/* degree neighbourhood of Sec. 3 (n >= 2q+1) -- (R1) and t < t_end;    */
+/* advancing cells draw their next increment afterwards.                */
 /*                                                                      */
 /* Increment laws (reading R11), from the 32-bit word x = B(c, k).x:    */
 /*   0  exponential: exp_ticks(x) (R5)                                  */
@@ -398,7 +400,10 @@ uint64_t aco_gap(int32_t law, uint32_t x)
     return isqrt64(s2 << 32);
 }
 
-static void neighbours_nd(int32_t dims, int64_t n, uint64_t c, uint64_t nb[6])
+/* The q-th degree neighbourhood of Sec. 3 (neighbours of neighbours, q times):   */
+/* every cell within Manhattan distance 1..q on the periodic array.  Writes the   */
+/* neighbour indices to nb[] and returns their number (2 dims for q = 1).         */
+static int neighbours_nd(int32_t dims, int64_t n, int32_t q, uint64_t c, uint64_t *nb)
 {
     int64_t coord[3] = {0, 0, 0}, stride[3] = {1, n, n * n};
     uint64_t rest = c;
@@ -406,17 +411,27 @@ static void neighbours_nd(int32_t dims, int64_t n, uint64_t c, uint64_t nb[6])
         coord[a] = (int64_t)(rest % (uint64_t)n);
         rest /= (uint64_t)n;
     }
-    for (int a = 0; a < dims; ++a) {
-        int64_t lo = (coord[a] - 1 + n) % n, hi = (coord[a] + 1) % n;
-        nb[2 * a] = c - (uint64_t)(coord[a] * stride[a]) + (uint64_t)(lo * stride[a]);
-        nb[2 * a + 1] = c - (uint64_t)(coord[a] * stride[a]) + (uint64_t)(hi * stride[a]);
-    }
+    int m = 0;
+    int64_t lim[3] = {q, dims > 1 ? q : 0, dims > 2 ? q : 0};
+    for (int64_t dz = -lim[2]; dz <= lim[2]; ++dz)
+        for (int64_t dy = -lim[1]; dy <= lim[1]; ++dy)
+            for (int64_t dx = -lim[0]; dx <= lim[0]; ++dx) {
+                int64_t dist = (dx < 0 ? -dx : dx) + (dy < 0 ? -dy : dy) + (dz < 0 ? -dz : dz);
+                if (dist == 0 || dist > q) continue;
+                int64_t d[3] = {dx, dy, dz};
+                uint64_t idx = 0;
+                for (int a = 0; a < dims; ++a)
+                    idx += (uint64_t)(((coord[a] + d[a]) % n + n) % n * stride[a]);
+                nb[m++] = idx;
+            }
+    return m;
 }
 
-int64_t aco_time_model(int32_t dims, int64_t n, int32_t law, uint64_t seed, int64_t t_end,
+int64_t aco_time_model(int32_t dims, int64_t n, int32_t q, int32_t law, uint64_t seed, int64_t t_end,
                        int64_t max_rounds, int64_t *enabled, int64_t *t_out, uint32_t *n_out)
 {
-    if (dims < 1 || dims > 3 || n < 2 || law < 0 || law > 2) return -2;
+    if (dims < 1 || dims > 3 || n < 2 || law < 0 || law > 2 || q < 1 || q > 8 || (q > 1 && n < 2 * q + 1))
+        return -2;
     uint64_t N = (uint64_t)n;
     for (int a = 1; a < dims; ++a) N *= (uint64_t)n;
     int64_t *t = (int64_t *)malloc(N * sizeof(int64_t));
@@ -435,10 +450,10 @@ int64_t aco_time_model(int32_t dims, int64_t n, int32_t law, uint64_t seed, int6
     while (rounds < max_rounds) {
         int64_t nen = 0;
         for (uint64_t c = 0; c < N; ++c) {
-            uint64_t nb[6];
-            neighbours_nd(dims, n, c, nb);
+            uint64_t nb[2 * 8 * 9 * 17];
+            int m = neighbours_nd(dims, n, q, c, nb);
             int ok = t[c] < t_end;
-            for (int d = 0; d < 2 * dims && ok; ++d)
+            for (int d = 0; d < m && ok; ++d)
                 if (nb[d] != c && !key_less(t, (uint32_t)c, (uint32_t)nb[d])) ok = 0;
             en[c] = (uint8_t)ok;
             nen += ok;

@@ -48,15 +48,19 @@ def test_root8_steps_by_python_integers():
         assert oracle.gap(oracle.LAW_ROOT8, x) == _isqrt_big(s2 << 32)
 
 
-def _brute(dims, n, law, seed, t_end, max_rounds):
+def _brute(dims, n, law, seed, t_end, max_rounds, q=1):
     N = n ** dims
     idx = np.arange(N)
     coords = [(idx // n ** a) % n for a in range(dims)]
     nbrs = []
-    for a in range(dims):
-        for d in (-1, 1):
-            nb = idx - coords[a] * n ** a + ((coords[a] + d) % n) * n ** a
-            nbrs.append(nb)
+    import itertools
+    for off in itertools.product(range(-q, q + 1), repeat=dims):
+        if not 0 < sum(abs(o) for o in off) <= q:
+            continue
+        nb = idx.copy()
+        for a, o in enumerate(off):
+            nb = nb - coords[a] * n ** a + ((coords[a] + o) % n) * n ** a
+        nbrs.append(nb)
     t = np.array([oracle.gap(law, int(b[0])) for b in oracle.philox_blocks(seed, idx, np.zeros(N, np.uint32), 0)],
                  dtype=np.int64)
     cnt = np.zeros(N, dtype=np.int64)
@@ -84,6 +88,25 @@ def test_model_equals_brute_force(dims, n, law):
     assert np.array_equal(en, en_b)
     assert np.array_equal(t, t_b) and np.array_equal(cnt, cnt_b)
     assert (t >= t_end).all()
+
+
+@pytest.mark.parametrize("dims,n,q", [(1, 9, 2), (1, 13, 4), (2, 5, 2), (2, 7, 3), (3, 5, 2)])
+def test_q_neighbourhood_equals_brute_force(dims, n, q):
+    """The q-th degree neighbourhood of Sec. 3: every cell within Manhattan distance q."""
+    for law in (0, 2):
+        en, t, cnt = oracle.time_model(dims, n, law, 31, 2 * T32, 10_000, q=q)
+        en_b, t_b, cnt_b = _brute(dims, n, law, 31, 2 * T32, 10_000, q=q)
+        assert np.array_equal(en, en_b)
+        assert np.array_equal(t, t_b) and np.array_equal(cnt, cnt_b)
+
+
+@pytest.mark.parametrize("q", [2, 3])
+def test_q_first_round_fraction(q):
+    """A cell is the strict minimum of itself and its 2q(q+1) neighbours (2D) w.p. 1/(2q(q+1)+1)."""
+    n = 300
+    en, _, _ = oracle.time_model(2, n, 0, 5, 2**61, 1, q=q)
+    p = 1 / (2 * q * (q + 1) + 1)
+    assert abs(en[0] / n**2 - p) < 5 * np.sqrt(p * (1 - p) / n**2) * 2
 
 
 def test_2d_exponential_equals_the_ising_round_model():
