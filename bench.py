@@ -623,6 +623,14 @@ def efficiency_measurement(ac, rounds=2000):
                                  "efficiency_first_round": float(frac[0]), "paper": paper.get((dims, law)),
                                  "advances": int(en.sum()), "device_ms": ms,
                                  "advances_per_s": float(en.sum()) / (ms / 1000.0)})
+    # the q-th degree neighbourhood of Sec. 3: a cell waits for every cell within distance q
+    out["q_neighbourhood"] = []
+    for q in (1, 2, 3, 4):
+        en, _, _, ms = ac.ac_time_model(2, 4096, ac.AC_LAW_EXP, 11, 2**61 - 1, rounds, q=q)
+        frac = en.astype(np.float64) / 4096 ** 2
+        out["q_neighbourhood"].append({"dims": 2, "n": 4096, "q": q, "neighbours": 2 * q * (q + 1),
+                                       "efficiency": float(frac[rounds // 2:].mean()),
+                                       "efficiency_first_round": float(frac[0]), "device_ms": ms})
     return out
 
 

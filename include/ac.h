@@ -231,7 +231,9 @@ ac_status ac_reset(ac_sim* sim, uint64_t seed, int32_t init);
  * torus (2) or an n x n x n periodic array (3), row-major index
  * ((z n) + y) n + x.  Cell c starts at t = gap(B(c, 0).x); in each synchronous
  * round a cell advances iff t < t_end and (t, index) is below the keys of all
- * its 2 dims neighbours (reading R1), drawing its k-th increment from
+ * its neighbours (reading R1) -- the 2 dims nearest cells for q = 1, or, for
+ * q > 1, every cell within Manhattan distance q (the q-th degree neighbourhood
+ * of Sec. 3; needs n >= 2q+1, q <= 8) -- drawing its k-th increment from
  * B(c, k).x, where B(c, k) is Philox4x32-10 of {c, k, 0, 0} under the key
  * (seed lo, seed hi).  Increment laws:
  *   AC_LAW_EXP     exponential: the integer logarithm gap of ac_run_until
@@ -247,7 +249,7 @@ ac_status ac_reset(ac_sim* sim, uint64_t seed, int32_t init);
  * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
  */
 enum { AC_LAW_EXP = 0, AC_LAW_UNIFORM = 1, AC_LAW_ROOT8 = 2 };
-ac_status ac_time_model(int32_t dims, int64_t n, int32_t law, uint64_t seed, int64_t t_end, int32_t max_rounds,
+ac_status ac_time_model(int32_t dims, int64_t n, int32_t q, int32_t law, uint64_t seed, int64_t t_end, int32_t max_rounds,
                         uint64_t* enabled, int32_t* rounds_out, int64_t* t_out, uint32_t* n_out,
                         double* device_ms);
 

@@ -97,7 +97,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ac_frames_status": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)], I32),
         "ac_create_life": ([ac_lattice, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, U64,
                             ctypes.POINTER(P)], I32),
-        "ac_time_model": ([I32, I64, I32, U64, I64, I32, P, ctypes.POINTER(I32), P, P,
+        "ac_time_model": ([I32, I64, I32, I32, U64, I64, I32, P, ctypes.POINTER(I32), P, P,
                            ctypes.POINTER(ctypes.c_double)], I32),
     }
     for name, (args, res) in sig.items():
@@ -264,16 +264,17 @@ def ac_frames_status(sim: int) -> tuple[int, int, int]:
     return K.value, B.value, dt.value
 
 
-def ac_time_model(dims: int, n: int, law: int, seed: int, t_end: int, max_rounds: int, want_state: bool = False):
-    """Time-only round model of Sec. 4 on the GPU: returns (advancing cells per round, final ticks or
-    None, final counts or None, device milliseconds)."""
+def ac_time_model(dims: int, n: int, law: int, seed: int, t_end: int, max_rounds: int, want_state: bool = False,
+                  q: int = 1):
+    """Time-only round model of Sec. 4 on the GPU (neighbourhood: Manhattan radius q): returns
+    (advancing cells per round, final ticks or None, final counts or None, device milliseconds)."""
     en = np.zeros(max_rounds, dtype=np.uint64)
     rounds = ctypes.c_int32()
     ms = ctypes.c_double()
     N = n ** dims
     t = np.empty(N, dtype=np.int64) if want_state else None
     cnt = np.empty(N, dtype=np.uint32) if want_state else None
-    _check(_lib.ac_time_model(int(dims), int(n), int(law), int(seed) & (2**64 - 1), int(t_end), int(max_rounds),
+    _check(_lib.ac_time_model(int(dims), int(n), int(q), int(law), int(seed) & (2**64 - 1), int(t_end), int(max_rounds),
                               _np_ptr(en, np.uint64), ctypes.byref(rounds),
                               None if t is None else _np_ptr(t, np.int64),
                               None if cnt is None else _np_ptr(cnt, np.uint32), ctypes.byref(ms)))

@@ -7,6 +7,9 @@
 // n x n x n periodic array, with exponential and uniform increments (and r^(1/8)),
 // and reports the limiting fraction of cells that advance per round.
 //
+// The neighbourhood is the 2 dims nearest cells, or the q-th degree neighbourhood of
+// Sec. 3 (every cell within Manhattan distance q).
+//
 // One launch per round, ping-pong time buffers (a cell's decision reads its
 // neighbours' times before any of them advances), per-cell counts in place (only
 // the owner touches them), and a per-round count of advancing cells.  Increments
@@ -55,6 +58,7 @@ struct TimeDesc {
   unsigned long long* hist;   // advancing cells per round
   unsigned n, N;
   int law;
+  int q;                      // neighbourhood: every cell within Manhattan distance q
   unsigned seed_lo, seed_hi, two;
   long long t_end;
 };
@@ -69,6 +73,11 @@ __global__ void time_init_kernel(TimeDesc D) {
   }
 }
 
+// key (tc, c) below (tn, nb): the (tick, index) order
+__device__ __forceinline__ bool key_below(long long tc, unsigned c, long long tn, unsigned nb) {
+  return (tc < tn) || (tc == tn && c < nb) || nb == c;
+}
+
 template <int DIMS>
 __global__ void __launch_bounds__(256) time_round_kernel(TimeDesc D, int round) {
   // uniform early exit once a round advanced nothing (the state is then final)
@@ -79,17 +88,44 @@ __global__ void __launch_bounds__(256) time_round_kernel(TimeDesc D, int round) 
     const unsigned c = (unsigned)i;
     const long long tc = D.t_in[c];
     bool ok = tc < D.t_end;
-    unsigned rest = c, stride = 1;
+    unsigned co[3] = {0u, 0u, 0u};
+    {
+      unsigned rest = c;
 #pragma unroll
-    for (int a = 0; a < DIMS; ++a) {
-      const unsigned q = rest % D.n;
-      rest /= D.n;
-      const unsigned lo = c - q * stride + ((q == 0 ? D.n : q) - 1) * stride;
-      const unsigned hi = c - q * stride + ((q + 1 == D.n) ? 0u : q + 1) * stride;
-      const long long tl = D.t_in[lo], th = D.t_in[hi];
-      ok &= (tc < tl) || (tc == tl && c < lo) || lo == c;
-      ok &= (tc < th) || (tc == th && c < hi) || hi == c;
-      stride *= D.n;
+      for (int a = 0; a < DIMS; ++a) {
+        co[a] = rest % D.n;
+        rest /= D.n;
+      }
+    }
+    if (D.q == 1) {
+      unsigned stride = 1;
+#pragma unroll
+      for (int a = 0; a < DIMS; ++a) {
+        const unsigned x = co[a];
+        const unsigned lo = c - x * stride + ((x == 0 ? D.n : x) - 1) * stride;
+        const unsigned hi = c - x * stride + ((x + 1 == D.n) ? 0u : x + 1) * stride;
+        ok &= key_below(tc, c, D.t_in[lo], lo);
+        ok &= key_below(tc, c, D.t_in[hi], hi);
+        stride *= D.n;
+      }
+    } else {
+      // the q-th degree neighbourhood (Sec. 3): all offsets with 0 < |dx|+|dy|+|dz| <= q
+      const int q = D.q;
+      const long long n = (long long)D.n;
+      const int qy = DIMS > 1 ? q : 0, qz = DIMS > 2 ? q : 0;
+      for (int dz = -qz; dz <= qz && ok; ++dz)
+        for (int dy = -qy; dy <= qy && ok; ++dy) {
+          const int rem = q - (dz < 0 ? -dz : dz) - (dy < 0 ? -dy : dy);
+          if (rem < 0) continue;
+          const unsigned zz = DIMS > 2 ? (unsigned)(((long long)co[2] + dz + n) % n) : 0u;
+          const unsigned yy = DIMS > 1 ? (unsigned)(((long long)co[1] + dy + n) % n) : 0u;
+          const unsigned rowbase = (zz * D.n + yy) * D.n;
+          for (int dx = -rem; dx <= rem; ++dx) {
+            if (dx == 0 && dy == 0 && dz == 0) continue;
+            const unsigned nb = rowbase + (unsigned)(((long long)co[0] + dx + n) % n);
+            ok &= key_below(tc, c, D.t_in[nb], nb);
+          }
+        }
     }
     long long tn = tc;
     if (ok) {
@@ -113,12 +149,13 @@ ac_status time_fail(ac_status st, const char* msg) {
 }  // namespace
 }  // namespace ac
 
-extern "C" ac_status ac_time_model(int32_t dims, int64_t n, int32_t law, uint64_t seed, int64_t t_end,
+extern "C" ac_status ac_time_model(int32_t dims, int64_t n, int32_t q, int32_t law, uint64_t seed, int64_t t_end,
                                    int32_t max_rounds, uint64_t* enabled, int32_t* rounds_out, int64_t* t_out,
                                    uint32_t* n_out, double* device_ms) {
   using namespace ac;
   if (dims < 1 || dims > 3) return time_fail(AC_ERR_ARG, "dims must be 1, 2 or 3");
   if (n < 2) return time_fail(AC_ERR_ARG, "n must be >= 2");
+  if (q < 1 || q > 8 || (q > 1 && n < 2 * q + 1)) return time_fail(AC_ERR_ARG, "q must be in 1..8 with n >= 2q+1");
   if (law < AC_LAW_EXP || law > AC_LAW_ROOT8) return time_fail(AC_ERR_ARG, "law must be 0, 1 or 2");
   if (max_rounds < 1 || !enabled || !rounds_out) return time_fail(AC_ERR_ARG, "max_rounds >= 1, enabled and rounds_out are required");
   if (t_end < 0) return time_fail(AC_ERR_ARG, "t_end must be >= 0");
@@ -159,6 +196,7 @@ extern "C" ac_status ac_time_model(int32_t dims, int64_t n, int32_t law, uint64_
     D.n = (unsigned)n;
     D.N = N;
     D.law = law;
+    D.q = q;
     D.seed_lo = (unsigned)(seed & 0xffffffffu);
     D.seed_hi = (unsigned)(seed >> 32);
     D.two = 2u;

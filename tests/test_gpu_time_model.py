@@ -30,6 +30,15 @@ def test_time_model_matches_oracle(dims, n, law):
     assert np.array_equal(t, t_ref) and np.array_equal(cnt, cnt_ref)
 
 
+@pytest.mark.parametrize("dims,n,q", [(1, 2001, 2), (1, 999, 5), (2, 41, 2), (2, 33, 3), (3, 11, 2)])
+def test_q_neighbourhood_matches_oracle(dims, n, q):
+    for law in (0, 1):
+        en_ref, t_ref, cnt_ref = oracle.time_model(dims, n, law, 77, 3 * T32, 100_000, q=q)
+        en, t, cnt, _ = ac.ac_time_model(dims, n, law, 77, 3 * T32, 100_000, want_state=True, q=q)
+        assert np.array_equal(en.astype(np.int64), en_ref), (dims, n, q, law)
+        assert np.array_equal(t, t_ref) and np.array_equal(cnt, cnt_ref)
+
+
 def test_round_cap_and_no_end():
     """max_rounds stops the run with the state after exactly that many rounds."""
     for dims, n in [(1, 500), (2, 30), (3, 9)]:
@@ -54,3 +63,7 @@ def test_time_model_argument_checks():
             ac.ac_time_model(*args, 1, T32, 10)
     with pytest.raises(ac.ACError):
         ac.ac_time_model(1, 10, 0, 1, -5, 10)
+    with pytest.raises(ac.ACError):
+        ac.ac_time_model(2, 6, 0, 1, T32, 10, q=3)          # n < 2q + 1
+    with pytest.raises(ac.ACError):
+        ac.ac_time_model(1, 100, 0, 1, T32, 10, q=9)
