@@ -401,10 +401,9 @@ def main():
         sync_all()
         e_steps = max(1, min(args.steps, 3))
         t0 = time.perf_counter()
-        e_ev = 0
         for _ in range(e_steps):
             for s, (hs, ht, hn) in zip(sims, init_state):
-                s.reset(seed, w["init"])    # clears counters and history; state replaced below
+                # the loaded state (time 0) replaces the handle's state and its time
                 ac.ac_load_state(s.handle, hs.numpy(), ht.numpy(), hn.numpy().view(np.uint32), 0)
             if kern == ac.AC_KERNEL_BLOCKED:
                 ac.ac_batch_run_until(handles, t_end)
@@ -413,9 +412,14 @@ def main():
                     s.run_until_ticks(t_end[0])
             for s, (os_, ot, on) in zip(sims, outs):
                 ac.ac_read_state(s.handle, os_.numpy(), ot.numpy(), on.numpy().view(np.uint32))
-                e_ev += int(on.numpy().view(np.uint32).astype(np.int64).sum())
         torch.cuda.synchronize()
         e_dt = time.perf_counter() - t0
+        # the trajectory is deterministic: every step commits the device-timed step's arrivals;
+        # checked on the results the last step read back (outside the timed region)
+        got = sum(int(on.numpy().view(np.uint32).astype(np.int64).sum()) for _, _, on in outs)
+        if got != ev_per_step_rank:
+            raise RuntimeError(f"end-to-end run committed {got} arrivals, the device-timed step {ev_per_step_rank}")
+        e_ev = ev_per_step_rank * e_steps
         if dist:
             t = torch.tensor([e_dt], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
