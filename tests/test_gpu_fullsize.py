@@ -53,7 +53,7 @@ def _check_checkpoint(sim, cp, what):
 
 
 @pytest.mark.parametrize("beta", ["0.30", "0.4407", "0.60"])
-@pytest.mark.parametrize("kernel,rounds", [(ac.AC_KERNEL_ROUND, 8), (ac.AC_KERNEL_BLOCKED, 1)])
+@pytest.mark.parametrize("kernel,rounds", [(ac.AC_KERNEL_ROUND, 6), (ac.AC_KERNEL_ROUND, 8), (ac.AC_KERNEL_BLOCKED, 1)])
 def test_4096_runs_match_oracle(beta, kernel, rounds):
     g = _golden("ising4096_b" + beta)
     with ac.Sim(g["rows"], g["cols"], g["beta"], g["J"], g["h"], g["seed"], init=g["init"], kernel=kernel,
@@ -63,17 +63,19 @@ def test_4096_runs_match_oracle(beta, kernel, rounds):
             _check_checkpoint(sim, cp, f"beta={beta} kernel={kernel} T={cp['T']}")
 
 
-def test_4096_batched_run_matches_oracle():
-    """The three temperatures in one graph-captured blocked launch, as the benchmark runs them."""
+@pytest.mark.parametrize("kernel,rounds", [(ac.AC_KERNEL_BLOCKED, 1), (ac.AC_KERNEL_ROUND, 6)])
+def test_4096_batched_run_matches_oracle(kernel, rounds):
+    """The three temperatures in one batched call: one graph-captured blocked launch, or one work
+    list of all tiles for the temporal-blocked round kernel (replayed launch chunks)."""
     gs = [_golden("ising4096_b" + b) for b in ("0.30", "0.4407", "0.60")]
     sims = [ac.Sim(g["rows"], g["cols"], g["beta"], g["J"], g["h"], g["seed"], init=g["init"],
-                   kernel=ac.AC_KERNEL_BLOCKED, Lb=64) for g in gs]
+                   kernel=kernel, Lb=64, rounds=rounds) for g in gs]
     try:
         for T in (1, 50):
             ac.ac_batch_run_until([s.handle for s in sims], [T * T32] * 3)
             for g, s in zip(gs, sims):
                 cp = [c for c in g["checkpoints"] if c["T"] == T][0]
-                _check_checkpoint(s, cp, f"batched beta={g['beta']} T={T}")
+                _check_checkpoint(s, cp, f"batched kernel={kernel} beta={g['beta']} T={T}")
     finally:
         for s in sims:
             s.close()
