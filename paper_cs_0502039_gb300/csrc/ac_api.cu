@@ -690,6 +690,129 @@ void frames_off(ac_sim* s) {
   s->f_K = 0;
 }
 
+// Hand frame f_K to fn (a device pointer, or a copy in the pinned host buffer) and
+// retire it.  The frame is complete: every cell's tick is above K dt.
+ac_status deliver_frame(ac_sim* s, ac_frame_fn fn, void* user, int on_host) {
+  const size_t N = s->ncells();
+  const int8_t* slot = s->frames + (size_t)(s->f_K % s->f_B) * N;
+  if (fn) {
+    if (on_host) {
+      AC_CUDA(cudaMemcpyAsync(s->frame_host, slot, N, cudaMemcpyDeviceToHost, s->stream));
+      AC_CUDA(cudaStreamSynchronize(s->stream));
+      fn(user, s->f_K, s->frame_host, N);
+    } else {
+      AC_CUDA(cudaStreamSynchronize(s->stream));
+      fn(user, s->f_K, slot, N);
+    }
+  }
+  ++s->f_K;
+  return AC_OK;
+}
+
+// Frames on the temporal-blocked kernel, with the window slid one frame at a time:
+// between launch chunks the host reads the smallest tick of the last launch's output
+// state, hands out every open frame below it, reopens those slots (filled from the
+// current state buffer) and raises the commit cap to (f_K + B) dt + 1 for the next
+// launches.  The lag bound is the same as with whole windows; no launch waits for
+// the whole lattice to reach a window's end.
+ac_status run_tb_frames(ac_sim* s, long long t_end, ac_frame_fn fn, void* user, int on_host, int D) {
+  const size_t N = s->ncells();
+  if (!s->key2) {
+    if (cudaMalloc(&s->key2, N * 8) != cudaSuccess || cudaMalloc(&s->cnt2, N * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AC_ERR_OOM, "second state buffer (%zu cells) allocation failed", N);
+    }
+  }
+  unsigned long long ev_before = 0, ev_after = 0;
+  ac_status st = read_event_counter(s, &ev_before);
+  if (st != AC_OK) return st;
+  const int region = ac::tb_region_for(D);
+  int tr = 0, tc = 0;
+  tb_tiling(s->rows, s->cols, region, D, ac::tb_grid(region), &tr, &tc);
+  const int total = tr * tc;
+  long long cap = std::min<long long>(t_end, (s->f_K + s->f_B) * s->f_dt + 1);
+  auto upload = [&](long long c) -> ac_status {
+    ac::LatDesc d = s->host_desc(c, 0);
+    d.tr = tr;
+    d.tc = tc;
+    AC_CUDA(cudaMemcpyAsync(s->d_desc, &d, sizeof d, cudaMemcpyHostToDevice, s->stream));
+    return AC_OK;
+  };
+  st = upload(cap);
+  if (st != AC_OK) return st;
+  ac::DevCounters c0{};
+  c0.kmin[0] = c0.kmin[1] = c0.kmin[2] = ~0ull;
+  AC_CUDA(cudaMemcpyAsync(s->d_ctr, &c0, sizeof c0, cudaMemcpyHostToDevice, s->stream));
+  AC_CUDA(cudaEventRecord(s->ev0, s->stream));
+  // about 8.3 synchronous rounds per unit time (Sec. 4), D per launch: check often
+  // enough that the cap is raised before cells wait long on it
+  const double lag = (double)s->f_B * (double)s->f_dt / kTicksPerUnit;
+  const int chunk = std::max(1, std::min(4, (int)(lag * 8.3 / D / 2.0)));
+  const double span = (double)(t_end - s->t_done) / kTicksPerUnit;
+  const double max_launches = 64.0 * (9.0 * std::ceil(span) + 16.0) / D + 4096.0;
+  int issued = 0;
+  ac::DevCounters c{};
+  for (;;) {
+    for (int i = 0; i < chunk; ++i) {
+      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, D, s->d_ctr, s->stream, true, s->model == 1));
+      ++issued;
+    }
+    AC_CUDA(cudaMemcpyAsync(&c, s->d_ctr, sizeof c, cudaMemcpyDeviceToHost, s->stream));
+    AC_CUDA(cudaStreamSynchronize(s->stream));
+    if (c.error) break;
+    const bool idle = c.seq > 0 && c.active[(c.seq + 2) % 3] == 0;
+    const long long W = s->f_K + s->f_B;
+    const long long first = s->f_K;
+    if (c.seq > 0) {
+      const long long tmin = (long long)(c.kmin[(c.seq - 1) % 3] >> 1);
+      while (s->f_K < W && s->f_K * s->f_dt < tmin && s->f_K * s->f_dt < t_end) {
+        st = deliver_frame(s, fn, user, on_host);
+        if (st != AC_OK) return st;
+      }
+    }
+    if (s->f_K > first) {
+      // reopened slots, filled from the state the last completed launch wrote
+      ac::LatDesc dd = s->host_desc(cap, 0);
+      if (c.seq & 1u) {
+        dd.key = s->key2;
+        dd.cnt = s->cnt2;
+      }
+      AC_CUDA(ac::launch_frames_fill(&dd, W, (int)(s->f_K - first), s->stream));
+      const long long ncap = std::min<long long>(t_end, (s->f_K + s->f_B) * s->f_dt + 1);
+      st = upload(ncap);
+      if (st != AC_OK) return st;
+      if (idle && ncap > cap) {   // the last launch found nothing below the old cap
+        const unsigned one = 1u;
+        AC_CUDA(cudaMemcpyAsync(&s->d_ctr->active[(c.seq + 2) % 3], &one, sizeof one, cudaMemcpyHostToDevice,
+                                s->stream));
+      }
+      cap = ncap;
+    } else if (idle || c.seq < (unsigned)issued) {
+      if (cap >= t_end) break;       // everything below t_end is committed
+    }
+    if ((double)issued > max_launches)
+      return fail(AC_ERR_STALL, "round kernel with frames: no completion after %d launches", issued);
+  }
+  AC_CUDA(cudaEventRecord(s->ev1, s->stream));
+  AC_CUDA(cudaMemcpyAsync(&c, s->d_ctr, sizeof c, cudaMemcpyDeviceToHost, s->stream));
+  AC_CUDA(cudaStreamSynchronize(s->stream));
+  float ms = 0.f;
+  AC_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+  const unsigned good = (c.error == AC_ERR_STATE) ? c.seq - 1u : c.seq;
+  if (good & 1u) {
+    std::swap(s->key, s->key2);
+    std::swap(s->cnt, s->cnt2);
+  }
+  s->last_grid = std::min(total, ac::tb_grid(region));
+  st = accumulate(s, c, ms, true);
+  if (st != AC_OK) return st;
+  st = read_event_counter(s, &ev_after);
+  if (st != AC_OK) return st;
+  s->events += ev_after - ev_before;
+  s->t_done = t_end;
+  return AC_OK;
+}
+
 // Snapshot frames (Fig. 3.7).  Frames [f_K, f_K + B) are open.  Commits are capped at
 // tick <= (f_K + B) dt -- the figure's lag bound: no cell gets more than B frames ahead
 // of the oldest frame not yet handed out -- so every frame a commit must write is
@@ -705,6 +828,21 @@ ac_status run_frames(ac_sim* s, long long t_end, ac_frame_fn fn, void* user, int
       return fail(AC_ERR_OOM, "pinned frame buffer (%zu bytes) allocation failed", N);
     }
   }
+  // the temporal-blocked kernel slides the window frame by frame (run_tb_frames); the
+  // other kernels run whole windows: to the cap, then every open frame is complete
+  if (t_end > s->t_done && s->cfg.kernel == ac::kKernelRound && (s->model == 1 || tb_applicable(s))) {
+    const int D = (s->model == 1) ? std::max(1, std::min(s->cfg.rounds, std::min(s->rows, s->cols) / 4))
+                                  : s->cfg.rounds;
+    bool fits = false;
+    ac_status st = tb_counts_fit(s, t_end, &fits);
+    if (st != AC_OK) return st;
+    if (fits) {
+      st = run_tb_frames(s, t_end, fn, user, on_host, D);
+      if (st != AC_OK) return st;
+    } else if (s->model == 1) {
+      return fail(AC_ERR_STATE, "Life: event counts too uneven for the temporal-blocked kernel");
+    }
+  }
   for (;;) {
     const long long W = s->f_K + s->f_B;
     const long long cap = std::min<long long>(t_end, W * s->f_dt + 1);
@@ -714,18 +852,8 @@ ac_status run_frames(ac_sim* s, long long t_end, ac_frame_fn fn, void* user, int
     }
     const long long first = s->f_K;
     while (s->f_K < W && s->f_K * s->f_dt + 1 <= s->t_done) {
-      const int8_t* slot = s->frames + (size_t)(s->f_K % s->f_B) * N;
-      if (fn) {
-        if (on_host) {
-          AC_CUDA(cudaMemcpyAsync(s->frame_host, slot, N, cudaMemcpyDeviceToHost, s->stream));
-          AC_CUDA(cudaStreamSynchronize(s->stream));
-          fn(user, s->f_K, s->frame_host, N);
-        } else {
-          AC_CUDA(cudaStreamSynchronize(s->stream));
-          fn(user, s->f_K, slot, N);
-        }
-      }
-      ++s->f_K;
+      ac_status st = deliver_frame(s, fn, user, on_host);
+      if (st != AC_OK) return st;
     }
     if (s->f_K > first) {
       const ac::LatDesc d = s->host_desc(s->t_done, 0);

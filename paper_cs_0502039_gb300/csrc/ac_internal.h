@@ -62,6 +62,8 @@ struct DevCounters {
   unsigned int launched;        // round kernel: launches that did work
   unsigned int seq;             // temporal-blocked kernel: launches completed in this call
   unsigned int blocks_done;     // temporal-blocked kernel: CTAs finished in the current launch
+  unsigned long long kmin[3];   // temporal-blocked kernel with frames: smallest output key of a
+                                // launch (mod-3 ring like active; the host presets all to ~0)
 };
 
 enum KernelKind { kKernelRound = 0, kKernelBlocked = 1 };

@@ -803,6 +803,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctr->active[(launch_idx + 1) % 3] = 0u;
+    if (FR) ctr->kmin[(launch_idx + 1) % 3] = ~0ull;
     atomicAdd(&ctr->launched, 1u);
   }
   const int tid = threadIdx.x;
@@ -1037,7 +1038,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
 
     // ---- write the tile back; count its arrivals; is anything left before t_end?
     bool live = false;
-    unsigned long long ev = 0;
+    unsigned long long ev = 0, kmin = ~0ull;
     if (own_col) {
       // own rows i = li0 + 4m - D for region rows li0 + 4m in [D, D + h): the same cells
       // whose offsets own_before summed at load
@@ -1053,8 +1054,13 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         key_out[gi] = kk;
         cnt_out[gi] = base + c16;
         live |= kk < t2;
+        if (FR) kmin = min(kmin, kk);
       }
       ev = (unsigned long long)(own_after - own_before);
+    }
+    if (FR) {   // the launch's smallest output key: frames below its tick are complete
+      for (int o = 16; o > 0; o >>= 1) kmin = min(kmin, __shfl_down_sync(kFull, kmin, o));
+      if (lane == 0 && kmin != ~0ull) atomicMin(&ctr->kmin[launch_idx % 3], kmin);
     }
     for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
     if (lane == 0 && ev) {
