@@ -98,6 +98,12 @@ def _bind(lib):
     lib.aco_exp_ticks_many.restype = None
     lib.aco_philox_blocks.argtypes = [ctypes.c_uint64, P, P, ctypes.c_uint32, P, ctypes.c_int64]
     lib.aco_philox_blocks.restype = None
+    lib.aco_rated_gap.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
+    lib.aco_rated_gap.restype = ctypes.c_uint64
+    lib.aco_init_rated.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, P, P, P, P]
+    lib.aco_init_rated.restype = None
+    lib.aco_run_rated.argtypes = [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_uint64, P, P, P, P, ctypes.c_int64]
+    lib.aco_run_rated.restype = ctypes.c_int64
     lib.aco_life_init.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
                                   ctypes.c_uint64, P, P, P]
     lib.aco_life_init.restype = None
@@ -224,6 +230,34 @@ def time_rounds(state: State, seed: int, t_end: int, max_rounds: int = 1 << 20):
     if r < 0:
         raise MemoryError("oracle allocation failed")
     return buf[:min(r, max_rounds)].copy()
+
+
+RATE_ONE = 1 << 20      # multiplier m of rate p = 2^20 / m
+
+
+def rated_gap(e: int, m: int) -> int:
+    """Gap of a cell with rate 2^20 / m for the rate-1 gap e (reading R13)."""
+    return int(_load().aco_rated_gap(int(e), int(m) & 0xFFFFFFFF))
+
+
+def init_rated(rows: int, cols: int, init_mode: int, seed: int, m) -> State:
+    """Initial state with per-cell rates 2^20 / m[c] (first arrivals scaled, reading R13)."""
+    st = init(rows, cols, init_mode, seed)
+    m = np.ascontiguousarray(m, dtype=np.uint32)
+    _load().aco_init_rated(rows, cols, int(init_mode), int(seed) & (2**64 - 1), _ptr(m), _ptr(st.s), _ptr(st.t),
+                           _ptr(st.n))
+    return st
+
+
+def run_rated(state: State, thr: np.ndarray, seed: int, m, t_end: int) -> int:
+    """As run(), with every gap scaled for the cell's rate 2^20 / m[c]."""
+    thr = np.ascontiguousarray(thr, dtype=np.uint32)
+    m = np.ascontiguousarray(m, dtype=np.uint32)
+    ev = _load().aco_run_rated(state.rows, state.cols, _ptr(thr), int(seed) & (2**64 - 1), _ptr(m), _ptr(state.s),
+                               _ptr(state.t), _ptr(state.n), int(t_end))
+    if ev < 0:
+        raise MemoryError("oracle heap allocation failed")
+    return int(ev)
 
 
 CONWAY_BIRTH, CONWAY_SURVIVE = 1 << 3, (1 << 2) | (1 << 3)

@@ -47,6 +47,8 @@
  *              neighbours, as in the appendix's prob[10].
  *   R7 nbrs    4 nearest neighbours on the periodic torus, counted with
  *              multiplicity (on a 2-wide torus both sides are one cell).
+ *   R13 rates  per-cell rates of law (A): gap scaled by m_c / 2^20 (see
+ *              aco_rated_gap below).
  *   R12 life   Life-like rules: Moore neighbourhood, birth / survival masks
  *              over the live-neighbour count (see aco_life_run below).
  *   R11 laws   time-only model of Sec. 4: exponential (R5), uniform on
@@ -236,6 +238,56 @@ int64_t aco_run(int32_t rows, int32_t cols, const uint32_t thr[10], uint64_t see
         philox_block(seed, c, n[c] + 1u, 0u, b);
         if (b[1] < thr[up + 5 * (s[c] > 0)]) s[c] = (int8_t)(-s[c]);  /* Eq. (1) */
         t[c] += (int64_t)aco_exp_ticks(b[0]);                          /* Eq. (5) */
+        n[c] += 1u;
+        sift_down(heap, N, 0, t);
+        ++events;
+    }
+    free(heap);
+    return events;
+}
+
+/* ------------------------------------------------------------------ */
+/* Per-cell rates: the general asynchrony law (A) of Sec. 2, next       */
+/* arrival t - ln(r) / p_c.  Reading R13: p_c = 2^20 / m_c for a 32-bit  */
+/* multiplier m_c >= 1, and the gap is                                  */
+/*   max(1, floor(exp_ticks(x) * m_c / 2^20))                           */
+/* (m_c = 2^20 is the rate-1 process of R5 exactly).  The first arrival */
+/* uses the same scaling of B(c,0).x.                                   */
+/* ------------------------------------------------------------------ */
+uint64_t aco_rated_gap(uint64_t e, uint32_t m)
+{
+    unsigned __int128 p = (unsigned __int128)e * (unsigned __int128)m;
+    uint64_t g = (uint64_t)(p >> 20);
+    return g ? g : 1u;
+}
+
+void aco_init_rated(int32_t rows, int32_t cols, int32_t init, uint64_t seed, const uint32_t *m,
+                    int8_t *s, int64_t *t, uint32_t *n)
+{
+    aco_init(rows, cols, init, seed, s, t, n);
+    uint64_t N = (uint64_t)rows * (uint64_t)cols;
+    for (uint64_t c = 0; c < N; ++c) t[c] = (int64_t)aco_rated_gap((uint64_t)t[c], m[c]);
+}
+
+int64_t aco_run_rated(int32_t rows, int32_t cols, const uint32_t thr[10], uint64_t seed, const uint32_t *m,
+                      int8_t *s, int64_t *t, uint32_t *n, int64_t t_end)
+{
+    uint64_t N = (uint64_t)rows * (uint64_t)cols;
+    uint32_t *heap = (uint32_t *)malloc(N * sizeof(uint32_t));
+    if (!heap) return -1;
+    for (uint64_t c = 0; c < N; ++c) heap[c] = (uint32_t)c;
+    for (uint64_t i = N / 2; i-- > 0;) sift_down(heap, N, i, t);
+    int64_t events = 0;
+    while (t[heap[0]] < t_end) {
+        uint32_t c = heap[0];
+        uint64_t nb[4];
+        neighbours(rows, cols, c, nb);
+        int up = 0;
+        for (int d = 0; d < 4; ++d) up += (s[nb[d]] > 0);
+        uint32_t b[4];
+        philox_block(seed, c, n[c] + 1u, 0u, b);
+        if (b[1] < thr[up + 5 * (s[c] > 0)]) s[c] = (int8_t)(-s[c]);
+        t[c] += (int64_t)aco_rated_gap(aco_exp_ticks(b[0]), m[c]);
         n[c] += 1u;
         sift_down(heap, N, 0, t);
         ++events;

@@ -1,4 +1,4 @@
-"""Full-size parity: 4096 x 4096 (three temperatures, T = 50) and 16384 x 16384.
+"""Full-size parity: 4096 x 4096 (three temperatures and the Life automaton, T = 50) and 16384 x 16384.
 
 The expected values in tests/golden/ were written by tests/golden/make_golden.py,
 which calls only the CPU oracle: for each checkpoint the committed-event total,
@@ -61,6 +61,17 @@ def test_4096_runs_match_oracle(beta, kernel, rounds):
         for cp in g["checkpoints"]:
             sim.run_until(cp["T"])
             _check_checkpoint(sim, cp, f"beta={beta} kernel={kernel} T={cp['T']}")
+
+
+@pytest.mark.parametrize("rounds", [6, 8])
+def test_4096_life_matches_oracle(rounds):
+    """The asynchronous Conway automaton on the 4096^2 torus to T = 50 against the oracle's run."""
+    g = _golden("life4096")
+    with ac.life(g["rows"], g["cols"], g["seed"], g["density"] / 2**32, g["birth"], g["survive"], g["init"],
+                 rounds) as sim:
+        for cp in g["checkpoints"]:
+            sim.run_until(cp["T"])
+            _check_checkpoint(sim, cp, f"life rounds={rounds} T={cp['T']}")
 
 
 @pytest.mark.parametrize("kernel,rounds", [(ac.AC_KERNEL_BLOCKED, 1), (ac.AC_KERNEL_ROUND, 6)])
