@@ -196,6 +196,21 @@ ac_status ac_round_history(const ac_sim* sim, uint64_t* counts, int32_t cap, int
 ac_status ac_reset(ac_sim* sim, uint64_t seed, int32_t init);
 
 /*
+ * Per-cell rates: the general asynchrony law (A) of Sec. 2, next arrival
+ * t - ln(r) / p_c.  m[c] (a host array of rows * cols entries, each >= 1) gives
+ * cell c the rate p_c = 2^20 / m[c]: each of its gaps, the first included, is
+ * max(1, floor(e * m[c] / 2^20)) for the rate-1 gap e of ac_run_until (so
+ * m[c] = 2^20 is rate 1 exactly).  NULL restores rate 1 everywhere.  Only at
+ * time 0 (before the first run, or after ac_reset); the handle is re-initialised
+ * with its seed and initial condition so that the first arrivals use the rates.
+ * ac_reset keeps the rates.  Works with every kernel and in batches; the Ising
+ * array only.  Errors: AC_ERR_ARG (a zero multiplier, a Life handle),
+ * AC_ERR_STATE (after a run), AC_ERR_OOM, AC_ERR_CUDA.
+ */
+#define AC_RATE_ONE (1u << 20)
+ac_status ac_set_rates(ac_sim* sim, const uint32_t* m);
+
+/*
  * Snapshot frames at regular times K * dt (Sec. 3, "Generating the output",
  * Fig. 3.7).  Frame K is the array of all spins (int8 +-1, row-major) after every
  * arrival with tick <= K * dt_ticks has been committed and none later -- the

@@ -218,8 +218,11 @@ static void sift_down(uint32_t *heap, uint64_t size, uint64_t i, const int64_t *
  * arrival is >= t_end (reading R2).  Returns the number of committed
  * arrivals, or -1 if the heap could not be allocated.
  */
-int64_t aco_run(int32_t rows, int32_t cols, const uint32_t thr[10], uint64_t seed,
-                int8_t *s, int64_t *t, uint32_t *n, int64_t t_end)
+uint64_t aco_rated_gap(uint64_t e, uint32_t m);
+
+/* The heap run; m = NULL for rate 1 everywhere, else per-cell rates (R13). */
+static int64_t run_heap(int32_t rows, int32_t cols, const uint32_t thr[10], uint64_t seed, const uint32_t *m,
+                        int8_t *s, int64_t *t, uint32_t *n, int64_t t_end)
 {
     uint64_t N = (uint64_t)rows * (uint64_t)cols;
     uint32_t *heap = (uint32_t *)malloc(N * sizeof(uint32_t));
@@ -237,13 +240,20 @@ int64_t aco_run(int32_t rows, int32_t cols, const uint32_t thr[10], uint64_t see
         uint32_t b[4];
         philox_block(seed, c, n[c] + 1u, 0u, b);
         if (b[1] < thr[up + 5 * (s[c] > 0)]) s[c] = (int8_t)(-s[c]);  /* Eq. (1) */
-        t[c] += (int64_t)aco_exp_ticks(b[0]);                          /* Eq. (5) */
+        uint64_t gap = aco_exp_ticks(b[0]);                            /* Eq. (5) */
+        t[c] += (int64_t)(m ? aco_rated_gap(gap, m[c]) : gap);
         n[c] += 1u;
         sift_down(heap, N, 0, t);
         ++events;
     }
     free(heap);
     return events;
+}
+
+int64_t aco_run(int32_t rows, int32_t cols, const uint32_t thr[10], uint64_t seed,
+                int8_t *s, int64_t *t, uint32_t *n, int64_t t_end)
+{
+    return run_heap(rows, cols, thr, seed, NULL, s, t, n, t_end);
 }
 
 /* ------------------------------------------------------------------ */
@@ -272,28 +282,7 @@ void aco_init_rated(int32_t rows, int32_t cols, int32_t init, uint64_t seed, con
 int64_t aco_run_rated(int32_t rows, int32_t cols, const uint32_t thr[10], uint64_t seed, const uint32_t *m,
                       int8_t *s, int64_t *t, uint32_t *n, int64_t t_end)
 {
-    uint64_t N = (uint64_t)rows * (uint64_t)cols;
-    uint32_t *heap = (uint32_t *)malloc(N * sizeof(uint32_t));
-    if (!heap) return -1;
-    for (uint64_t c = 0; c < N; ++c) heap[c] = (uint32_t)c;
-    for (uint64_t i = N / 2; i-- > 0;) sift_down(heap, N, i, t);
-    int64_t events = 0;
-    while (t[heap[0]] < t_end) {
-        uint32_t c = heap[0];
-        uint64_t nb[4];
-        neighbours(rows, cols, c, nb);
-        int up = 0;
-        for (int d = 0; d < 4; ++d) up += (s[nb[d]] > 0);
-        uint32_t b[4];
-        philox_block(seed, c, n[c] + 1u, 0u, b);
-        if (b[1] < thr[up + 5 * (s[c] > 0)]) s[c] = (int8_t)(-s[c]);
-        t[c] += (int64_t)aco_rated_gap(aco_exp_ticks(b[0]), m[c]);
-        n[c] += 1u;
-        sift_down(heap, N, 0, t);
-        ++events;
-    }
-    free(heap);
-    return events;
+    return run_heap(rows, cols, thr, seed, m, s, t, n, t_end);
 }
 
 /* ------------------------------------------------------------------ */

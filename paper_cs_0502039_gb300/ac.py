@@ -54,7 +54,9 @@ EXPORTS = ["ac_create", "ac_set_stream", "ac_configure", "ac_run_until", "ac_run
            "ac_read_state", "ac_read_state_device", "ac_load_state", "ac_stats", "ac_round_history",
            "ac_destroy", "ac_last_error", "ac_thresholds", "ac_reset", "ac_set_option", "ac_batch_create", "ac_batch_run_until",
            "ac_dev_exp_ticks", "ac_dev_philox", "ac_run_blocked_static", "ac_frames_configure",
-           "ac_run_until_frames", "ac_frames_status", "ac_time_model", "ac_create_life"]
+           "ac_run_until_frames", "ac_frames_status", "ac_time_model", "ac_create_life", "ac_set_rates"]
+
+AC_RATE_ONE = 1 << 20
 
 AC_LIFE_CONWAY_BIRTH, AC_LIFE_CONWAY_SURVIVE = 1 << 3, (1 << 2) | (1 << 3)
 
@@ -95,6 +97,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ac_frames_configure": ([P, I64, I64, I32], I32),
         "ac_run_until_frames": ([P, I64, FRAME_FN, P, I32], I32),
         "ac_frames_status": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)], I32),
+        "ac_set_rates": ([P, P], I32),
         "ac_create_life": ([ac_lattice, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, U64,
                             ctypes.POINTER(P)], I32),
         "ac_time_model": ([I32, I64, I32, I32, U64, I64, I32, P, ctypes.POINTER(I32), P, P,
@@ -133,6 +136,14 @@ def ac_create_life(rows: int, cols: int, init: int, density: int, birth: int, su
     _check(_lib.ac_create_life(ac_lattice(rows, cols, init), int(density) & 0xFFFFFFFF, int(birth), int(survive),
                                seed & (2**64 - 1), ctypes.byref(out)))
     return out.value
+
+
+def ac_set_rates(sim: int, m) -> None:
+    """Per-cell rates 2^20 / m[c] (None: rate 1 everywhere); only at time 0."""
+    if m is None:
+        _check(_lib.ac_set_rates(sim, None))
+    else:
+        _check(_lib.ac_set_rates(sim, _np_ptr(np.ascontiguousarray(m, dtype=np.uint32), np.uint32)))
 
 
 def ac_set_stream(sim: int, stream: int) -> None:
@@ -338,6 +349,10 @@ class Sim:
     def reset(self, seed: int, init: int = AC_INIT_RANDOM) -> None:
         ac_reset(self.handle, seed, init)
         self.seed = int(seed)
+
+    def set_rates(self, m) -> None:
+        """Per-cell rates 2^20 / m[c] (None: all 1); re-initialises the handle at time 0."""
+        ac_set_rates(self.handle, m)
 
     def set_option(self, option: int, value: int) -> None:
         ac_set_option(self.handle, option, value)

@@ -102,6 +102,7 @@ struct ac_sim {
   // model: 0 = Ising heat bath, 1 = Life-like automaton (birth / survival masks, density)
   int model = 0;
   uint32_t life_birth = 0, life_survive = 0, life_density = 0;
+  unsigned* d_rates = nullptr;              // per-cell rate multipliers (nullptr: all rate 1)
   int8_t* frames = nullptr;
   int8_t* frame_host = nullptr;             // pinned copy handed to host callbacks
   int f_B = 0;
@@ -140,6 +141,7 @@ struct ac_sim {
     d.drop_publish = drop_publish;
     d.model = model;
     d.life_density = life_density;
+    d.rates = d_rates;
     if (model == 1) {
       d.thr[0] = life_birth;
       d.thr[1] = life_survive;
@@ -252,6 +254,7 @@ void free_sim(ac_sim* s) {
   cudaFree(s->d_hist);
   cudaFree(s->d_red);
   cudaFree(s->frames);
+  cudaFree(s->d_rates);
   if (s->frame_host) cudaFreeHost(s->frame_host);
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
@@ -953,6 +956,28 @@ ac_status ac_run_until_ticks(ac_sim* sim, int64_t t_end) {
   if (t_end >= kTickLimit) return fail(AC_ERR_ARG, "t_end must be < 2^61");
   if (sim->f_B > 0) return run_frames(sim, t_end, nullptr, nullptr, 0);
   return run_core(sim, t_end);
+}
+
+ac_status ac_set_rates(ac_sim* sim, const uint32_t* m) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  if (sim->t_done != 0) return fail(AC_ERR_STATE, "rates are set at time 0 (before the first run or after ac_reset)");
+  if (sim->model != 0) return fail(AC_ERR_ARG, "per-cell rates apply to the Ising array");
+  const size_t N = sim->ncells();
+  if (!m) {
+    cudaFree(sim->d_rates);
+    sim->d_rates = nullptr;
+  } else {
+    for (size_t c = 0; c < N; ++c)
+      if (m[c] == 0u) return fail(AC_ERR_ARG, "rate multiplier of cell %zu is 0 (needs m >= 1)", c);
+    if (!sim->d_rates && cudaMalloc(&sim->d_rates, N * 4) != cudaSuccess) {
+      cudaGetLastError();
+      sim->d_rates = nullptr;
+      return fail(AC_ERR_OOM, "rate array (%zu cells) allocation failed", N);
+    }
+    AC_CUDA(cudaMemcpyAsync(sim->d_rates, m, N * 4, cudaMemcpyHostToDevice, sim->stream));
+  }
+  drop_runners_of(sim);
+  return ac_reset(sim, sim->seed, sim->init);   // first arrivals drawn at the new rates
 }
 
 ac_status ac_frames_configure(ac_sim* sim, int64_t dt_ticks, int64_t K0, int32_t B) {

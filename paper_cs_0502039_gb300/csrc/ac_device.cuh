@@ -93,4 +93,13 @@ __device__ __forceinline__ unsigned long long exp_ticks(uint32_t x, uint32_t two
   return __umul64hi(nl, kLn2Q64) + 1ull;
 }
 
+// Gap of a cell with rate 2^20 / m for the rate-1 gap e: max(1, floor(e m / 2^20)),
+// from the full 128-bit product (the general asynchrony law (A) of Sec. 2).
+__device__ __forceinline__ unsigned long long rated_gap(unsigned long long e, uint32_t m) {
+  const unsigned long long lo = e * (unsigned long long)m;
+  const unsigned long long hi = __umul64hi(e, (unsigned long long)m);
+  const unsigned long long g = (hi << 44) | (lo >> 20);
+  return g ? g : 1ull;
+}
+
 }  // namespace ac

@@ -46,6 +46,9 @@ struct LatDesc {
   // live neighbours; a random initial cell is alive iff its init word < life_density)
   int model;
   unsigned life_density;
+  // per-cell rates (law (A) of Sec. 2): cell c's gaps are max(1, floor(e * rates[c] / 2^20))
+  // for the rate-1 gap e, i.e. rate 2^20 / rates[c]; nullptr = every cell at rate 1
+  const unsigned* rates;
 };
 
 // Device counters of one run call (zeroed by the host before the call).

@@ -328,7 +328,9 @@ __device__ __forceinline__ void commit_tile(const Smem<LB>& sm, const LatDesc& L
     const unsigned n_old = DIRECT ? L.cnt[gidx] : sm.C[r * LB + c];
     const Philox4 b = philox_event(gidx, n_old + 1u, 0u, L.seed_lo, L.seed_hi);
     const unsigned flip = b.y < sm.thr[j + 5u * sp] ? 1u : 0u;
-    const unsigned long long nk = (key & ~1ull) + (exp_ticks(b.x, L.two) << 1) + (sp ^ flip);
+    unsigned long long gap = exp_ticks(b.x, L.two);
+    if (L.rates) gap = rated_gap(gap, L.rates[gidx]);
+    const unsigned long long nk = (key & ~1ull) + (gap << 1) + (sp ^ flip);
     *kp = nk;
     if (L.f_open) write_frames(frame_view(L), gidx, key >> 1, nk >> 1, (unsigned)nk & 1u);
     if (DIRECT) {
@@ -393,7 +395,9 @@ __global__ void init_kernel(LatDesc L, int init_mode) {
       const uint32_t x = philox_event((uint32_t)c, 0u, 1u, L.seed_lo, L.seed_hi).x;
       up = L.model ? (x < L.life_density ? 1u : 0u) : (x & 1u);   // Life: alive with the given density
     }
-    L.key[c] = (exp_ticks(b0.x, L.two) << 1) | up;
+    unsigned long long t0 = exp_ticks(b0.x, L.two);
+    if (L.rates) t0 = rated_gap(t0, L.rates[c]);
+    L.key[c] = (t0 << 1) | up;
     L.cnt[c] = 0u;
   }
 }
@@ -901,6 +905,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     // ---- R synchronous rounds over the shrinking region
     const unsigned long long t2 = L.t2;
     const uint32_t two = L.two, seed_lo = L.seed_lo, seed_hi = L.seed_hi;
+    const unsigned* __restrict__ rates = L.rates;
     constexpr unsigned kEven = 0x55555555u, kOdd = 0xAAAAAAAAu;
     int cur = 0;
     for (int k = 1; k <= R; ++k) {
@@ -990,7 +995,11 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         }
         const Philox4 pa = philox_event(gia, base + c16a + 1u, 0u, seed_lo, seed_hi);
         const Philox4 pb = philox_event(gib, base + c16b + 1u, 0u, seed_lo, seed_hi);
-        const unsigned long long gapa = exp_ticks(pa.x, two), gapb = exp_ticks(pb.x, two);
+        unsigned long long gapa = exp_ticks(pa.x, two), gapb = exp_ticks(pb.x, two);
+        if (rates) {
+          gapa = rated_gap(gapa, rates[gia]);
+          gapb = rated_gap(gapb, rates[gib]);
+        }
         const unsigned nsa = LIFE ? (tha >> moore_live<RW>(kpa)) & 1u : spa ^ (pa.y < tha ? 1u : 0u);
         const unsigned nsb = LIFE ? (thb >> moore_live<RW>(kpb)) & 1u : spb ^ (pb.y < thb ? 1u : 0u);
         const unsigned long long nka = (keya & ~1ull) + (gapa << 1) + nsa;
@@ -1023,7 +1032,9 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
                              ((unsigned)kp[1] & 1u);
           ns = sp ^ (b.y < thr[j + 5u * sp] ? 1u : 0u);
         }
-        const unsigned long long nk = (key & ~1ull) + (exp_ticks(b.x, two) << 1) + ns;
+        unsigned long long gap = exp_ticks(b.x, two);
+        if (rates) gap = rated_gap(gap, rates[gidx]);
+        const unsigned long long nk = (key & ~1ull) + (gap << 1) + ns;
         *kp = nk;
         C[r * RW + cc] = (unsigned short)(c16 + 1u);
         if (FR && r >= D && r < D + g.h && cc >= D && cc < D + g.w)
