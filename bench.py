@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the per-kernel side measurements")
     ap.add_argument("--workload", default="ising4096",
-                    choices=["ising4096", "batch", "serve", "frames", "configs", "efficiency", "life"],
+                    choices=["ising4096", "batch", "serve", "frames", "configs", "efficiency", "life", "rates"],
                     help="ising4096: the headline step; batch: the 512-lattice batch only; serve: the request stream")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the replayed request stream")
     ap.add_argument("--single", action="store_true",
@@ -245,6 +245,14 @@ def main():
     if args.workload == "configs":
         res = configs_measurement()
         print(json.dumps({"workload": args.workload, **res}), flush=True)
+        return 0
+    if args.workload == "rates":
+        import torch
+        torch.cuda.set_device(0)
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_cs_0502039_gb300 as ac
+        print(json.dumps({"workload": args.workload, **rates_measurement(ac)}), flush=True)
         return 0
     if args.workload == "life":
         import torch
@@ -586,6 +594,30 @@ def frames_measurement(ac, rounds=6, lb=64):
             assert ev == ev0
             out["cases"].append({"lag": lag, "dt": dt_units, "B": B, "frames": int(w["T"] / dt_units), "mode": mode,
                                  "seconds": t, "events_per_s": ev / t, "relative": t0 / t})
+    return out
+
+
+def rates_measurement(ac, rounds=6):
+    """Per-cell rates (law (A) of Sec. 2) on the 4096^2 beta = 0.4407 lattice to T = 50: rate
+    multipliers drawn log-uniformly so that rates span 1/8 .. 8 (seed 5), against rate 1."""
+    import numpy as np
+    import torch
+    w = WORKLOAD
+    N = w["rows"] * w["cols"]
+    rng = np.random.default_rng(5)
+    m = np.exp(rng.uniform(np.log(ac.AC_RATE_ONE / 8), np.log(ac.AC_RATE_ONE * 8), N)).astype(np.uint32)
+    out = {"lattice": f"{w['rows']}x{w['cols']}", "beta": 0.4407, "T": w["T"], "rounds": rounds, "cases": []}
+    for name, rates in (("rate 1", None), ("rates 1/8 .. 8", m)):
+        with ac.Sim(w["rows"], w["cols"], 0.4407, w["J"], w["h"], w["seed"], init=w["init"],
+                    kernel=ac.AC_KERNEL_ROUND, Lb=64, rounds=rounds) as sim:
+            sim.set_rates(rates)
+            sim.run_until(w["T"])
+            sim.reset(w["seed"], w["init"])
+            torch.cuda.synchronize()
+            sim.run_until(w["T"])
+            st = sim.stats()
+        out["cases"].append({"case": name, "events": st["events"], "device_ms": st["device_ms"],
+                             "events_per_s": st["events"] / (st["device_ms"] / 1000.0)})
     return out
 
 
