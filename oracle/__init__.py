@@ -98,6 +98,11 @@ def _bind(lib):
     lib.aco_exp_ticks_many.restype = None
     lib.aco_philox_blocks.argtypes = [ctypes.c_uint64, P, P, ctypes.c_uint32, P, ctypes.c_int64]
     lib.aco_philox_blocks.restype = None
+    lib.aco_thresholds_q.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, P]
+    lib.aco_thresholds_q.restype = None
+    lib.aco_run_q.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_uint64, P, P, P,
+                              ctypes.c_int64]
+    lib.aco_run_q.restype = ctypes.c_int64
     lib.aco_rated_gap.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
     lib.aco_rated_gap.restype = ctypes.c_uint64
     lib.aco_init_rated.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, P, P, P, P]
@@ -230,6 +235,28 @@ def time_rounds(state: State, seed: int, t_end: int, max_rounds: int = 1 << 20):
     if r < 0:
         raise MemoryError("oracle allocation failed")
     return buf[:min(r, max_rounds)].copy()
+
+
+def thresholds_q(beta: float, J: float, h: float, q: int) -> np.ndarray:
+    """Heat-bath table of the q-th degree neighbourhood (reading R14): index j + (M+1)(s>0),
+    M = 2q(q+1) neighbours, j of them up."""
+    M = 2 * q * (q + 1)
+    out = np.zeros(2 * (M + 1), dtype=np.uint32)
+    _load().aco_thresholds_q(float(beta), float(J), float(h), int(q), _ptr(out))
+    return out
+
+
+def run_q(state: State, q: int, thr: np.ndarray, seed: int, t_end: int) -> int:
+    """As run(), for the Ising array on the q-th degree neighbourhood (every cell within Manhattan
+    distance q); thr from thresholds_q."""
+    if state.rows < 2 * q + 1 or state.cols < 2 * q + 1:
+        raise ValueError("rows and cols must be >= 2q + 1")
+    thr = np.ascontiguousarray(thr, dtype=np.uint32)
+    ev = _load().aco_run_q(state.rows, state.cols, int(q), _ptr(thr), int(seed) & (2**64 - 1), _ptr(state.s),
+                           _ptr(state.t), _ptr(state.n), int(t_end))
+    if ev < 0:
+        raise MemoryError("oracle heap allocation failed")
+    return int(ev)
 
 
 RATE_ONE = 1 << 20      # multiplier m of rate p = 2^20 / m

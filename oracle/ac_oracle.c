@@ -47,6 +47,8 @@
  *              neighbours, as in the appendix's prob[10].
  *   R7 nbrs    4 nearest neighbours on the periodic torus, counted with
  *              multiplicity (on a 2-wide torus both sides are one cell).
+ *   R14 q-nbhd the Ising array on the q-th degree neighbourhood (see
+ *              aco_run_q below).
  *   R13 rates  per-cell rates of law (A): gap scaled by m_c / 2^20 (see
  *              aco_rated_gap below).
  *   R12 life   Life-like rules: Moore neighbourhood, birth / survival masks
@@ -283,6 +285,60 @@ int64_t aco_run_rated(int32_t rows, int32_t cols, const uint32_t thr[10], uint64
                       int8_t *s, int64_t *t, uint32_t *n, int64_t t_end)
 {
     return run_heap(rows, cols, thr, seed, m, s, t, n, t_end);
+}
+
+/* ------------------------------------------------------------------ */
+/* The Ising array on the q-th degree neighbourhood of Sec. 3 (reading  */
+/* R14): every cell within Manhattan distance q is a neighbour, M =     */
+/* 2q(q+1) of them; the heat-bath rule of R6 with S = sum of their      */
+/* spins (S = 2j - M for j up neighbours), table index j + (M+1)(s>0),  */
+/* and a cell waits for all of them.  q = 1 is the model above.  Needs  */
+/* rows, cols >= 2q + 1 (distinct neighbours).                          */
+/* ------------------------------------------------------------------ */
+void aco_thresholds_q(double beta, double J, double h, int32_t q, uint32_t *thr)
+{
+    const int M = 2 * q * (q + 1);
+    for (int sp = 0; sp < 2; ++sp) {
+        double s = sp ? 1.0 : -1.0;
+        for (int j = 0; j <= M; ++j) {
+            double S = (double)(2 * j - M);
+            double p = 1.0 / (1.0 + exp(beta * 2.0 * s * (J * S + h)));
+            double v = ldexp(p, 32);
+            thr[j + (M + 1) * sp] = (v < 4294967295.0) ? (uint32_t)floor(v) : 0xFFFFFFFFu;
+        }
+    }
+}
+
+int64_t aco_run_q(int32_t rows, int32_t cols, int32_t q, const uint32_t *thr, uint64_t seed,
+                  int8_t *s, int64_t *t, uint32_t *n, int64_t t_end)
+{
+    const int M = 2 * q * (q + 1);
+    uint64_t N = (uint64_t)rows * (uint64_t)cols;
+    uint32_t *heap = (uint32_t *)malloc(N * sizeof(uint32_t));
+    if (!heap) return -1;
+    for (uint64_t c = 0; c < N; ++c) heap[c] = (uint32_t)c;
+    for (uint64_t i = N / 2; i-- > 0;) sift_down(heap, N, i, t);
+    int64_t events = 0;
+    while (t[heap[0]] < t_end) {
+        uint32_t c = heap[0];
+        int64_t r = (int64_t)(c / (uint32_t)cols), x = (int64_t)(c % (uint32_t)cols);
+        int up = 0;
+        for (int dr = -q; dr <= q; ++dr)
+            for (int dx = -q; dx <= q; ++dx) {
+                int dist = (dr < 0 ? -dr : dr) + (dx < 0 ? -dx : dx);
+                if (dist == 0 || dist > q) continue;
+                up += s[((r + dr + rows) % rows) * cols + (x + dx + cols) % cols] > 0;
+            }
+        uint32_t b[4];
+        philox_block(seed, c, n[c] + 1u, 0u, b);
+        if (b[1] < thr[up + (M + 1) * (s[c] > 0)]) s[c] = (int8_t)(-s[c]);
+        t[c] += (int64_t)aco_exp_ticks(b[0]);
+        n[c] += 1u;
+        sift_down(heap, N, 0, t);
+        ++events;
+    }
+    free(heap);
+    return events;
 }
 
 /* ------------------------------------------------------------------ */
