@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the per-kernel side measurements")
     ap.add_argument("--workload", default="ising4096",
-                    choices=["ising4096", "batch", "serve", "frames", "configs", "efficiency", "life", "rates"],
+                    choices=["ising4096", "batch", "serve", "frames", "configs", "efficiency", "life", "rates",
+                             "qnbhd"],
                     help="ising4096: the headline step; batch: the 512-lattice batch only; serve: the request stream")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the replayed request stream")
     ap.add_argument("--single", action="store_true",
@@ -245,6 +246,14 @@ def main():
     if args.workload == "configs":
         res = configs_measurement()
         print(json.dumps({"workload": args.workload, **res}), flush=True)
+        return 0
+    if args.workload == "qnbhd":
+        import torch
+        torch.cuda.set_device(0)
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_cs_0502039_gb300 as ac
+        print(json.dumps({"workload": args.workload, **qnbhd_measurement(ac)}), flush=True)
         return 0
     if args.workload == "rates":
         import torch
@@ -594,6 +603,30 @@ def frames_measurement(ac, rounds=6, lb=64):
             assert ev == ev0
             out["cases"].append({"lag": lag, "dt": dt_units, "B": B, "frames": int(w["T"] / dt_units), "mode": mode,
                                  "seconds": t, "events_per_s": ev / t, "relative": t0 / t})
+    return out
+
+
+def qnbhd_measurement(ac):
+    """The Ising array on the q-th degree neighbourhood (Sec. 3) on a 4096^2 torus, random start
+    (seed 7), beta 0.15, run to T = 50 with the temporal-blocked kernel, for q = 1, 2, 3."""
+    import torch
+    w = WORKLOAD
+    out = {"lattice": f"{w['rows']}x{w['cols']}", "beta": 0.15, "T": w["T"], "cases": []}
+    for q, rounds in ((1, 6), (2, 3), (3, 2), (2, 6), (3, 4)):
+        if q == 1:
+            sim = ac.Sim(w["rows"], w["cols"], 0.15, 1.0, 0.0, w["seed"], kernel=ac.AC_KERNEL_ROUND, Lb=64,
+                         rounds=rounds)
+        else:
+            sim = ac.ising_q(w["rows"], w["cols"], 0.15, q, seed=w["seed"], rounds=rounds)
+        with sim:
+            sim.run_until(w["T"])
+            sim.reset(w["seed"], 0)
+            torch.cuda.synchronize()
+            sim.run_until(w["T"])
+            st = sim.stats()
+        out["cases"].append({"q": q, "neighbours": 2 * q * (q + 1), "rounds_per_launch": rounds, "halo": q * rounds,
+                             "events": st["events"], "device_ms": st["device_ms"],
+                             "events_per_s": st["events"] / (st["device_ms"] / 1000.0)})
     return out
 
 

@@ -99,6 +99,21 @@ ac_status ac_create(ac_lattice lat, double beta, double J, double h, uint64_t se
  * launch capped at min(rows, cols) / 4, default 6); not in batches.
  * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
  */
+/*
+ * Create the Ising array on the q-th degree neighbourhood of Sec. 3 (q = 2 or 3):
+ * every cell within Manhattan distance q is a neighbour, M = 2q(q+1) of them.  The
+ * heat-bath rule of ac_create uses S = the sum of their spins, i.e. the table
+ * p = 1/(1 + exp(beta dE)), dE = 2 s (J S + h), thr = min(floor(p 2^32), 2^32 - 1),
+ * index j + (M+1)(s > 0) for j up neighbours; a cell may commit once its
+ * (tick, index) key is below all M neighbours' keys.  Initial state and arrivals
+ * as for ac_create.  Needs rows, cols >= 4q.  Runs on the round kernel only
+ * (temporal blocking, the region losing q rings per round; rounds per launch
+ * capped at 16 / q and min(rows, cols) / (4q), default 6); not in batches; no
+ * per-cell rates.  Observables of ac_stats keep the nearest-neighbour bonds.
+ * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
+ */
+ac_status ac_create_q(ac_lattice lat, double beta, double J, double h, int32_t q, uint64_t seed, ac_sim** out);
+
 #define AC_LIFE_CONWAY_BIRTH (1u << 3)
 #define AC_LIFE_CONWAY_SURVIVE ((1u << 2) | (1u << 3))
 ac_status ac_create_life(ac_lattice lat, uint32_t density, uint32_t birth, uint32_t survive, uint64_t seed,

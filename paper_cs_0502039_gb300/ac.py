@@ -54,7 +54,8 @@ EXPORTS = ["ac_create", "ac_set_stream", "ac_configure", "ac_run_until", "ac_run
            "ac_read_state", "ac_read_state_device", "ac_load_state", "ac_stats", "ac_round_history",
            "ac_destroy", "ac_last_error", "ac_thresholds", "ac_reset", "ac_set_option", "ac_batch_create", "ac_batch_run_until",
            "ac_dev_exp_ticks", "ac_dev_philox", "ac_run_blocked_static", "ac_frames_configure",
-           "ac_run_until_frames", "ac_frames_status", "ac_time_model", "ac_create_life", "ac_set_rates"]
+           "ac_run_until_frames", "ac_frames_status", "ac_time_model", "ac_create_life", "ac_set_rates",
+           "ac_create_q"]
 
 AC_RATE_ONE = 1 << 20
 
@@ -98,6 +99,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ac_run_until_frames": ([P, I64, FRAME_FN, P, I32], I32),
         "ac_frames_status": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)], I32),
         "ac_set_rates": ([P, P], I32),
+        "ac_create_q": ([ac_lattice, D, D, D, I32, U64, ctypes.POINTER(P)], I32),
         "ac_create_life": ([ac_lattice, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, U64,
                             ctypes.POINTER(P)], I32),
         "ac_time_model": ([I32, I64, I32, I32, U64, I64, I32, P, ctypes.POINTER(I32), P, P,
@@ -135,6 +137,12 @@ def ac_create_life(rows: int, cols: int, init: int, density: int, birth: int, su
     out = ctypes.c_void_p()
     _check(_lib.ac_create_life(ac_lattice(rows, cols, init), int(density) & 0xFFFFFFFF, int(birth), int(survive),
                                seed & (2**64 - 1), ctypes.byref(out)))
+    return out.value
+
+
+def ac_create_q(rows: int, cols: int, init: int, beta: float, J: float, h: float, q: int, seed: int) -> int:
+    out = ctypes.c_void_p()
+    _check(_lib.ac_create_q(ac_lattice(rows, cols, init), beta, J, h, int(q), seed & (2**64 - 1), ctypes.byref(out)))
     return out.value
 
 
@@ -300,6 +308,15 @@ def life(rows: int, cols: int, seed: int = 0, density: float = 0.5, birth: int =
     d = min(int(density * 2**32), 2**32 - 1) if density < 1.0 else 2**32 - 1
     h = ac_create_life(rows, cols, init, d, birth, survive, seed)
     sim = Sim(rows, cols, 0.0, 0.0, 0.0, seed, init=init, handle=h)
+    sim.configure(AC_KERNEL_ROUND, 64, rounds, 0)
+    return sim
+
+
+def ising_q(rows: int, cols: int, beta: float, q: int, J: float = 1.0, h: float = 0.0, seed: int = 0,
+            init: int = 0, rounds: int = 6) -> "Sim":
+    """A Sim handle holding the Ising array on the q-th degree neighbourhood (q = 2, 3)."""
+    hnd = ac_create_q(rows, cols, init, beta, J, h, q, seed)
+    sim = Sim(rows, cols, beta, J, h, seed, init=init, handle=hnd)
     sim.configure(AC_KERNEL_ROUND, 64, rounds, 0)
     return sim
 

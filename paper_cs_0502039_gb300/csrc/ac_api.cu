@@ -76,7 +76,8 @@ struct ac_sim {
   uint64_t seed = 0;
   cudaStream_t stream = nullptr;
   ac::LaunchCfg cfg{};
-  uint32_t thr[10] = {};
+  uint32_t thr[ac::kThrMax] = {};
+  int q = 1;                                // neighbourhood radius (model 2)
   int tr = 0, tc = 0;
 
   unsigned long long* key = nullptr;
@@ -140,6 +141,7 @@ struct ac_sim {
     d.t2 = 2ull * (unsigned long long)t_end;
     d.drop_publish = drop_publish;
     d.model = model;
+    d.q = q;
     d.life_density = life_density;
     d.rates = d_rates;
     if (model == 1) {
@@ -373,6 +375,20 @@ void tb_tiling_batch(int rows, int cols, int region, int halo, int* tr, int* tc)
   *tc = std::max(2, ceil_div(cols, own));
 }
 
+// Halo depth D and rounds per launch R of the temporal-blocked kernel for the handle's
+// model: D = R for the 4-neighbour array and the Life automaton, D = q R for the q-th
+// degree neighbourhood (the region loses q rings per round); D <= 16 and rows, cols >= 4D.
+void tb_depth(const ac_sim* s, int* D, int* R) {
+  const int side = std::min(s->rows, s->cols);
+  if (s->model == 0) {
+    *R = *D = s->cfg.rounds;
+  } else {
+    const int q = (s->model == 2) ? s->q : 1;
+    *R = std::max(1, std::min({s->cfg.rounds, ac::kTbMaxHalo / q, side / (4 * q)}));
+    *D = q * (*R);
+  }
+}
+
 bool tb_applicable(const ac_sim* s) {
   const int D = s->cfg.rounds;
   return s->cfg.rounds > 1 && D <= ac::kTbMaxHalo && s->rows >= 4 * D && s->cols >= 4 * D;
@@ -395,7 +411,7 @@ ac_status tb_counts_fit(ac_sim* s, long long t_end, bool* fits) {
   return AC_OK;
 }
 
-ac_status run_tb(ac_sim* s, long long t_end, int D) {
+ac_status run_tb(ac_sim* s, long long t_end, int D, int R) {
   const size_t N = s->ncells();
   if (!s->key2) {
     if (cudaMalloc(&s->key2, N * 8) != cudaSuccess || cudaMalloc(&s->cnt2, N * 4) != cudaSuccess) {
@@ -419,7 +435,7 @@ ac_status run_tb(ac_sim* s, long long t_end, int D) {
   int launch_idx = 0;
   for (;;) {
     for (int i = 0; i < chunk; ++i) {
-      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, D, s->d_ctr, s->stream, s->f_B > 0, s->model == 1));
+      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, R, s->d_ctr, s->stream, s->f_B > 0, s->model));
       ++launch_idx;
     }
     ac::DevCounters cc{};
@@ -450,21 +466,22 @@ ac_status run_tb(ac_sim* s, long long t_end, int D) {
 }
 
 ac_status run_round(ac_sim* s, long long t_end) {
-  if (s->model == 1) {
-    // the Life automaton runs on the temporal-blocked kernel only (its enable test needs
-    // the diagonal neighbours, which the region holds): halo depth capped by the lattice
-    const int D = std::max(1, std::min(s->cfg.rounds, std::min(s->rows, s->cols) / 4));
+  if (s->model != 0) {
+    // the Life automaton and the q-th degree neighbourhood run on the temporal-blocked
+    // kernel only (their enable tests need the diagonal / farther cells the region holds)
+    int D = 0, R = 0;
+    tb_depth(s, &D, &R);
     bool fits = false;
     ac_status st = tb_counts_fit(s, t_end, &fits);
     if (st != AC_OK) return st;
-    if (!fits) return fail(AC_ERR_STATE, "Life: event counts too uneven for the temporal-blocked kernel");
-    return run_tb(s, t_end, D);
+    if (!fits) return fail(AC_ERR_STATE, "event counts too uneven for the temporal-blocked kernel");
+    return run_tb(s, t_end, D, R);
   }
   if (tb_applicable(s)) {
     bool fits = false;
     ac_status st = tb_counts_fit(s, t_end, &fits);
     if (st != AC_OK) return st;
-    if (fits) return run_tb(s, t_end, s->cfg.rounds);
+    if (fits) return run_tb(s, t_end, s->cfg.rounds, s->cfg.rounds);
     // counts too uneven for the 16-bit window: one exact synchronous round per launch
     const int saved = s->cfg.rounds;
     s->cfg.rounds = 1;
@@ -718,7 +735,7 @@ ac_status deliver_frame(ac_sim* s, ac_frame_fn fn, void* user, int on_host) {
 // current state buffer) and raises the commit cap to (f_K + B) dt + 1 for the next
 // launches.  The lag bound is the same as with whole windows; no launch waits for
 // the whole lattice to reach a window's end.
-ac_status run_tb_frames(ac_sim* s, long long t_end, ac_frame_fn fn, void* user, int on_host, int D) {
+ac_status run_tb_frames(ac_sim* s, long long t_end, ac_frame_fn fn, void* user, int on_host, int D, int R) {
   const size_t N = s->ncells();
   if (!s->key2) {
     if (cudaMalloc(&s->key2, N * 8) != cudaSuccess || cudaMalloc(&s->cnt2, N * 4) != cudaSuccess) {
@@ -750,14 +767,14 @@ ac_status run_tb_frames(ac_sim* s, long long t_end, ac_frame_fn fn, void* user, 
   // about 8.3 synchronous rounds per unit time (Sec. 4), D per launch: check often
   // enough that the cap is raised before cells wait long on it
   const double lag = (double)s->f_B * (double)s->f_dt / kTicksPerUnit;
-  const int chunk = std::max(1, std::min(4, (int)(lag * 8.3 / D / 2.0)));
+  const int chunk = std::max(1, std::min(4, (int)(lag * 8.3 / R / 2.0)));
   const double span = (double)(t_end - s->t_done) / kTicksPerUnit;
   const double max_launches = 64.0 * (9.0 * std::ceil(span) + 16.0) / D + 4096.0;
   int issued = 0;
   ac::DevCounters c{};
   for (;;) {
     for (int i = 0; i < chunk; ++i) {
-      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, D, s->d_ctr, s->stream, true, s->model == 1));
+      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, R, s->d_ctr, s->stream, true, s->model));
       ++issued;
     }
     AC_CUDA(cudaMemcpyAsync(&c, s->d_ctr, sizeof c, cudaMemcpyDeviceToHost, s->stream));
@@ -833,17 +850,17 @@ ac_status run_frames(ac_sim* s, long long t_end, ac_frame_fn fn, void* user, int
   }
   // the temporal-blocked kernel slides the window frame by frame (run_tb_frames); the
   // other kernels run whole windows: to the cap, then every open frame is complete
-  if (t_end > s->t_done && s->cfg.kernel == ac::kKernelRound && (s->model == 1 || tb_applicable(s))) {
-    const int D = (s->model == 1) ? std::max(1, std::min(s->cfg.rounds, std::min(s->rows, s->cols) / 4))
-                                  : s->cfg.rounds;
+  if (t_end > s->t_done && s->cfg.kernel == ac::kKernelRound && (s->model != 0 || tb_applicable(s))) {
+    int D = 0, R = 0;
+    tb_depth(s, &D, &R);
     bool fits = false;
     ac_status st = tb_counts_fit(s, t_end, &fits);
     if (st != AC_OK) return st;
     if (fits) {
-      st = run_tb_frames(s, t_end, fn, user, on_host, D);
+      st = run_tb_frames(s, t_end, fn, user, on_host, D, R);
       if (st != AC_OK) return st;
-    } else if (s->model == 1) {
-      return fail(AC_ERR_STATE, "Life: event counts too uneven for the temporal-blocked kernel");
+    } else if (s->model != 0) {
+      return fail(AC_ERR_STATE, "event counts too uneven for the temporal-blocked kernel");
     }
   }
   for (;;) {
@@ -920,6 +937,33 @@ ac_status ac_create_life(ac_lattice lat, uint32_t density, uint32_t birth, uint3
   return AC_OK;
 }
 
+ac_status ac_create_q(ac_lattice lat, double beta, double J, double h, int32_t q, uint64_t seed, ac_sim** out) {
+  if (!out) return fail(AC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (q < 2 || q > 3) return fail(AC_ERR_ARG, "q must be 2 or 3 (q = 1 is ac_create)");
+  if (lat.rows < 4 * q || lat.cols < 4 * q) return fail(AC_ERR_ARG, "rows, cols must be >= 4q (got %d x %d)", lat.rows, lat.cols);
+  ac_status st = check_params(lat, beta, J, h);
+  if (st != AC_OK) return st;
+  st = create_one(lat, beta, J, h, seed, out);
+  if (st != AC_OK) return st;
+  ac_sim* s = *out;
+  s->model = 2;
+  s->q = q;
+  const int M = 2 * q * (q + 1);
+  for (int sp = 0; sp < 2; ++sp) {
+    const double sv = sp ? 1.0 : -1.0;
+    for (int j = 0; j <= M; ++j) {
+      const double S = (double)(2 * j - M);
+      const double p = 1.0 / (1.0 + std::exp(beta * 2.0 * sv * (J * S + h)));
+      const double v = std::ldexp(p, 32);
+      s->thr[j + (M + 1) * sp] = (v < 4294967295.0) ? (uint32_t)std::floor(v) : 0xFFFFFFFFu;
+    }
+  }
+  s->cfg.kernel = ac::kKernelRound;
+  s->cfg.rounds = 6;
+  return AC_OK;
+}
+
 ac_status ac_set_stream(ac_sim* sim, void* stream) {
   if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
   sim->stream = (cudaStream_t)stream;
@@ -934,8 +978,8 @@ ac_status ac_configure(ac_sim* sim, int32_t kernel, int32_t Lb, int32_t rounds, 
   if (Lb != 32 && Lb != 64 && Lb != 128) return fail(AC_ERR_ARG, "Lb must be 32, 64 or 128");
   if (rounds < 1 || rounds > 1 << 20) return fail(AC_ERR_ARG, "rounds must be in [1, 2^20]");
   if (polls < 0 || polls > 1 << 20) return fail(AC_ERR_ARG, "polls must be in [0, 2^20]");
-  if (sim->model == 1 && kernel != AC_KERNEL_ROUND)
-    return fail(AC_ERR_ARG, "the Life automaton runs on the round kernel (AC_KERNEL_ROUND) only");
+  if (sim->model != 0 && kernel != AC_KERNEL_ROUND)
+    return fail(AC_ERR_ARG, "the Life automaton and the q-th degree neighbourhood run on the round kernel only");
   sim->cfg.kernel = kernel;
   sim->cfg.lb = Lb;
   sim->cfg.threads = 4 * Lb;
@@ -1232,7 +1276,7 @@ ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_en
   for (int i = 0; i < n; ++i) {
     if (!sims[i]) return fail(AC_ERR_ARG, "sims[%d] is NULL", i);
     if (sims[i]->f_B > 0) return fail(AC_ERR_ARG, "sims[%d] has snapshot frames: run it with ac_run_until_frames", i);
-    if (sims[i]->model != 0) return fail(AC_ERR_ARG, "sims[%d] is a Life automaton: batches hold Ising lattices", i);
+    if (sims[i]->model != 0) return fail(AC_ERR_ARG, "sims[%d] is not the 4-neighbour Ising array: batches hold those only", i);
     if (sims[i]->cfg.lb != sims[0]->cfg.lb) return fail(AC_ERR_ARG, "all handles must share a tile side");
     if (sims[i]->stream != sims[0]->stream) return fail(AC_ERR_ARG, "all handles must share a stream");
     if (t_end[i] < sims[i]->t_done) return fail(AC_ERR_ARG, "t_end[%d] is below its previous t_end", i);

@@ -16,6 +16,10 @@ namespace ac {
 // same for columns; every tile side is <= lb.
 // Edge words: pub[(ti*tc + tj)*4*lb + e*lb + p] is the key of the tile's boundary
 // cell p on edge e (0 top row, 1 bottom row, 2 left column, 3 right column).
+// Threshold table capacity: 10 entries for the 4-neighbour array, 2 (M + 1) for the
+// q-th degree neighbourhood with M = 2 q (q + 1) neighbours (q <= 3).
+constexpr int kThrMax = 50;
+
 struct LatDesc {
   unsigned long long* key;
   unsigned int* cnt;
@@ -28,7 +32,8 @@ struct LatDesc {
   int tr, tc;
   int lb;
   int tile_base;             // first tile of this lattice in the launch's work list
-  unsigned int thr[10];      // flip thresholds, index j + 5*(s > 0)
+  unsigned int thr[kThrMax]; // flip thresholds, index j + 5*(s > 0) (q-th degree neighbourhood:
+                             // j + (M+1)*(s > 0)); the Life automaton keeps its masks in thr[0..1]
   unsigned int seed_lo, seed_hi;
   long long t_end;           // commit arrivals with tick < t_end
   unsigned long long t2;     // 2 * t_end: key < t2  <=>  tick < t_end
@@ -43,8 +48,11 @@ struct LatDesc {
   int f_open, f_slot0, f_B;
   // model: 0 = Ising heat bath (thr = flip thresholds); 1 = Life-like automaton on the
   // Moore neighbourhood (thr[0] = birth mask, thr[1] = survival mask over the number of
-  // live neighbours; a random initial cell is alive iff its init word < life_density)
+  // live neighbours; a random initial cell is alive iff its init word < life_density);
+  // 2 = Ising heat bath on the q-th degree neighbourhood (every cell within Manhattan
+  // distance q, 2 <= q <= 3)
   int model;
+  int q;
   unsigned life_density;
   // per-cell rates (law (A) of Sec. 2): cell c's gaps are max(1, floor(e * rates[c] / 2^20))
   // for the rate-1 gap e, i.e. rate 2^20 / rates[c]; nullptr = every cell at rate 1
@@ -111,9 +119,11 @@ cudaError_t launch_pack(const LatDesc* host_desc, const int8_t* s_in, const long
 // ping-pong parity) is kept on the device in ctr->seq, so every launch of a run has
 // the same arguments and a sequence of launches can be captured in a CUDA graph.
 // frames: the lattices have open snapshot frames (the kernel variant that writes them);
-// life: the lattices hold the Life-like automaton (all lattices of a launch share the model).
+// model: the lattices' model (LatDesc::model; all lattices of a launch share it).
+// The q-th degree neighbourhood model shrinks the region by q rings per round:
+// halo = q * rounds.
 cudaError_t launch_tb(const LatDesc* d_desc, int nlat, int total_tiles, int region, int halo, int rounds,
-                      DevCounters* ctr, cudaStream_t s, bool frames = false, bool life = false);
+                      DevCounters* ctr, cudaStream_t s, bool frames = false, int model = 0);
 // Frames [K, K + count) were just opened: write each cell's spin into those whose tick
 // lies before the cell's next arrival (later commits write the others).
 cudaError_t launch_frames_fill(const LatDesc* host_desc, long long K, int count, cudaStream_t s);

@@ -393,7 +393,7 @@ __global__ void init_kernel(LatDesc L, int init_mode) {
     else if (init_mode == 2) up = 0u;
     else {
       const uint32_t x = philox_event((uint32_t)c, 0u, 1u, L.seed_lo, L.seed_hi).x;
-      up = L.model ? (x < L.life_density ? 1u : 0u) : (x & 1u);   // Life: alive with the given density
+      up = (L.model == 1) ? (x < L.life_density ? 1u : 0u) : (x & 1u);   // Life: alive with the given density
     }
     unsigned long long t0 = exp_ticks(b0.x, L.two);
     if (L.rates) t0 = rated_gap(t0, L.rates[c]);
@@ -658,7 +658,7 @@ struct TbCfg {
   static constexpr size_t cBytes = size_t(RW) * RW * 2;
   static constexpr size_t lBytes = size_t(LIST) * 2;
   static constexpr size_t gBytes = size_t(RW) * 4 * 2;
-  static constexpr size_t mBytes = 64;
+  static constexpr size_t mBytes = (4 + kThrMax) * 4;   // n_en[2], overflow flag, thresholds
   static constexpr size_t fBytes = 64;            // snapshot-frame view (frame variant), 16-byte aligned
   static constexpr size_t fOff = (kBytes + cBytes + lBytes + gBytes + mBytes + 15) / 16 * 16;
   static constexpr size_t bytes = fOff + fBytes;
@@ -775,10 +775,59 @@ __device__ __forceinline__ unsigned life_scan_exact(const unsigned long long* K,
   return mask;
 }
 
+// ---- Ising array on the q-th degree neighbourhood (Sec. 3): every cell within
+// Manhattan distance q is a neighbour; a cell may commit once its key is below all of
+// theirs.  Enabled cells are then more than q apart, so commits never read each other.
+
+// up spins among the diamond of radius q around the region cell at kp
+template <int RW>
+__device__ __forceinline__ unsigned q_up(const unsigned long long* kp, int q) {
+  unsigned j = 0;
+  for (int dr = -q; dr <= q; ++dr) {
+    const int rem = q - (dr < 0 ? -dr : dr);
+    for (int dx = -rem; dx <= rem; ++dx)
+      if (dr != 0 || dx != 0) j += (unsigned)kp[dr * RW + dx] & 1u;
+  }
+  return j;
+}
+
+// Enable test of a thread's column pair over ROWS rows: ticks compared directly, equal
+// ticks ordered by the cells' lattice indices.  Cells closer than q to the region's
+// edge are never valid for this model and are skipped (their diamonds leave the region).
+template <int RW, int ROWS>
+__device__ __forceinline__ unsigned q_scan_exact(const unsigned long long* K, const unsigned* rowoff,
+                                                 const unsigned* colg, int rbase, int pc,
+                                                 unsigned long long t2, int q) {
+  unsigned mask = 0;
+  for (int i = 0; i < ROWS; ++i) {
+    const int r = rbase + i;
+    for (int e = 0; e < 2; ++e) {
+      const int c = pc + e;
+      if (r < q || r > RW - 1 - q || c < q || c > RW - 1 - q) continue;
+      const unsigned long long kc = K[r * RW + c];
+      const unsigned long long tc = kc >> 1;
+      const unsigned gc = rowoff[r] + colg[c];
+      bool ok = kc < t2;
+      for (int dr = -q; dr <= q && ok; ++dr) {
+        const int rem = q - (dr < 0 ? -dr : dr);
+        for (int dx = -rem; dx <= rem; ++dx) {
+          if (dr == 0 && dx == 0) continue;
+          const unsigned long long tn = K[(r + dr) * RW + c + dx] >> 1;
+          const unsigned gn = rowoff[r + dr] + colg[c + dx];
+          ok &= (tc < tn) || (tc == tn && gc < gn);
+        }
+      }
+      mask |= (unsigned)ok << (2 * i + e);
+    }
+  }
+  return mask;
+}
+
 // FR: snapshot frames are open (write_frames for the tile's own cells).
-// LIFE: the Life-like automaton (Moore neighbourhood, birth / survival masks in
-// thr[0] / thr[1]) instead of the Ising heat bath.
-template <int RW, bool FR, bool LIFE>
+// MODEL: 0 the Ising heat bath; 1 the Life-like automaton (Moore neighbourhood, birth /
+// survival masks in thr[0] / thr[1]); 2 the Ising heat bath on the q-th degree
+// neighbourhood (radius L.q; the region shrinks by q rings per round).
+template <int RW, bool FR, int MODEL>
 __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     tb_kernel(const LatDesc* __restrict__ lats, int nlat, int total_tiles, int D, int R, DevCounters* ctr) {
   using Cfg = TbCfg<RW>;
@@ -791,8 +840,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   unsigned int* colg = rowoff + RW;
   unsigned int* misc = colg + RW;
   unsigned int* n_en = misc;          // [2]
-  unsigned int* thr = misc + 2;       // [10]
-  unsigned int* s_over = misc + 12;   // count window overflow in this region
+  unsigned int* s_over = misc + 2;    // count window overflow in this region
+  unsigned int* thr = misc + 4;       // [kThrMax]
   FrameView* fv = reinterpret_cast<FrameView*>(smem_raw + Cfg::fOff);
   static_assert(sizeof(FrameView) <= Cfg::fBytes, "frame view does not fit");
 
@@ -877,13 +926,13 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       int sh;
       rowoff[tid] = (unsigned)wrap_index(min(g.r0 - D + tid, 2 * L.rows - 1), L.rows, sh, 2) * (unsigned)L.cols;
       colg[tid] = (unsigned)wrap_index(min(g.c0 - D + tid, 2 * L.cols - 1), L.cols, sh, 2);
-    } else if (tid < RW + 10) {
+    } else if (tid < RW + kThrMax) {
       thr[tid - RW] = L.thr[tid - RW];
     }
     if (over) atomicOr(s_over, 1u);
     cp_async_wait_all();
     __syncthreads();
-    if (edge && !LIFE) {   // halo cells from across the torus seam: key +-2 (one tick of tie order)
+    if (edge && MODEL == 0) {   // halo cells from across the torus seam: key +-2 (one tick of tie order)
       if (lj < RC) {
         for (int i = li0; i < RH; i += Cfg::LSTRIDE) {
           int shr;
@@ -908,9 +957,11 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     const unsigned* __restrict__ rates = L.rates;
     constexpr unsigned kEven = 0x55555555u, kOdd = 0xAAAAAAAAu;
     int cur = 0;
+    const int qn = (MODEL == 2) ? L.q : 1;     // rings lost per round
     for (int k = 1; k <= R; ++k) {
-      const unsigned colm = ((pc >= k && pc < RC - k) ? kEven : 0u) | ((pc + 1 >= k && pc + 1 < RC - k) ? kOdd : 0u);
-      const int rlo = max(k - rbase, 0), rhi = min(RH - k - rbase, Cfg::ROWS);
+      const int kk = k * qn;
+      const unsigned colm = ((pc >= kk && pc < RC - kk) ? kEven : 0u) | ((pc + 1 >= kk && pc + 1 < RC - kk) ? kOdd : 0u);
+      const int rlo = max(kk - rbase, 0), rhi = min(RH - kk - rbase, Cfg::ROWS);
       unsigned rowm = 0u;
       if (rhi > rlo) {
         const unsigned hi_bits = (2 * rhi >= 32) ? 0xFFFFFFFFu : ((1u << (2 * rhi)) - 1u);
@@ -918,10 +969,13 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       }
       const unsigned valid = colm & rowm;
       unsigned mask = 0;
-      if (LIFE && valid) {
+      if (MODEL == 1 && valid) {
         mask = edge ? life_scan_exact<RW, Cfg::ROWS>(K, rowoff, colg, rbase, pc, t2)
                     : life_scan<RW, Cfg::ROWS>(K, rbase, pc, t2);
         mask &= valid;
+        scanned += (unsigned long long)__popc(valid);
+      } else if (MODEL == 2 && valid) {
+        mask = q_scan_exact<RW, Cfg::ROWS>(K, rowoff, colg, rbase, pc, t2, qn) & valid;
         scanned += (unsigned long long)__popc(valid);
       } else if (valid) {
         const unsigned long long* q = K + rbase * RW + pc;
@@ -982,9 +1036,13 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const uint32_t gia = rowoff[ra] + colg[ca], gib = rowoff[rb] + colg[cb];
         const unsigned c16a = C[ra * RW + ca], c16b = C[rb * RW + cb];
         unsigned tha, thb;
-        if (LIFE) {   // rule mask of the current state; the new state is its bit k
+        if (MODEL == 1) {   // rule mask of the current state; the new state is its bit k
           tha = thr[spa];
           thb = thr[spb];
+        } else if (MODEL == 2) {
+          const unsigned M1 = 2u * qn * (qn + 1) + 1u;
+          tha = thr[q_up<RW>(kpa, qn) + M1 * spa];
+          thb = thr[q_up<RW>(kpb, qn) + M1 * spb];
         } else {
           const unsigned ja = ((unsigned)kpa[-RW] & 1u) + ((unsigned)kpa[RW] & 1u) + ((unsigned)kpa[-1] & 1u) +
                               ((unsigned)kpa[1] & 1u);
@@ -1000,8 +1058,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
           gapa = rated_gap(gapa, rates[gia]);
           gapb = rated_gap(gapb, rates[gib]);
         }
-        const unsigned nsa = LIFE ? (tha >> moore_live<RW>(kpa)) & 1u : spa ^ (pa.y < tha ? 1u : 0u);
-        const unsigned nsb = LIFE ? (thb >> moore_live<RW>(kpb)) & 1u : spb ^ (pb.y < thb ? 1u : 0u);
+        const unsigned nsa = MODEL == 1 ? (tha >> moore_live<RW>(kpa)) & 1u : spa ^ (pa.y < tha ? 1u : 0u);
+        const unsigned nsb = MODEL == 1 ? (thb >> moore_live<RW>(kpb)) & 1u : spb ^ (pb.y < thb ? 1u : 0u);
         const unsigned long long nka = (keya & ~1ull) + (gapa << 1) + nsa;
         const unsigned long long nkb = (keyb & ~1ull) + (gapb << 1) + nsb;
         *kpa = nka;
@@ -1025,8 +1083,11 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const unsigned c16 = C[r * RW + cc];
         const Philox4 b = philox_event(gidx, base + c16 + 1u, 0u, seed_lo, seed_hi);
         unsigned ns;
-        if (LIFE) {
+        if (MODEL == 1) {
           ns = (thr[sp] >> moore_live<RW>(kp)) & 1u;
+        } else if (MODEL == 2) {
+          const unsigned M1 = 2u * qn * (qn + 1) + 1u;
+          ns = sp ^ (b.y < thr[q_up<RW>(kp, qn) + M1 * sp] ? 1u : 0u);
         } else {
           const unsigned j = ((unsigned)kp[-RW] & 1u) + ((unsigned)kp[RW] & 1u) + ((unsigned)kp[-1] & 1u) +
                              ((unsigned)kp[1] & 1u);
@@ -1385,37 +1446,45 @@ cudaError_t launch_pack(const LatDesc* h, const int8_t* si, const long long* ti,
 }
 
 
-template <int RW, bool FR, bool LIFE>
+template <int RW, bool FR, int MODEL>
 cudaError_t tb_launch_rw(const LatDesc* d, int nlat, int total, int halo, int rounds, DevCounters* ctr,
                          cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW, FR, LIFE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW, FR, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)TbCfg<RW>::bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int grid = std::min(total, tb_grid(RW));
-  tb_kernel<RW, FR, LIFE><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds, ctr);
+  tb_kernel<RW, FR, MODEL><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds, ctr);
   return cudaGetLastError();
+}
+
+template <int RW, int MODEL>
+cudaError_t tb_launch_frames(const LatDesc* d, int nlat, int total, int halo, int rounds, DevCounters* ctr,
+                             cudaStream_t s, bool frames) {
+  return frames ? tb_launch_rw<RW, true, MODEL>(d, nlat, total, halo, rounds, ctr, s)
+                : tb_launch_rw<RW, false, MODEL>(d, nlat, total, halo, rounds, ctr, s);
 }
 
 template <int RW>
 cudaError_t tb_launch_model(const LatDesc* d, int nlat, int total, int halo, int rounds, DevCounters* ctr,
-                            cudaStream_t s, bool frames, bool life) {
-  if (life)
-    return frames ? tb_launch_rw<RW, true, true>(d, nlat, total, halo, rounds, ctr, s)
-                  : tb_launch_rw<RW, false, true>(d, nlat, total, halo, rounds, ctr, s);
-  return frames ? tb_launch_rw<RW, true, false>(d, nlat, total, halo, rounds, ctr, s)
-                : tb_launch_rw<RW, false, false>(d, nlat, total, halo, rounds, ctr, s);
+                            cudaStream_t s, bool frames, int model) {
+  switch (model) {
+    case 0: return tb_launch_frames<RW, 0>(d, nlat, total, halo, rounds, ctr, s, frames);
+    case 1: return tb_launch_frames<RW, 1>(d, nlat, total, halo, rounds, ctr, s, frames);
+    case 2: return tb_launch_frames<RW, 2>(d, nlat, total, halo, rounds, ctr, s, frames);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_tb(const LatDesc* d, int nlat, int total, int region, int halo, int rounds, DevCounters* ctr,
-                      cudaStream_t s, bool frames, bool life) {
+                      cudaStream_t s, bool frames, int model) {
   if (halo < 1 || rounds < 1 || rounds > halo || 4 * halo >= region) return cudaErrorInvalidValue;
   switch (region) {
-    case 96: return tb_launch_model<96>(d, nlat, total, halo, rounds, ctr, s, frames, life);
-    case 128: return tb_launch_model<128>(d, nlat, total, halo, rounds, ctr, s, frames, life);
+    case 96: return tb_launch_model<96>(d, nlat, total, halo, rounds, ctr, s, frames, model);
+    case 128: return tb_launch_model<128>(d, nlat, total, halo, rounds, ctr, s, frames, model);
     default: return cudaErrorInvalidValue;
   }
 }
