@@ -34,7 +34,7 @@ MUTANTS = {
                              lambda: dyn.test_heap_equals_linear_scan(3, 2, 3, 0.3, -0.1, 6)),
     "tie_break_reversed": ("(t[a] == t[b] && a < b)", "(t[a] == t[b] && a > b)",
                            dyn.test_forced_tie_is_broken_by_index),
-    "gap_and_uniform_swapped": ("if (b[1] < thr[up", "if (b[0] < thr[up",
+    "gap_and_uniform_swapped": ("if (b[1] < thr[up + 5 * (s[c] > 0)])", "if (b[0] < thr[up + 5 * (s[c] > 0)])",
                                 lambda: dyn.test_heap_equals_linear_scan(4, 5, 5, 1.0, 0.05, 4)),
     "philox_words_swapped": ("uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;",
                              "uint32_t n0 = (uint32_t)(p1 >> 32) ^ c3 ^ k0;",
