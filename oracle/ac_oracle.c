@@ -47,15 +47,15 @@
  *              neighbours, as in the appendix's prob[10].
  *   R7 nbrs    4 nearest neighbours on the periodic torus, counted with
  *              multiplicity (on a 2-wide torus both sides are one cell).
- *   R14 q-nbhd the Ising array on the q-th degree neighbourhood (see
- *              aco_run_q below).
- *   R13 rates  per-cell rates of law (A): gap scaled by m_c / 2^20 (see
- *              aco_rated_gap below).
- *   R12 life   Life-like rules: Moore neighbourhood, birth / survival masks
- *              over the live-neighbour count (see aco_life_run below).
  *   R11 laws   time-only model of Sec. 4: exponential (R5), uniform on
  *              (0, 1] as x + 1 ticks, and r^(1/8) as three nested integer
  *              square roots (see aco_gap below).
+ *   R12 life   Life-like rules: Moore neighbourhood, birth / survival masks
+ *              over the live-neighbour count (see aco_life_run below).
+ *   R13 rates  per-cell rates of law (A): gap scaled by m_c / 2^20 (see
+ *              aco_rated_gap below).
+ *   R14 q-nbhd the Ising array on the q-th degree neighbourhood (see
+ *              aco_run_q below).
  *
  * Build: plain C99 + libm, -O2 -ffp-contract=off (no fused multiply-add, so
  * the binary64 table is the same on every host).
