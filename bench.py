@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the per-kernel side measurements")
     ap.add_argument("--workload", default="ising4096",
                     choices=["ising4096", "batch", "serve", "frames", "configs", "efficiency", "life", "rates",
-                             "qnbhd"],
+                             "qnbhd", "sizes"],
                     help="ising4096: the headline step; batch: the 512-lattice batch only; serve: the request stream")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the replayed request stream")
     ap.add_argument("--single", action="store_true",
@@ -247,6 +247,14 @@ def main():
         res = configs_measurement()
         print(json.dumps({"workload": args.workload, **res}), flush=True)
         return 0
+    if args.workload == "sizes":
+        import torch
+        torch.cuda.set_device(0)
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_cs_0502039_gb300 as ac
+        print(json.dumps({"workload": args.workload, **sizes_measurement(ac)}), flush=True)
+        return 0
     if args.workload == "qnbhd":
         import torch
         torch.cuda.set_device(0)
@@ -317,7 +325,7 @@ def main():
     tuned = None
     if not args.no_autotune:
         from paper_cs_0502039_gb300 import autotune
-        tuned = autotune.tune(w["rows"], w["cols"], T=4.0)
+        tuned = autotune.tune(w["rows"], w["cols"])
         kern, args.lb, args.rounds, args.polls = tuned["kernel"], tuned["Lb"], tuned["rounds"], tuned["polls"]
         args.kernel = "blocked" if kern == ac.AC_KERNEL_BLOCKED else "round"
     # weak scaling: every rank runs its own replica batch (seed offset by rank)
@@ -606,6 +614,33 @@ def frames_measurement(ac, rounds=6, lb=64):
     return out
 
 
+def sizes_measurement(ac):
+    """Single-lattice throughput against the lattice side L (beta 0.4407, random start from seed 7):
+    the temporal-blocked round kernel at 6 rounds per launch, the blocked kernel with tiles of 64 and
+    128, and the autotuner's choice for the size class.  T is chosen so that a run is a few tens of
+    milliseconds or more."""
+    import torch
+    from paper_cs_0502039_gb300 import autotune
+    R, B = ac.AC_KERNEL_ROUND, ac.AC_KERNEL_BLOCKED
+    out = {"beta": 0.4407, "cases": []}
+    for L, T in ((256, 200), (512, 100), (1024, 50), (2048, 50), (4096, 50), (8192, 10), (16384, 5)):
+        tuned = autotune.tune(L, L)
+        row = {"L": L, "T": T, "autotuned_config": {k: tuned[k] for k in ("kernel", "Lb", "rounds", "polls")}}
+        for name, kern, lb, rounds, polls in (("round_r6", R, 64, 6, 0), ("blocked_lb64", B, 64, 1, 8),
+                                              ("blocked_lb128", B, 128, 1, 8),
+                                              ("autotuned", tuned["kernel"], tuned["Lb"], tuned["rounds"],
+                                               tuned["polls"])):
+            with ac.Sim(L, L, 0.4407, 1.0, 0.0, 7, kernel=kern, Lb=lb, rounds=rounds, polls=polls) as sim:
+                sim.run_until(min(T, 2))
+                sim.reset(7)
+                torch.cuda.synchronize()
+                sim.run_until(T)
+                st = sim.stats()
+            row[name] = {"events_per_s": st["events"] / (st["device_ms"] / 1000.0), "device_ms": st["device_ms"]}
+        out["cases"].append(row)
+    return out
+
+
 def qnbhd_measurement(ac):
     """The Ising array on the q-th degree neighbourhood (Sec. 3) on a 4096^2 torus, random start
     (seed 7), beta 0.15, run to T = 50 with the temporal-blocked kernel, for q = 1, 2, 3."""
@@ -774,7 +809,7 @@ def configs_measurement():
 
     out["c1"] = [measure(64, 64, 0, 1, 0.44, 0.0, 10, k, lb, r, p, 10)
                  for k, lb, r, p in [(R, 32, 1, 0), (R, 64, 4, 0), (B, 32, 1, 8), (B, 64, 1, 8)]]
-    tuned = autotune.tune(16384, 16384, T=2.0)
+    tuned = autotune.tune(16384, 16384)
     cfgs = [(tuned["kernel"], tuned["Lb"], tuned["rounds"], tuned["polls"]), (R, 64, 6, 0),
             (B, 32, 1, 8), (B, 64, 1, 8), (B, 128, 1, 8)]
     out["c3"] = [measure(16384, 16384, 1, 3, 1.0, 0.05, 20, k, lb, r, p, 1) for k, lb, r, p in cfgs]

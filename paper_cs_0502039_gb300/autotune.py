@@ -1,9 +1,9 @@
 """Autotuner: pick the kernel and its tuning per lattice size class by timing them.
 
 For a (rows, cols) class -- each side rounded up to a power of two -- every candidate
-configuration runs the same short trajectory (a lattice of the class's size, seed 1,
-beta 0.44) and the one with the highest committed-arrival rate (device time of the
-run calls) wins.  The trajectory is the same for every candidate (Sec. 3: it does not
+configuration runs the same trajectory (a lattice of the class's size, seed 1, beta
+0.44, about 5e8 arrivals by default) and the one with the highest committed-arrival
+rate (device time of the run calls) wins.  The trajectory is the same for every candidate (Sec. 3: it does not
 depend on the partition or the schedule), so the tuner changes speed only; it also
 checks that every candidate ends in the same state fingerprint.  Results are cached
 in a JSON file keyed by GPU name and size class.
@@ -63,14 +63,22 @@ def measure(rows: int, cols: int, cfg: dict, T: float = 2.0) -> dict:
                 events_per_s=st["events"] / max(st["device_ms"], 1e-6) * 1e3, checksum=st["checksum"])
 
 
-def tune(rows: int, cols: int, T: float = 2.0, cache_path: str | None = None, force: bool = False) -> dict:
-    """Best configuration for the size class of (rows, cols); cached."""
+def horizon(rows: int, cols: int) -> float:
+    """Trial length: about 5e8 arrivals (fixed per-call costs then weigh as in real runs), T in [2, 50]."""
+    return min(50.0, max(2.0, 5e8 / (_bucket(rows) * _bucket(cols))))
+
+
+def tune(rows: int, cols: int, T: float | None = None, cache_path: str | None = None, force: bool = False) -> dict:
+    """Best configuration for the size class of (rows, cols); cached.  T: the trial run's length
+    (default: horizon())."""
     path = cache_path or os.environ.get("AC_AUTOTUNE_CACHE", DEFAULT_CACHE)
     cache = _load(path)
     key = class_key(rows, cols)
     if key in cache and not force:
         return cache[key]
     R, C = _bucket(rows), _bucket(cols)
+    if T is None:
+        T = horizon(rows, cols)
     results = [measure(R, C, cfg, T) for cfg in CANDIDATES]
     sums = {r["checksum"] for r in results}
     if len(sums) != 1:
