@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--rounds", type=int, default=8,
                     help="round kernel: synchronous rounds per launch (>1: temporal blocking); blocked: refresh")
     ap.add_argument("--polls", type=int, default=8)
+    ap.add_argument("--batched", action="store_true",
+                    help="round kernel: run the lattices of a step as one batch (one work list of all their "
+                         "tiles) instead of one after another")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --kernel/--lb/--rounds/--polls as given instead of the autotuned configuration")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -336,10 +339,15 @@ def main():
     handles = [s.handle for s in sims]
     t_end = [w["T"] * T32] * len(sims)
 
+    # the step's lattices run one after another (measured faster end to end than one batched
+    # call, whose host-side checks cost more than its shorter device time saves); --batched
+    # runs them as one batch, as the blocked kernel always does
+    batched = kern == ac.AC_KERNEL_BLOCKED or args.batched
+
     def step():
         for s in sims:
             s.reset(seed, w["init"])
-        if kern == ac.AC_KERNEL_BLOCKED:
+        if batched:
             ac.ac_batch_run_until(handles, t_end)
         else:
             for s in sims:
@@ -362,14 +370,18 @@ def main():
         step()
         st = [s.stats() for s in sims]
         ev_step = sum(x["events"] for x in st)
-        if kern == ac.AC_KERNEL_BLOCKED:
-            kern_ms_list.append(st[0]["device_ms"])          # one batched launch (same on every handle)
+        if batched:
+            kern_ms_list.append(st[0]["device_ms"])          # one batched call (same on every handle)
         else:
             kern_ms_list.append(sum(x["device_ms"] for x in st))
-    # init per lattice, then: blocked = publish + one kernel; round = (count-range check +)
-    # the round launches of each lattice
-    launches_per_step = (len(sims) + 2 if kern == ac.AC_KERNEL_BLOCKED
-                         else sum(1 + (1 if args.rounds > 1 else 1) + x["launches"] for x in st))
+    # init per lattice, then: blocked = publish + one kernel; batched round = count-range check +
+    # the launches over all lattices' tiles; per lattice = count-range check + its launches
+    if kern == ac.AC_KERNEL_BLOCKED:
+        launches_per_step = len(sims) + 2
+    elif batched:
+        launches_per_step = len(sims) + 1 + st[0]["launches"]
+    else:
+        launches_per_step = sum(2 + x["launches"] for x in st)
 
     sync_all()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -430,7 +442,7 @@ def main():
             for s, (hs, ht, hn) in zip(sims, init_state):
                 # the loaded state (time 0) replaces the handle's state and its time
                 ac.ac_load_state(s.handle, hs.numpy(), ht.numpy(), hn.numpy().view(np.uint32), 0)
-            if kern == ac.AC_KERNEL_BLOCKED:
+            if batched:
                 ac.ac_batch_run_until(handles, t_end)
             else:
                 for s in sims:
