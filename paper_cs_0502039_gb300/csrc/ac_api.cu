@@ -614,7 +614,9 @@ ac_status batch_run_tb(int32_t n, ac_sim* const* sims, const int64_t* t_end, Bat
     range[2 * i + 1] = 0u;
   }
   AC_CUDA(cudaMemcpyAsync(R->d_range, range.data(), range.size() * 4, cudaMemcpyHostToDevice, stream));
-  AC_CUDA(ac::launch_count_range_batch(R->d_desc, n, R->d_range, stream));
+  size_t max_cells = 0;
+  for (int i = 0; i < n; ++i) max_cells = std::max(max_cells, sims[i]->ncells());
+  AC_CUDA(ac::launch_count_range_batch(R->d_desc, n, max_cells, R->d_range, stream));
   AC_CUDA(cudaMemcpyAsync(range.data(), R->d_range, range.size() * 4, cudaMemcpyDeviceToHost, stream));
   std::vector<unsigned long long> before(n), after(n);
   for (int i = 0; i < n; ++i)

@@ -127,7 +127,8 @@ cudaError_t launch_tb(const LatDesc* d_desc, int nlat, int total_tiles, int regi
 // Frames [K, K + count) were just opened: write each cell's spin into those whose tick
 // lies before the cell's next arrival (later commits write the others).
 cudaError_t launch_frames_fill(const LatDesc* host_desc, long long K, int count, cudaStream_t s);
-cudaError_t launch_count_range_batch(const LatDesc* d_desc, int nlat, unsigned* d_out2n, cudaStream_t s);
+cudaError_t launch_count_range_batch(const LatDesc* d_desc, int nlat, size_t max_cells, unsigned* d_out2n,
+                                     cudaStream_t s);
 int tb_grid(int region);   // resident CTAs of the temporal-blocked kernel
 cudaError_t launch_validate(const int8_t* s_in, const long long* t_in, size_t N, long long tmin, long long tmax,
                             unsigned long long* d_first_bad, cudaStream_t st);

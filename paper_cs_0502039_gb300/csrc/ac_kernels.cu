@@ -1426,9 +1426,12 @@ cudaError_t launch_count_range(const LatDesc* h, unsigned* d_out2, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_count_range_batch(const LatDesc* d, int nlat, unsigned* d_out2n, cudaStream_t st) {
+cudaError_t launch_count_range_batch(const LatDesc* d, int nlat, size_t max_cells, unsigned* d_out2n,
+                                     cudaStream_t st) {
   if (nlat <= 0) return cudaSuccess;
-  count_range_batch_kernel<<<dim3(8, (unsigned)nlat), 256, 0, st>>>(d, d_out2n);
+  // about 32 cells per thread for the largest lattice
+  const size_t bx = std::min<size_t>(1024, std::max<size_t>(1, (max_cells + 256 * 32 - 1) / (256 * 32)));
+  count_range_batch_kernel<<<dim3((unsigned)bx, (unsigned)nlat), 256, 0, st>>>(d, d_out2n);
   return cudaGetLastError();
 }
 
