@@ -204,6 +204,16 @@ ac_status ac_stats(const ac_sim* sim, ac_stats_t* out);
 ac_status ac_round_history(const ac_sim* sim, uint64_t* counts, int32_t cap, int32_t* n_rounds);
 
 /*
+ * BKL classes (Sec. 3, "The BKL algorithm"): the flip probability of a cell
+ * depends only on its spin s and its number j of up neighbours, so the cells fall
+ * into 10 classes; counts[j + 5 (s > 0)] receives the number of cells in each
+ * (the index of the threshold table, so sum_k counts[k] * thr[k] / 2^32 is the
+ * expected number of flips per unit time).  The 4-neighbour Ising array only.
+ * Errors: AC_ERR_ARG, AC_ERR_CUDA.
+ */
+ac_status ac_class_counts(const ac_sim* sim, uint64_t counts[10]);
+
+/*
  * Return the handle to time 0 with a new seed and initial condition, reusing its
  * device memory (the same initial state as ac_create; counters and statistics of
  * the trajectory restart).  No allocation.  Errors: AC_ERR_ARG, AC_ERR_CUDA.

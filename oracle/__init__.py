@@ -98,6 +98,8 @@ def _bind(lib):
     lib.aco_exp_ticks_many.restype = None
     lib.aco_philox_blocks.argtypes = [ctypes.c_uint64, P, P, ctypes.c_uint32, P, ctypes.c_int64]
     lib.aco_philox_blocks.restype = None
+    lib.aco_class_counts.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P]
+    lib.aco_class_counts.restype = None
     lib.aco_thresholds_q.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, P]
     lib.aco_thresholds_q.restype = None
     lib.aco_run_q.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_uint64, P, P, P,
@@ -339,6 +341,13 @@ def time_model(dims: int, n: int, law: int, seed: int, t_end: int, max_rounds: i
     if r < 0:
         raise ValueError("dims must be 1..3, n >= 2, law 0..2, q in 1..8 with n >= 2q+1")
     return en[:r].copy(), t, cnt
+
+
+def class_counts(state: State) -> np.ndarray:
+    """Cells per BKL class (Sec. 3): index j + 5 (s > 0), j = up neighbours, as in the table."""
+    out = np.zeros(10, dtype=np.int64)
+    _load().aco_class_counts(state.rows, state.cols, _ptr(state.s), _ptr(out))
+    return out
 
 
 def observables(state: State):

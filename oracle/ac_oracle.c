@@ -592,6 +592,23 @@ void aco_observables(int32_t rows, int32_t cols, const int8_t *s, int64_t out[2]
     out[1] = b;
 }
 
+/* BKL classes (Sec. 3, "The BKL algorithm"): the heat-bath flip probability of */
+/* a cell depends only on its spin and its number j of up neighbours, so the     */
+/* cells fall into 10 classes, index j + 5 (s > 0) as in the threshold table.   */
+/* out[k] = number of cells in class k.                                         */
+void aco_class_counts(int32_t rows, int32_t cols, const int8_t *s, int64_t out[10])
+{
+    for (int k = 0; k < 10; ++k) out[k] = 0;
+    uint64_t N = (uint64_t)rows * (uint64_t)cols;
+    for (uint64_t c = 0; c < N; ++c) {
+        uint64_t nb[4];
+        neighbours(rows, cols, c, nb);
+        int up = 0;
+        for (int d = 0; d < 4; ++d) up += (s[nb[d]] > 0);
+        out[up + 5 * (s[c] > 0)] += 1;
+    }
+}
+
 /* SplitMix64 finaliser (Steele, Lea, Flood, OOPSLA'14) used as a mixer. */
 static uint64_t mix64(uint64_t z)
 {

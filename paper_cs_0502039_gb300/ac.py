@@ -55,7 +55,7 @@ EXPORTS = ["ac_create", "ac_set_stream", "ac_configure", "ac_run_until", "ac_run
            "ac_destroy", "ac_last_error", "ac_thresholds", "ac_reset", "ac_set_option", "ac_batch_create", "ac_batch_run_until",
            "ac_dev_exp_ticks", "ac_dev_philox", "ac_run_blocked_static", "ac_frames_configure",
            "ac_run_until_frames", "ac_frames_status", "ac_time_model", "ac_create_life", "ac_set_rates",
-           "ac_create_q"]
+           "ac_create_q", "ac_class_counts"]
 
 AC_RATE_ONE = 1 << 20
 
@@ -99,6 +99,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ac_run_until_frames": ([P, I64, FRAME_FN, P, I32], I32),
         "ac_frames_status": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)], I32),
         "ac_set_rates": ([P, P], I32),
+        "ac_class_counts": ([P, P], I32),
         "ac_create_q": ([ac_lattice, D, D, D, I32, U64, ctypes.POINTER(P)], I32),
         "ac_create_life": ([ac_lattice, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, U64,
                             ctypes.POINTER(P)], I32),
@@ -144,6 +145,13 @@ def ac_create_q(rows: int, cols: int, init: int, beta: float, J: float, h: float
     out = ctypes.c_void_p()
     _check(_lib.ac_create_q(ac_lattice(rows, cols, init), beta, J, h, int(q), seed & (2**64 - 1), ctypes.byref(out)))
     return out.value
+
+
+def ac_class_counts(sim: int) -> np.ndarray:
+    """Cells per BKL class, index j + 5 (s > 0) (j up neighbours)."""
+    out = np.zeros(10, dtype=np.uint64)
+    _check(_lib.ac_class_counts(sim, _np_ptr(out, np.uint64)))
+    return out
 
 
 def ac_set_rates(sim: int, m) -> None:
@@ -366,6 +374,9 @@ class Sim:
     def reset(self, seed: int, init: int = AC_INIT_RANDOM) -> None:
         ac_reset(self.handle, seed, init)
         self.seed = int(seed)
+
+    def class_counts(self) -> np.ndarray:
+        return ac_class_counts(self.handle)
 
     def set_rates(self, m) -> None:
         """Per-cell rates 2^20 / m[c] (None: all 1); re-initialises the handle at time 0."""

@@ -298,7 +298,7 @@ ac_status create_one(ac_lattice lat, double beta, double J, double h, uint64_t s
   if (cudaMalloc(&s->key, N * 8) != cudaSuccess || cudaMalloc(&s->cnt, N * 4) != cudaSuccess ||
       cudaMalloc(&s->d_events, 8) != cudaSuccess || cudaMalloc(&s->d_desc, sizeof(ac::LatDesc)) != cudaSuccess ||
       cudaMalloc(&s->d_ctr, sizeof(ac::DevCounters)) != cudaSuccess ||
-      cudaMalloc(&s->d_red, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMalloc(&s->d_red, 16 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     free_sim(s);
     return fail(AC_ERR_OOM, "cudaMalloc of the lattice state (%zu cells) failed", N);
@@ -1201,6 +1201,17 @@ ac_status ac_round_history(const ac_sim* sim, uint64_t* counts, int32_t cap, int
     AC_CUDA(cudaMemcpyAsync(counts, sim->d_hist, (size_t)m * 8, cudaMemcpyDeviceToHost, sim->stream));
     AC_CUDA(cudaStreamSynchronize(sim->stream));
   }
+  return AC_OK;
+}
+
+ac_status ac_class_counts(const ac_sim* sim, uint64_t counts[10]) {
+  if (!sim || !counts) return fail(AC_ERR_ARG, "sim and counts are required");
+  if (sim->model != 0) return fail(AC_ERR_ARG, "classes are defined for the 4-neighbour Ising array");
+  const ac::LatDesc d = sim->host_desc(sim->t_done, 0);
+  AC_CUDA(cudaMemsetAsync(sim->d_red, 0, 10 * sizeof(unsigned long long), sim->stream));
+  AC_CUDA(ac::launch_class_counts(&d, sim->d_red, sim->stream));
+  AC_CUDA(cudaMemcpyAsync(counts, sim->d_red, 10 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, sim->stream));
+  AC_CUDA(cudaStreamSynchronize(sim->stream));
   return AC_OK;
 }
 

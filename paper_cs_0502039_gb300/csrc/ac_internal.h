@@ -111,6 +111,7 @@ cudaError_t launch_blocked(const LatDesc* d_desc, int nlat, int total_tiles, con
                            int grid, unsigned int* tile_done, DevCounters* ctr, cudaStream_t s);
 cudaError_t launch_reduce(const LatDesc* host_desc, unsigned long long* d_out4, cudaStream_t s);
 cudaError_t launch_count_range(const LatDesc* host_desc, unsigned* d_out2, cudaStream_t s);
+cudaError_t launch_class_counts(const LatDesc* host_desc, unsigned long long* d_out10, cudaStream_t s);
 cudaError_t launch_unpack(const LatDesc* host_desc, int8_t* s_out, long long* t_out,
                           unsigned int* n_out, cudaStream_t st);
 cudaError_t launch_pack(const LatDesc* host_desc, const int8_t* s_in, const long long* t_in,

@@ -1206,6 +1206,25 @@ __global__ void reduce_kernel(LatDesc L, unsigned long long* out) {
 }
 
 // out[0] = min count, out[1] = max count (out initialised to {~0, 0} by the caller)
+// BKL classes (Sec. 3): cells counted by spin and number j of up neighbours, index
+// j + 5 (s > 0) as in the threshold table; block counters in shared memory.
+__global__ void class_count_kernel(LatDesc L, unsigned long long* out) {
+  __shared__ unsigned long long sc[10];
+  if (threadIdx.x < 10) sc[threadIdx.x] = 0ull;
+  __syncthreads();
+  const size_t N = (size_t)L.rows * L.cols;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = c / L.cols, q = c - r * L.cols;
+    const size_t up = (r == 0 ? L.rows - 1 : r - 1) * L.cols + q, dn = (r + 1 == (size_t)L.rows ? 0 : r + 1) * L.cols + q;
+    const size_t lf = r * L.cols + (q == 0 ? L.cols - 1 : q - 1), rt = r * L.cols + (q + 1 == (size_t)L.cols ? 0 : q + 1);
+    const unsigned j = (unsigned)(L.key[up] & 1ull) + (unsigned)(L.key[dn] & 1ull) + (unsigned)(L.key[lf] & 1ull) +
+                       (unsigned)(L.key[rt] & 1ull);
+    atomicAdd(&sc[j + 5u * (unsigned)(L.key[c] & 1ull)], 1ull);
+  }
+  __syncthreads();
+  if (threadIdx.x < 10 && sc[threadIdx.x]) atomicAdd(&out[threadIdx.x], sc[threadIdx.x]);
+}
+
 __global__ void count_range_kernel(LatDesc L, unsigned* out) {
   const size_t N = (size_t)L.rows * L.cols;
   unsigned mn = 0xFFFFFFFFu, mx = 0u;
@@ -1423,6 +1442,12 @@ cudaError_t launch_reduce(const LatDesc* h, unsigned long long* d_out4, cudaStre
 cudaError_t launch_count_range(const LatDesc* h, unsigned* d_out2, cudaStream_t st) {
   const size_t N = (size_t)h->rows * h->cols;
   count_range_kernel<<<grid_for(N, 256), 256, 0, st>>>(*h, d_out2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_class_counts(const LatDesc* h, unsigned long long* d_out10, cudaStream_t st) {
+  const size_t N = (size_t)h->rows * h->cols;
+  class_count_kernel<<<grid_for(N, 256), 256, 0, st>>>(*h, d_out10);
   return cudaGetLastError();
 }
 

@@ -161,3 +161,14 @@ def test_temporal_blocking_with_uneven_loaded_counts():
         sim.run_until(4)
         s, t, n = sim.read_state()
     assert_same(ref, s, t, n, "uneven counts")
+
+
+def test_bkl_class_counts():
+    """Cells per BKL class (spin, up neighbours) equal the oracle's count of its own state."""
+    for rows, cols, seed, T, kernel, rounds in [(2, 3, 1, 4, ROUND, 1), (64, 64, 1, 10, ROUND, 6),
+                                                (100, 130, 6, 3, BLOCKED, 1)]:
+        ref = oracle_state(rows, cols, 0.44, 1.0, 0.0, seed, T)
+        with ac.Sim(rows, cols, 0.44, 1.0, 0.0, seed, kernel=kernel, Lb=32, rounds=rounds) as sim:
+            sim.run_until(T)
+            got = sim.class_counts()
+        assert np.array_equal(got.astype(np.int64), oracle.class_counts(ref)) and got.sum() == rows * cols

@@ -60,3 +60,20 @@ def test_saturation():
     thr = oracle.thresholds(50.0, 1.0, 0.0)
     assert thr[0] == 0 and thr[9] == 0          # strongly uphill: never flips
     assert thr[4] == 2**32 - 1 and thr[5] == 2**32 - 1   # downhill: always (but u = 2^32-1)
+
+
+def test_class_counts_by_brute_force():
+    """BKL classes (Sec. 3): cells counted by (spin, up neighbours), index j + 5 (s > 0)."""
+    import oracle as _o
+    for rows, cols, seed, T in [(2, 2, 1, 0), (3, 5, 2, 3), (16, 12, 3, 5)]:
+        st = _o.init(rows, cols, 0, seed)
+        if T:
+            _o.run(st, _o.thresholds(0.44), seed, T << 32)
+        want = np.zeros(10, dtype=np.int64)
+        for c in range(rows * cols):
+            r, q = divmod(c, cols)
+            nb = [((r - 1) % rows) * cols + q, ((r + 1) % rows) * cols + q,
+                  r * cols + (q - 1) % cols, r * cols + (q + 1) % cols]
+            j = sum(1 for d in nb if st.s[d] > 0)
+            want[j + 5 * (1 if st.s[c] > 0 else 0)] += 1
+        assert np.array_equal(_o.class_counts(st), want)
