@@ -88,3 +88,34 @@ def test_rate_argument_checks():
     with ac.life(16, 16, 1) as lf:
         with pytest.raises(ac.ACError):
             lf.set_rates(np.full(256, ONE, dtype=np.uint32))
+
+
+def test_rates_with_frames_and_resume():
+    """Per-cell rates with snapshot frames, and a checkpoint reloaded mid-run."""
+    rows, cols, seed, beta, T = 96, 80, 8, 0.44, 4
+    m = _rates(rows * cols, 31)
+    dt = T32 // 2
+    st = oracle.init_rated(rows, cols, 0, seed, m)
+    thr = oracle.thresholds(beta)
+    ref_frames = []
+    for K in range(2 * T):
+        oracle.run_rated(st, thr, seed, m, K * dt + 1)
+        ref_frames.append(st.s.copy())
+    oracle.run_rated(st, thr, seed, m, T * T32)
+    with ac.Sim(rows, cols, beta, 1.0, 0.0, seed, kernel=ROUND, Lb=64, rounds=4) as sim:
+        sim.set_rates(m)
+        sim.configure_frames(dt, 0, 2)
+        got = sim.run_until_frames(T * T32)
+        s, t, n = sim.read_state()
+    assert [k for k, _ in got] == list(range(2 * T))
+    assert all(np.array_equal(f, ref_frames[k]) for k, f in got)
+    assert_same(st, s, t, n, "rates with frames")
+    # checkpoint at T = 2, reload into a fresh handle with the same rates, continue to T
+    mid = oracle.init_rated(rows, cols, 0, seed, m)
+    oracle.run_rated(mid, thr, seed, m, 2 * T32)
+    with ac.Sim(rows, cols, beta, 1.0, 0.0, seed, kernel=BLOCKED, Lb=32, polls=8) as sim:
+        sim.set_rates(m)
+        sim.load_state(mid.s, mid.t, mid.n, 2 * T32)
+        sim.run_until(T)
+        s, t, n = sim.read_state()
+    assert_same(st, s, t, n, "rates after a reload")
