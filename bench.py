@@ -35,6 +35,7 @@ BYTES_PER_EVENT = 26          # read + write of a cell's 13-byte state (int8 spi
 WORKLOAD = dict(name="ising4096x4096_T50", rows=4096, cols=4096, betas=[0.30, 0.4407, 0.60], J=1.0, h=0.0,
                 seed=7, init=0, T=50)
 CPU_SAMPLE_T = 0.5            # oracle sample: time prefix [0, 0.5) of the beta = 0.4407 lattice
+ISSUE_PER_SM_CLK = 4          # one warp instruction per clock from each of an SM's four schedulers
 
 
 def parse():
@@ -138,8 +139,8 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def committed_traffic(kernel_name):
-    """DRAM bytes per step from the committed ncu summary, if it matches this kernel source."""
+def committed_profile(kernel_name, key):
+    """A per-step figure from the committed ncu summary, if it was taken on this kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -149,7 +150,12 @@ def committed_traffic(kernel_name):
     ent = rec.get(kernel_name)
     if not ent or ent.get("source_sha256") != kernel_source_hash():
         return None
-    return ent.get("dram_bytes_per_step")
+    return ent.get(key)
+
+
+def committed_traffic(kernel_name):
+    """DRAM bytes per step (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    return committed_profile(kernel_name, "dram_bytes_per_step")
 
 
 def measured_peaks():
@@ -419,6 +425,19 @@ def main():
                 "traffic": committed_traffic(kname), "peak_source": peak_src,
                 "kernel": kname, "bytes_per_event": BYTES_PER_EVENT,
                 "events_per_launch": ev_per_step_rank, "launch_ms": kern_launch_ms}
+    # the kernel is bound by integer issue, not by DRAM: executed warp instructions per step (ncu
+    # sm__inst_executed.sum on this source) over the live kernel time, against every scheduler
+    # issuing one warp instruction per clock at the maximum SM clock
+    inst = committed_profile(kname, "warp_inst_per_step")
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_max = clk.summary()["sm_max_mhz"] or 2070.0
+    issue_peak = ISSUE_PER_SM_CLK * n_sm * clk_max * 1e6 / 1e9
+    issue = {"bound": "alu", "unit": "Gwarp-inst/s", "peak": issue_peak, "achieved": None, "frac": None,
+             "peak_source": f"{ISSUE_PER_SM_CLK} x {n_sm} SMs x {clk_max:.0f} MHz",
+             "warp_inst_per_event": None if inst is None else inst / ev_per_step_rank}
+    if inst is not None:
+        issue["achieved"] = inst / (kern_launch_ms / 1000.0) / 1e9
+        issue["frac"] = issue["achieved"] / issue_peak
 
     # end-to-end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -493,7 +512,7 @@ def main():
                           "events_per_step": ev_all / args.steps,
                           "l2": "state 3 x 201 MB > 129 MB L2 (no flush)",
                           "parallelism": f"replicas x{world}"},
-               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "roofline": roofline, "roofline_issue": issue, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(),
                "kernel_stats": {k: stats0[k] for k in ("visits", "polls", "rounds", "scanned", "enabled",
                                                        "grid", "ctas_per_sm")},
