@@ -659,10 +659,44 @@ struct TbCfg {
   static constexpr size_t lBytes = size_t(LIST) * 2;
   static constexpr size_t gBytes = size_t(RW) * 4 * 2;
   static constexpr size_t mBytes = (4 + kThrMax) * 4;   // n_en[2], overflow flag, thresholds
+  // order planes of the 4-neighbour array: 32 cells per word, one word row per region row
+  static constexpr int W = RW / 32;
+  static constexpr size_t pOff = kBytes + cBytes + lBytes + gBytes + mBytes;
+  static constexpr size_t pBytes = size_t(3) * RW * W * 4;
   static constexpr size_t fBytes = 64;            // snapshot-frame view (frame variant), 16-byte aligned
-  static constexpr size_t fOff = (kBytes + cBytes + lBytes + gBytes + mBytes + 15) / 16 * 16;
+  static constexpr size_t fOff = (pOff + pBytes + 15) / 16 * 16;
   static constexpr size_t bytes = fOff + fBytes;
+  static_assert(RW % 32 == 0 && pOff % 4 == 0, "order-plane layout");
 };
+
+// Order planes of the 4-neighbour array (one bit per lattice edge, packed 32 cells to a
+// word): H bit (i, j) says cell (i, j) precedes its right neighbour in (tick, index)
+// order, V bit (i, j) that it precedes the cell below, LV bit (i, j) that its tick is
+// below the commit bound.  Cell (i, j) is enabled (Fig. 3.2) iff H(i, j), V(i, j),
+// LV(i, j) are set and H(i, j-1), V(i-1, j) are clear, so a round's enable test is a
+// few word operations per 32 cells.  An edge's bit changes only when one of its two
+// cells commits, and the cells committed in one round are pairwise non-adjacent, so
+// every bit has at most one writer per round.  A committed cell's old bits are known
+// (it was enabled), so it updates them with xor masks.
+__device__ __forceinline__ void order_update(unsigned* H, unsigned* V, unsigned* LV, int W, int r, int c,
+                                             unsigned long long nk, unsigned long long kl, unsigned long long kr,
+                                             unsigned long long ku, unsigned long long kd, unsigned long long t2) {
+  const unsigned long long lo = nk & ~1ull;
+  const unsigned bit = 1u << (c & 31);
+  const int wc = r * W + (c >> 5);
+  const unsigned hc = (lo <= kr) ? 0u : bit;           // no longer before the right neighbour
+  const bool hl = (kl & ~1ull) <= nk;                  // the left neighbour now precedes it
+  if (c & 31) {
+    const unsigned m = hc | (hl ? (bit >> 1) : 0u);
+    if (m) atomicXor(&H[wc], m);
+  } else {                                             // the left edge's bit is in the previous word
+    if (hc) atomicXor(&H[wc], hc);
+    if (hl) atomicXor(&H[wc - 1], 0x80000000u);
+  }
+  if (!(lo <= kd)) atomicXor(&V[wc], bit);
+  if ((ku & ~1ull) <= nk) atomicXor(&V[wc - W], bit);
+  if (nk >= t2) atomicAnd(&LV[wc], ~bit);
+}
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -842,6 +876,9 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   unsigned int* n_en = misc;          // [2]
   unsigned int* s_over = misc + 2;    // count window overflow in this region
   unsigned int* thr = misc + 4;       // [kThrMax]
+  unsigned int* OH = reinterpret_cast<unsigned int*>(smem_raw + Cfg::pOff);   // order planes
+  unsigned int* OV = OH + RW * Cfg::W;
+  unsigned int* OL = OV + RW * Cfg::W;
   FrameView* fv = reinterpret_cast<FrameView*>(smem_raw + Cfg::fOff);
   static_assert(sizeof(FrameView) <= Cfg::fBytes, "frame view does not fit");
 
@@ -956,10 +993,44 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     const uint32_t two = L.two, seed_lo = L.seed_lo, seed_hi = L.seed_hi;
     const unsigned* __restrict__ rates = L.rates;
     constexpr unsigned kEven = 0x55555555u, kOdd = 0xAAAAAAAAu;
+    constexpr int W = Cfg::W;
+    if (MODEL == 0) {
+      // order planes of the loaded region; a warp covers 32 consecutive columns of one
+      // row.  Relations with cells outside the loaded rectangle are never read.
+      for (int i = li0; i < RW; i += Cfg::LSTRIDE) {
+        const unsigned long long kc = K[i * RW + lj];
+        const unsigned long long kr = K[i * RW + lj + 1];
+        const unsigned long long kd = K[(i + 1) * RW + lj];
+        const unsigned hb = __ballot_sync(kFull, (kc & ~1ull) <= kr);
+        const unsigned vb = __ballot_sync(kFull, (kc & ~1ull) <= kd);
+        const unsigned lb = __ballot_sync(kFull, kc < t2);
+        if (lane == 0) {
+          OH[i * W + (lj >> 5)] = hb;
+          OV[i * W + (lj >> 5)] = vb;
+          OL[i * W + (lj >> 5)] = lb;
+        }
+      }
+      __syncthreads();
+    }
     int cur = 0;
     const int qn = (MODEL == 2) ? L.q : 1;     // rings lost per round
     for (int k = 1; k <= R; ++k) {
       const int kk = k * qn;
+      unsigned mask = 0;
+      // the word scanned by this thread (4-neighbour array): row oi, columns 32 ow ...
+      const int oi = tid / W, ow = tid % W;
+      if (MODEL == 0) {
+        if (oi < RW && oi >= kk && oi < RH - kk) {
+          const int lo = max(kk - 32 * ow, 0), hi = min(RC - kk - 32 * ow, 32);
+          if (hi > lo) {
+            const unsigned cm = (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+            const unsigned h = OH[oi * W + ow];
+            const unsigned hl = (h << 1) | (ow > 0 ? (OH[oi * W + ow - 1] >> 31) : 0u);
+            mask = h & ~hl & OV[oi * W + ow] & ~OV[(oi - 1) * W + ow] & OL[oi * W + ow] & cm;
+            scanned += (unsigned long long)__popc(cm);
+          }
+        }
+      }
       const unsigned colm = ((pc >= kk && pc < RC - kk) ? kEven : 0u) | ((pc + 1 >= kk && pc + 1 < RC - kk) ? kOdd : 0u);
       const int rlo = max(kk - rbase, 0), rhi = min(RH - kk - rbase, Cfg::ROWS);
       unsigned rowm = 0u;
@@ -967,8 +1038,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const unsigned hi_bits = (2 * rhi >= 32) ? 0xFFFFFFFFu : ((1u << (2 * rhi)) - 1u);
         rowm = hi_bits & ~((1u << (2 * rlo)) - 1u);
       }
-      const unsigned valid = colm & rowm;
-      unsigned mask = 0;
+      const unsigned valid = MODEL == 0 ? 0u : colm & rowm;
       if (MODEL == 1 && valid) {
         mask = edge ? life_scan_exact<RW, Cfg::ROWS>(K, rowoff, colg, rbase, pc, t2)
                     : life_scan<RW, Cfg::ROWS>(K, rbase, pc, t2);
@@ -976,27 +1046,6 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         scanned += (unsigned long long)__popc(valid);
       } else if (MODEL == 2 && valid) {
         mask = q_scan_exact<RW, Cfg::ROWS>(K, rowoff, colg, rbase, pc, t2, qn) & valid;
-        scanned += (unsigned long long)__popc(valid);
-      } else if (valid) {
-        const unsigned long long* q = K + rbase * RW + pc;
-        ulonglong2 cv = *reinterpret_cast<const ulonglong2*>(q);
-        const ulonglong2 uv = *reinterpret_cast<const ulonglong2*>(q - RW);
-        bool upa = (cv.x | 1ull) < uv.x, upb = (cv.y | 1ull) < uv.y;
-#pragma unroll
-        for (int i = 0; i < Cfg::ROWS; ++i) {
-          const ulonglong2 dv = *reinterpret_cast<const ulonglong2*>(q + (i + 1) * RW);
-          const unsigned long long left = q[i * RW - 1], right = q[i * RW + 2];
-          const unsigned long long loa = cv.x & ~1ull, lob = cv.y & ~1ull;
-          const bool da = loa <= dv.x, db = lob <= dv.y;
-          const bool ab = loa <= cv.y;   // a before b; its complement is "b before a"
-          const bool ea = (cv.x < t2) & upa & da & ((cv.x | 1ull) < left) & ab;
-          const bool eb = (cv.y < t2) & upb & db & !ab & (lob <= right);
-          mask |= ((unsigned)ea << (2 * i)) | ((unsigned)eb << (2 * i + 1));
-          upa = !da;
-          upb = !db;
-          cv = dv;
-        }
-        mask &= valid;
         scanned += (unsigned long long)__popc(valid);
       }
       // exclusive prefix of the per-lane counts (< 32) from five independent ballots
@@ -1016,7 +1065,9 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       while (mask) {
         const int b = __ffs(mask) - 1;
         mask &= mask - 1;
-        if (off < Cfg::LIST) list[off] = (unsigned short)(((rbase + (b >> 1)) << 8) | (pc + (b & 1)));
+        if (off < Cfg::LIST)
+          list[off] = MODEL == 0 ? (unsigned short)((oi << 8) | (32 * ow + b))
+                                 : (unsigned short)(((rbase + (b >> 1)) << 8) | (pc + (b & 1)));
         ++off;
       }
       __syncthreads();
@@ -1044,12 +1095,10 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
           tha = thr[q_up<RW>(kpa, qn) + M1 * spa];
           thb = thr[q_up<RW>(kpb, qn) + M1 * spb];
         } else {
-          const unsigned ja = ((unsigned)kpa[-RW] & 1u) + ((unsigned)kpa[RW] & 1u) + ((unsigned)kpa[-1] & 1u) +
-                              ((unsigned)kpa[1] & 1u);
-          const unsigned jb = ((unsigned)kpb[-RW] & 1u) + ((unsigned)kpb[RW] & 1u) + ((unsigned)kpb[-1] & 1u) +
-                              ((unsigned)kpb[1] & 1u);
-          tha = thr[ja + 5u * spa];
-          thb = thr[jb + 5u * spb];
+          tha = thr[((unsigned)kpa[-RW] & 1u) + ((unsigned)kpa[RW] & 1u) + ((unsigned)kpa[-1] & 1u) +
+                    ((unsigned)kpa[1] & 1u) + 5u * spa];
+          thb = thr[((unsigned)kpb[-RW] & 1u) + ((unsigned)kpb[RW] & 1u) + ((unsigned)kpb[-1] & 1u) +
+                    ((unsigned)kpb[1] & 1u) + 5u * spb];
         }
         const Philox4 pa = philox_event(gia, base + c16a + 1u, 0u, seed_lo, seed_hi);
         const Philox4 pb = philox_event(gib, base + c16b + 1u, 0u, seed_lo, seed_hi);
@@ -1066,6 +1115,10 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         *kpb = nkb;
         C[ra * RW + ca] = (unsigned short)(c16a + 1u);
         C[rb * RW + cb] = (unsigned short)(c16b + 1u);
+        if (MODEL == 0) {
+          order_update(OH, OV, OL, W, ra, ca, nka, kpa[-1], kpa[1], kpa[-RW], kpa[RW], t2);
+          order_update(OH, OV, OL, W, rb, cb, nkb, kpb[-1], kpb[1], kpb[-RW], kpb[RW], t2);
+        }
         if (FR) {   // own cells only: halo commits are repeated by the owning tile
           if (ra >= D && ra < D + g.h && ca >= D && ca < D + g.w)
             write_frames(*fv, gia, keya >> 1, nka >> 1, (unsigned)nka & 1u);
@@ -1098,6 +1151,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const unsigned long long nk = (key & ~1ull) + (gap << 1) + ns;
         *kp = nk;
         C[r * RW + cc] = (unsigned short)(c16 + 1u);
+        if (MODEL == 0) order_update(OH, OV, OL, W, r, cc, nk, kp[-1], kp[1], kp[-RW], kp[RW], t2);
         if (FR && r >= D && r < D + g.h && cc >= D && cc < D + g.w)
           write_frames(*fv, gidx, key >> 1, nk >> 1, (unsigned)nk & 1u);
       }
