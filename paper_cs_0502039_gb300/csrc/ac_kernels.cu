@@ -906,15 +906,17 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
     const LatDesc& L = lats[find_lattice(lats, nlat, tile)];
     const Geom g = tile_geom(L, tile - L.tile_base);
+    // in registers: the copies below are asm statements that clobber memory
+    const int Lrows = L.rows, Lcols = L.cols;
     const unsigned long long* key_in = parity ? L.key2 : L.key;
     const unsigned int* cnt_in = parity ? L.cnt2 : L.cnt;
     unsigned long long* key_out = parity ? L.key : L.key2;
     unsigned int* cnt_out = parity ? L.cnt : L.cnt2;
     const int RH = g.h + 2 * D, RC = g.w + 2 * D;
     // the region wraps across the torus seam (small tiles of interior positions can too)
-    const bool edge = (g.r0 < D) || (g.r0 + g.h + D > L.rows) || (g.c0 < D) || (g.c0 + g.w + D > L.cols);
+    const bool edge = (g.r0 < D) || (g.r0 + g.h + D > Lrows) || (g.c0 < D) || (g.c0 + g.w + D > Lcols);
     // counts are kept as 16-bit offsets from a window start taken at the tile centre
-    const unsigned ccen = __ldg(&cnt_in[(size_t)(g.r0 + g.h / 2) * L.cols + g.c0 + g.w / 2]);
+    const unsigned ccen = __ldg(&cnt_in[(size_t)(g.r0 + g.h / 2) * Lcols + g.c0 + g.w / 2]);
     const unsigned base = ccen > 32768u ? ccen - 32768u : 0u;
     const unsigned cap = 65535u - (unsigned)R;
 
@@ -926,7 +928,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       if (FR) *fv = frame_view(L);
     }
     int shc;
-    const int gc = wrap_index(g.c0 - D + lj, L.cols, shc, 2);
+    const int gc = wrap_index(g.c0 - D + lj, Lcols, shc, 2);
     bool over = false;
     __syncthreads();
     // the thread's own-tile cells' count offsets at load (the write-back uses the same
@@ -937,16 +939,18 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       // all of the thread's global loads are in flight together (one batch)
       constexpr int MROWS = RW / Cfg::LSTRIDE;
       unsigned cvs[MROWS];
+      int shr0;
+      int gr = wrap_index(g.r0 - D + li0, Lrows, shr0, 2);   // the wrapped lattice row, stepped
 #pragma unroll
       for (int m = 0; m < MROWS; ++m) {
         const int i = li0 + Cfg::LSTRIDE * m;
         if (i < RH) {
-          int shr;
-          const int gr = wrap_index(g.r0 - D + i, L.rows, shr, 2);
-          const size_t gi = (size_t)gr * L.cols + gc;
+          const uint32_t gi = (uint32_t)gr * (uint32_t)Lcols + (uint32_t)gc;   // rows * cols < 2^32
           cp_async8(&K[i * RW + lj], &key_in[gi]);
           cvs[m] = cnt_in[gi];
         }
+        gr += Cfg::LSTRIDE;
+        if (gr >= Lrows) gr -= Lrows;
       }
 #pragma unroll
       for (int m = 0; m < MROWS; ++m) {
@@ -961,8 +965,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     }
     if (tid < RW) {
       int sh;
-      rowoff[tid] = (unsigned)wrap_index(min(g.r0 - D + tid, 2 * L.rows - 1), L.rows, sh, 2) * (unsigned)L.cols;
-      colg[tid] = (unsigned)wrap_index(min(g.c0 - D + tid, 2 * L.cols - 1), L.cols, sh, 2);
+      rowoff[tid] = (unsigned)wrap_index(min(g.r0 - D + tid, 2 * Lrows - 1), Lrows, sh, 2) * (unsigned)Lcols;
+      colg[tid] = (unsigned)wrap_index(min(g.c0 - D + tid, 2 * Lcols - 1), Lcols, sh, 2);
     } else if (tid < RW + kThrMax) {
       thr[tid - RW] = L.thr[tid - RW];
     }
@@ -973,7 +977,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       if (lj < RC) {
         for (int i = li0; i < RH; i += Cfg::LSTRIDE) {
           int shr;
-          wrap_index(g.r0 - D + i, L.rows, shr, 2);
+          wrap_index(g.r0 - D + i, Lrows, shr, 2);
           if (shr + shc) K[i * RW + lj] += (unsigned long long)(long long)(shr + shc);
         }
       }
@@ -1173,7 +1177,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         if (ri < D) continue;
         const int i = ri - D;
         const int si = ri * RW + lj;
-        const size_t gi = (size_t)(g.r0 + i) * L.cols + g.c0 + lj - D;
+        const uint32_t gi = (uint32_t)(g.r0 + i) * (uint32_t)Lcols + (uint32_t)(g.c0 + lj - D);
         const unsigned long long kk = K[si];
         const unsigned c16 = C[si];
         own_after += c16;
