@@ -1052,16 +1052,16 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         mask = q_scan_exact<RW, Cfg::ROWS>(K, rowoff, colg, rbase, pc, t2, qn) & valid;
         scanned += (unsigned long long)__popc(valid);
       }
-      // exclusive prefix of the per-lane counts (< 32) from five independent ballots
+      // exclusive prefix of the per-lane counts by an inclusive warp scan
       const int cnt = __popc(mask);
-      const unsigned lt = (1u << lane) - 1u;
-      int excl = 0, total = 0;
+      int incl = cnt;
 #pragma unroll
-      for (int b = 0; b < 5; ++b) {
-        const unsigned bal = __ballot_sync(kFull, (cnt >> b) & 1);
-        excl += __popc(bal & lt) << b;
-        total += __popc(bal) << b;
+      for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += v;
       }
+      const int total = __shfl_sync(kFull, incl, 31);
+      const int excl = incl - cnt;
       int wbase = 0;
       if (lane == 0 && total) wbase = (int)atomicAdd(&n_en[cur], (unsigned)total);
       wbase = __shfl_sync(kFull, wbase, 0);
@@ -1090,6 +1090,19 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const unsigned spa = (unsigned)keya & 1u, spb = (unsigned)keyb & 1u;
         const uint32_t gia = rowoff[ra] + colg[ca], gib = rowoff[rb] + colg[cb];
         const unsigned c16a = C[ra * RW + ca], c16b = C[rb * RW + cb];
+        // the 4-neighbour array's neighbour keys, read once for the heat-bath sum and the
+        // order planes (no commit of this round writes a neighbour of a listed cell)
+        unsigned long long nua = 0, nda = 0, nla = 0, nra = 0, nub = 0, ndb = 0, nlb = 0, nrb = 0;
+        if (MODEL == 0) {
+          nua = kpa[-RW];
+          nda = kpa[RW];
+          nla = kpa[-1];
+          nra = kpa[1];
+          nub = kpb[-RW];
+          ndb = kpb[RW];
+          nlb = kpb[-1];
+          nrb = kpb[1];
+        }
         unsigned tha, thb;
         if (MODEL == 1) {   // rule mask of the current state; the new state is its bit k
           tha = thr[spa];
@@ -1099,10 +1112,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
           tha = thr[q_up<RW>(kpa, qn) + M1 * spa];
           thb = thr[q_up<RW>(kpb, qn) + M1 * spb];
         } else {
-          tha = thr[((unsigned)kpa[-RW] & 1u) + ((unsigned)kpa[RW] & 1u) + ((unsigned)kpa[-1] & 1u) +
-                    ((unsigned)kpa[1] & 1u) + 5u * spa];
-          thb = thr[((unsigned)kpb[-RW] & 1u) + ((unsigned)kpb[RW] & 1u) + ((unsigned)kpb[-1] & 1u) +
-                    ((unsigned)kpb[1] & 1u) + 5u * spb];
+          tha = thr[((unsigned)nua & 1u) + ((unsigned)nda & 1u) + ((unsigned)nla & 1u) + ((unsigned)nra & 1u) + 5u * spa];
+          thb = thr[((unsigned)nub & 1u) + ((unsigned)ndb & 1u) + ((unsigned)nlb & 1u) + ((unsigned)nrb & 1u) + 5u * spb];
         }
         const Philox4 pa = philox_event(gia, base + c16a + 1u, 0u, seed_lo, seed_hi);
         const Philox4 pb = philox_event(gib, base + c16b + 1u, 0u, seed_lo, seed_hi);
@@ -1120,8 +1131,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         C[ra * RW + ca] = (unsigned short)(c16a + 1u);
         C[rb * RW + cb] = (unsigned short)(c16b + 1u);
         if (MODEL == 0) {
-          order_update(OH, OV, OL, W, ra, ca, nka, kpa[-1], kpa[1], kpa[-RW], kpa[RW], t2);
-          order_update(OH, OV, OL, W, rb, cb, nkb, kpb[-1], kpb[1], kpb[-RW], kpb[RW], t2);
+          order_update(OH, OV, OL, W, ra, ca, nka, nla, nra, nua, nda, t2);
+          order_update(OH, OV, OL, W, rb, cb, nkb, nlb, nrb, nub, ndb, t2);
         }
         if (FR) {   // own cells only: halo commits are repeated by the owning tile
           if (ra >= D && ra < D + g.h && ca >= D && ca < D + g.w)
