@@ -913,6 +913,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     unsigned long long* key_out = parity ? L.key : L.key2;
     unsigned int* cnt_out = parity ? L.cnt : L.cnt2;
     const int RH = g.h + 2 * D, RC = g.w + 2 * D;
+    // lattice index of region cell (0, 0) when the region does not wrap (unused otherwise)
+    const uint32_t g00 = (uint32_t)(g.r0 - D) * (uint32_t)Lcols + (uint32_t)(g.c0 - D);
     // the region wraps across the torus seam (small tiles of interior positions can too)
     const bool edge = (g.r0 < D) || (g.r0 + g.h + D > Lrows) || (g.c0 < D) || (g.c0 + g.w + D > Lcols);
     // counts are kept as 16-bit offsets from a window start taken at the tile centre
@@ -1088,7 +1090,14 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         unsigned long long* kpb = K + rb * RW + cb;
         const unsigned long long keya = *kpa, keyb = *kpb;
         const unsigned spa = (unsigned)keya & 1u, spb = (unsigned)keyb & 1u;
-        const uint32_t gia = rowoff[ra] + colg[ca], gib = rowoff[rb] + colg[cb];
+        uint32_t gia, gib;
+        if (edge) {
+          gia = rowoff[ra] + colg[ca];
+          gib = rowoff[rb] + colg[cb];
+        } else {   // the region does not wrap: lattice index from the region's first cell
+          gia = g00 + (uint32_t)(ra * Lcols + ca);
+          gib = g00 + (uint32_t)(rb * Lcols + cb);
+        }
         const unsigned c16a = C[ra * RW + ca], c16b = C[rb * RW + cb];
         // the 4-neighbour array's neighbour keys, read once for the heat-bath sum and the
         // order planes (no commit of this round writes a neighbour of a listed cell)
@@ -1151,14 +1160,18 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const unsigned c16 = C[r * RW + cc];
         const Philox4 b = philox_event(gidx, base + c16 + 1u, 0u, seed_lo, seed_hi);
         unsigned ns;
+        unsigned long long nu = 0, nd = 0, nl = 0, nr = 0;   // neighbour keys, read once
         if (MODEL == 1) {
           ns = (thr[sp] >> moore_live<RW>(kp)) & 1u;
         } else if (MODEL == 2) {
           const unsigned M1 = 2u * qn * (qn + 1) + 1u;
           ns = sp ^ (b.y < thr[q_up<RW>(kp, qn) + M1 * sp] ? 1u : 0u);
         } else {
-          const unsigned j = ((unsigned)kp[-RW] & 1u) + ((unsigned)kp[RW] & 1u) + ((unsigned)kp[-1] & 1u) +
-                             ((unsigned)kp[1] & 1u);
+          nu = kp[-RW];
+          nd = kp[RW];
+          nl = kp[-1];
+          nr = kp[1];
+          const unsigned j = ((unsigned)nu & 1u) + ((unsigned)nd & 1u) + ((unsigned)nl & 1u) + ((unsigned)nr & 1u);
           ns = sp ^ (b.y < thr[j + 5u * sp] ? 1u : 0u);
         }
         unsigned long long gap = exp_ticks(b.x, two);
@@ -1166,7 +1179,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const unsigned long long nk = (key & ~1ull) + (gap << 1) + ns;
         *kp = nk;
         C[r * RW + cc] = (unsigned short)(c16 + 1u);
-        if (MODEL == 0) order_update(OH, OV, OL, W, r, cc, nk, kp[-1], kp[1], kp[-RW], kp[RW], t2);
+        if (MODEL == 0) order_update(OH, OV, OL, W, r, cc, nk, nl, nr, nu, nd, t2);
         if (FR && r >= D && r < D + g.h && cc >= D && cc < D + g.w)
           write_frames(*fv, gidx, key >> 1, nk >> 1, (unsigned)nk & 1u);
       }
