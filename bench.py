@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -131,11 +132,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _code_only(text):
+    """Source text without comments, trailing blanks and empty lines: an edit that only
+    changes comments leaves the compiled kernels, and so the committed profile, valid."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("ac_kernels.cu", "ac_device.cuh"):
-        with open(os.path.join(ROOT, "paper_cs_0502039_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_cs_0502039_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()
 
 

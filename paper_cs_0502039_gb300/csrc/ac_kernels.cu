@@ -639,11 +639,13 @@ __global__ void __launch_bounds__(4 * LB) blocked_kernel(const LatDesc* __restri
 // side are unchanged, and between the sides they give the (tick, index) order of
 // the seam (the Life variant compares lattice indices there instead).  Counts are
 // held as 16-bit offsets from the tile centre's count.  Requires rows, cols >= 4D
-// (the region never overlaps itself).
+// (the region never overlaps itself).  The 4-neighbour array tests enablement on
+// order planes (one bit per lattice edge, see order_update); the Life and q-th degree
+// variants scan the keys of their wider neighbourhoods directly.
 template <int RW>
 struct TbCfg {
-  static constexpr int PAIRS = RW / 2;            // a thread scans a column pair ...
-  static constexpr int GROUPS = 8;                // ... in one of 8 row bands
+  static constexpr int PAIRS = RW / 2;            // dense scans (Life, q-neighbourhood): a thread
+  static constexpr int GROUPS = 8;                // scans a column pair in one of 8 row bands
   static constexpr int ROWS = RW / GROUPS;        // rows per band (12 or 16)
   static constexpr int NT = PAIRS * GROUPS;       // 384 or 512 threads = 4 * RW
   static constexpr int LSTRIDE = NT / RW;         // load / store mapping: rows per column sweep
