@@ -37,10 +37,11 @@ CASES = [
     (64, 520, 0.9, 1.0, -0.05, 12, 3, 1),
 ]
 
-# rounds > 1 selects the temporal-blocked round kernel where rows, cols >= 4 * rounds
+# rounds > 1 selects the temporal-blocked round kernel where rows, cols >= 4 * rounds; 12 is the
+# deepest halo of the 96-wide region, 13 the shallowest of the 128-wide one
 CONFIGS = [
     (ROUND, 32, 1, 0), (ROUND, 64, 1, 0), (ROUND, 32, 5, 0), (ROUND, 128, 3, 0), (ROUND, 64, 2, 0),
-    (ROUND, 64, 8, 0), (ROUND, 64, 16, 0),
+    (ROUND, 64, 8, 0), (ROUND, 64, 12, 0), (ROUND, 64, 13, 0), (ROUND, 64, 16, 0),
     (BLOCKED, 32, 1, 8), (BLOCKED, 64, 1, 8), (BLOCKED, 128, 1, 8), (BLOCKED, 32, 4, 0),
 ]
 
