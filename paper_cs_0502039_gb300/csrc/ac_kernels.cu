@@ -639,13 +639,13 @@ __global__ void __launch_bounds__(4 * LB) blocked_kernel(const LatDesc* __restri
 // side are unchanged, and between the sides they give the (tick, index) order of
 // the seam (the Life variant compares lattice indices there instead).  Counts are
 // held as 16-bit offsets from the tile centre's count.  Requires rows, cols >= 4D
-// (the region never overlaps itself).  The 4-neighbour array tests enablement on
-// order planes (one bit per lattice edge, see order_update); the Life and q-th degree
-// variants scan the keys of their wider neighbourhoods directly.
+// (the region never overlaps itself).  The 4-neighbour array and the Life automaton
+// test enablement on order planes (one bit per lattice edge, see order_update and
+// moore_order_update); the q-th degree variant scans the keys of its diamond directly.
 template <int RW>
 struct TbCfg {
-  static constexpr int PAIRS = RW / 2;            // dense scans (Life, q-neighbourhood): a thread
-  static constexpr int GROUPS = 8;                // scans a column pair in one of 8 row bands
+  static constexpr int PAIRS = RW / 2;            // dense scan (q-neighbourhood): a thread scans
+  static constexpr int GROUPS = 8;                // a column pair in one of 8 row bands
   static constexpr int ROWS = RW / GROUPS;        // rows per band (12 or 16)
   static constexpr int NT = PAIRS * GROUPS;       // 384 or 512 threads = 4 * RW
   static constexpr int LSTRIDE = NT / RW;         // load / store mapping: rows per column sweep
@@ -661,10 +661,11 @@ struct TbCfg {
   static constexpr size_t lBytes = size_t(LIST) * 2;
   static constexpr size_t gBytes = size_t(RW) * 4 * 2;
   static constexpr size_t mBytes = (4 + kThrMax) * 4;   // n_en[2], overflow flag, thresholds
-  // order planes of the 4-neighbour array: 32 cells per word, one word row per region row
+  // order planes: 32 cells per word, one word row per region row; H, V, LV for the
+  // 4-neighbour array, and the two diagonals as well for the Moore neighbourhood
   static constexpr int W = RW / 32;
   static constexpr size_t pOff = kBytes + cBytes + lBytes + gBytes + mBytes;
-  static constexpr size_t pBytes = size_t(3) * RW * W * 4;
+  static constexpr size_t pBytes = size_t(5) * RW * W * 4;
   static constexpr size_t fBytes = 64;            // snapshot-frame view (frame variant), 16-byte aligned
   static constexpr size_t fOff = (pOff + pBytes + 15) / 16 * 16;
   static constexpr size_t bytes = fOff + fBytes;
@@ -700,6 +701,67 @@ __device__ __forceinline__ void order_update(unsigned* H, unsigned* V, unsigned*
   if (nk >= t2) atomicAnd(&LV[wc], ~bit);
 }
 
+// (tick, lattice index) order of two cells from their keys and indices: the exact order
+// in a region that wraps across the torus seam, where region order is not index order.
+__device__ __forceinline__ bool precedes_exact(unsigned long long ka, unsigned ga, unsigned long long kb, unsigned gb) {
+  const unsigned long long ta = ka >> 1, tb = kb >> 1;
+  return ta < tb || (ta == tb && ga < gb);
+}
+
+__device__ __forceinline__ void plane_flip(unsigned* P, int W, int r, int c, bool flip) {
+  if (flip) atomicXor(&P[r * W + (c >> 5)], 1u << (c & 31));
+}
+
+// Order planes of the Moore neighbourhood (Life-like automaton): besides H (right) and V
+// (below), SE bit (i, j) says cell (i, j) precedes (i+1, j+1) and SW bit (i, j) that it
+// precedes (i+1, j-1).  Cell (i, j) is enabled iff its own H, V, SE, SW and LV bits are
+// set and H(i, j-1), V(i-1, j), SE(i-1, j-1), SW(i-1, j+1) are clear.  Enabled cells
+// are at Chebyshev distance >= 2, so each edge bit has at most one writer per round; a
+// committed cell flips those of its 8 edges whose order changed (its own four were set,
+// the four towards earlier cells clear).  With exact = false the region does not wrap
+// and region order is index order, so a key compare with the index tie rule decides.
+template <int RW>
+__device__ __forceinline__ void moore_order_update(unsigned* OH, unsigned* OV, unsigned* OL, unsigned* OSE,
+                                                   unsigned* OSW, int r, int c, unsigned long long nk, unsigned gc,
+                                                   const unsigned long long* kp, bool exact, const unsigned* rowoff,
+                                                   const unsigned* colg, unsigned long long t2) {
+  constexpr int W = RW / 32;
+  const unsigned long long kl = kp[-1], kr = kp[1], ku = kp[-RW], kd = kp[RW];
+  const unsigned long long kul = kp[-RW - 1], kur = kp[-RW + 1], kdl = kp[RW - 1], kdr = kp[RW + 1];
+  bool e_c, e_l, s_c, s_u, se_c, se_ul, sw_c, sw_ur;
+  if (exact) {
+    const unsigned r0 = rowoff[r - 1], r1 = rowoff[r], r2 = rowoff[r + 1];
+    const unsigned c0 = colg[c - 1], c1 = colg[c], c2 = colg[c + 1];
+    e_c = precedes_exact(nk, gc, kr, r1 + c2);
+    e_l = precedes_exact(kl, r1 + c0, nk, gc);
+    s_c = precedes_exact(nk, gc, kd, r2 + c1);
+    s_u = precedes_exact(ku, r0 + c1, nk, gc);
+    se_c = precedes_exact(nk, gc, kdr, r2 + c2);
+    se_ul = precedes_exact(kul, r0 + c0, nk, gc);
+    sw_c = precedes_exact(nk, gc, kdl, r2 + c0);
+    sw_ur = precedes_exact(kur, r0 + c2, nk, gc);
+  } else {
+    const unsigned long long lo = nk & ~1ull;
+    e_c = lo <= kr;
+    e_l = (kl & ~1ull) <= nk;
+    s_c = lo <= kd;
+    s_u = (ku & ~1ull) <= nk;
+    se_c = lo <= kdr;
+    se_ul = (kul & ~1ull) <= nk;
+    sw_c = lo <= kdl;
+    sw_ur = (kur & ~1ull) <= nk;
+  }
+  plane_flip(OH, W, r, c, !e_c);
+  plane_flip(OH, W, r, c - 1, e_l);
+  plane_flip(OV, W, r, c, !s_c);
+  plane_flip(OV, W, r - 1, c, s_u);
+  plane_flip(OSE, W, r, c, !se_c);
+  plane_flip(OSE, W, r - 1, c - 1, se_ul);
+  plane_flip(OSW, W, r, c, !sw_c);
+  plane_flip(OSW, W, r - 1, c + 1, sw_ur);
+  if (nk >= t2) atomicAnd(&OL[r * W + (c >> 5)], ~(1u << (c & 31)));
+}
+
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
@@ -724,7 +786,8 @@ __device__ __forceinline__ int wrap_index(int x, int n, int& shift, int up_shift
 // Sec. 3, e.g. Conway's Game of Life): a cell may commit once its key is below the
 // keys of all 8 Moore neighbours (its update reads all of them), so enabled cells
 // are pairwise at Chebyshev distance >= 2 and the same shrinking-region argument as
-// for the 4-neighbour array holds.
+// for the 4-neighbour array holds.  The enable test reads order planes (see
+// moore_order_update).
 
 // live cells among the 8 Moore neighbours of the region cell at kp
 template <int RW>
@@ -732,83 +795,6 @@ __device__ __forceinline__ unsigned moore_live(const unsigned long long* kp) {
   return ((unsigned)kp[-RW - 1] & 1u) + ((unsigned)kp[-RW] & 1u) + ((unsigned)kp[-RW + 1] & 1u) +
          ((unsigned)kp[-1] & 1u) + ((unsigned)kp[1] & 1u) + ((unsigned)kp[RW - 1] & 1u) +
          ((unsigned)kp[RW] & 1u) + ((unsigned)kp[RW + 1] & 1u);
-}
-
-// Enable test of a thread's column pair (pc, pc + 1) over ROWS region rows from rbase,
-// for a region that does not wrap: region row-major order is the index order, so a
-// neighbour in the row above or to the left needs tick_c < tick_n ((key_c | 1) < key_n)
-// and one below or to the right tick_c <= tick_n ((key_c & ~1) <= key_n).  The relations
-// between a row and the row below are carried to the next row (complemented).
-template <int RW, int ROWS>
-__device__ __forceinline__ unsigned life_scan(const unsigned long long* K, int rbase, int pc,
-                                              unsigned long long t2) {
-  const unsigned long long* q = K + rbase * RW + pc;
-  ulonglong2 mv = *reinterpret_cast<const ulonglong2*>(q);
-  unsigned long long m0 = q[-1], m3 = q[2];
-  // up-row relations of the first row
-  const ulonglong2 uv = *reinterpret_cast<const ulonglong2*>(q - RW);
-  const unsigned long long u0 = q[-RW - 1], u3 = q[-RW + 2];
-  bool a_u1 = (mv.x | 1ull) < uv.x, a_u2 = (mv.x | 1ull) < uv.y;   // a before its up, up-right
-  bool b_u1 = (mv.y | 1ull) < uv.x, b_u2 = (mv.y | 1ull) < uv.y;   // b before its up-left, up
-  bool a_u0 = (mv.x | 1ull) < u0, b_u3 = (mv.y | 1ull) < u3;
-  unsigned mask = 0;
-#pragma unroll
-  for (int i = 0; i < ROWS; ++i) {
-    const unsigned long long* qd = q + (i + 1) * RW;
-    const ulonglong2 dv = *reinterpret_cast<const ulonglong2*>(qd);
-    const unsigned long long d0 = qd[-1], d3 = qd[2];
-    const unsigned long long loa = mv.x & ~1ull, lob = mv.y & ~1ull;
-    const unsigned long long hia = mv.x | 1ull, hib = mv.y | 1ull;
-    const bool a_d0 = loa <= d0, a_d1 = loa <= dv.x, a_d2 = loa <= dv.y;
-    const bool b_d1 = lob <= dv.x, b_d2 = lob <= dv.y, b_d3 = lob <= d3;
-    const bool ab = loa <= mv.y;
-    const bool ea = (mv.x < t2) & a_u0 & a_u1 & a_u2 & (hia < m0) & ab & a_d0 & a_d1 & a_d2;
-    const bool eb = (mv.y < t2) & b_u1 & b_u2 & b_u3 & !ab & (lob <= m3) & b_d1 & b_d2 & b_d3;
-    mask |= ((unsigned)ea << (2 * i)) | ((unsigned)eb << (2 * i + 1));
-    // next row: its a sits below a, its b below b; up-left of a and up-right of b are new
-    const ulonglong2 nv = dv;
-    a_u1 = !a_d1;
-    a_u2 = !b_d1;
-    b_u1 = !a_d2;
-    b_u2 = !b_d2;
-    a_u0 = (nv.x | 1ull) < m0;
-    b_u3 = (nv.y | 1ull) < m3;
-    mv = nv;
-    m0 = d0;
-    m3 = d3;
-  }
-  return mask;
-}
-
-// The same test for a region that wraps across the torus seam: ticks compared
-// directly, equal ticks ordered by the cells' lattice indices.
-template <int RW, int ROWS>
-__device__ __forceinline__ unsigned life_scan_exact(const unsigned long long* K, const unsigned* rowoff,
-                                                    const unsigned* colg, int rbase, int pc,
-                                                    unsigned long long t2) {
-  unsigned mask = 0;
-  for (int i = 0; i < ROWS; ++i) {
-    const int r = rbase + i;
-    for (int e = 0; e < 2; ++e) {
-      const int c = pc + e;
-      if (r > RW - 1 || c < 1 || c > RW - 2) continue;   // never a valid cell (masked by the caller)
-      const unsigned long long kc = K[r * RW + c];
-      const unsigned long long tc = kc >> 1;
-      const unsigned gc = rowoff[r] + colg[c];
-      bool ok = kc < t2;
-#pragma unroll
-      for (int dr = -1; dr <= 1; ++dr)
-#pragma unroll
-        for (int dc = -1; dc <= 1; ++dc) {
-          if (dr == 0 && dc == 0) continue;
-          const unsigned long long tn = K[(r + dr) * RW + c + dc] >> 1;
-          const unsigned gn = rowoff[r + dr] + colg[c + dc];
-          ok &= (tc < tn) || (tc == tn && gc < gn);
-        }
-      mask |= (unsigned)ok << (2 * i + e);
-    }
-  }
-  return mask;
 }
 
 // ---- Ising array on the q-th degree neighbourhood (Sec. 3): every cell within
@@ -881,6 +867,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   unsigned int* OH = reinterpret_cast<unsigned int*>(smem_raw + Cfg::pOff);   // order planes
   unsigned int* OV = OH + RW * Cfg::W;
   unsigned int* OL = OV + RW * Cfg::W;
+  unsigned int* OSE = OL + RW * Cfg::W;
+  unsigned int* OSW = OSE + RW * Cfg::W;
   FrameView* fv = reinterpret_cast<FrameView*>(smem_raw + Cfg::fOff);
   static_assert(sizeof(FrameView) <= Cfg::fBytes, "frame view does not fit");
 
@@ -1002,20 +990,47 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     const unsigned* __restrict__ rates = L.rates;
     constexpr unsigned kEven = 0x55555555u, kOdd = 0xAAAAAAAAu;
     constexpr int W = Cfg::W;
-    if (MODEL == 0) {
+    if (MODEL == 0 || MODEL == 1) {
       // order planes of the loaded region; a warp covers 32 consecutive columns of one
-      // row.  Relations with cells outside the loaded rectangle are never read.
+      // row.  Relations with cells outside the loaded rectangle are never read (the
+      // reads past the region's last row and column stay inside shared memory).
       for (int i = li0; i < RW; i += Cfg::LSTRIDE) {
         const unsigned long long kc = K[i * RW + lj];
         const unsigned long long kr = K[i * RW + lj + 1];
         const unsigned long long kd = K[(i + 1) * RW + lj];
-        const unsigned hb = __ballot_sync(kFull, (kc & ~1ull) <= kr);
-        const unsigned vb = __ballot_sync(kFull, (kc & ~1ull) <= kd);
+        bool ph, pv, pse = false, psw = false;
+        if (MODEL == 1 && edge) {   // the Moore neighbourhood across the seam: exact order
+          const unsigned gc = rowoff[i] + colg[lj], gd = rowoff[i + 1];
+          ph = precedes_exact(kc, gc, kr, rowoff[i] + colg[lj + 1]);
+          pv = precedes_exact(kc, gc, kd, gd + colg[lj]);
+          pse = precedes_exact(kc, gc, K[(i + 1) * RW + lj + 1], gd + colg[lj + 1]);
+          psw = precedes_exact(kc, gc, K[(i + 1) * RW + lj - 1], gd + colg[lj - 1]);
+        } else {
+          const unsigned long long lo = kc & ~1ull;
+          ph = lo <= kr;
+          pv = lo <= kd;
+          if (MODEL == 1) {
+            pse = lo <= K[(i + 1) * RW + lj + 1];
+            psw = lo <= K[(i + 1) * RW + lj - 1];
+          }
+        }
+        const unsigned hb = __ballot_sync(kFull, ph);
+        const unsigned vb = __ballot_sync(kFull, pv);
         const unsigned lb = __ballot_sync(kFull, kc < t2);
+        unsigned seb = 0u, swb = 0u;
+        if (MODEL == 1) {
+          seb = __ballot_sync(kFull, pse);
+          swb = __ballot_sync(kFull, psw);
+        }
         if (lane == 0) {
-          OH[i * W + (lj >> 5)] = hb;
-          OV[i * W + (lj >> 5)] = vb;
-          OL[i * W + (lj >> 5)] = lb;
+          const int wi = i * W + (lj >> 5);
+          OH[wi] = hb;
+          OV[wi] = vb;
+          OL[wi] = lb;
+          if (MODEL == 1) {
+            OSE[wi] = seb;
+            OSW[wi] = swb;
+          }
         }
       }
       __syncthreads();
@@ -1027,14 +1042,21 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       unsigned mask = 0;
       // the word scanned by this thread (4-neighbour array): row oi, columns 32 ow ...
       const int oi = tid / W, ow = tid % W;
-      if (MODEL == 0) {
+      if (MODEL == 0 || MODEL == 1) {
         if (oi < RW && oi >= kk && oi < RH - kk) {
           const int lo = max(kk - 32 * ow, 0), hi = min(RC - kk - 32 * ow, 32);
           if (hi > lo) {
             const unsigned cm = (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
-            const unsigned h = OH[oi * W + ow];
-            const unsigned hl = (h << 1) | (ow > 0 ? (OH[oi * W + ow - 1] >> 31) : 0u);
-            mask = h & ~hl & OV[oi * W + ow] & ~OV[(oi - 1) * W + ow] & OL[oi * W + ow] & cm;
+            const int wi = oi * W + ow, wu = wi - W;
+            const unsigned h = OH[wi];
+            const unsigned hl = (h << 1) | (ow > 0 ? (OH[wi - 1] >> 31) : 0u);
+            unsigned m = h & ~hl & OV[wi] & ~OV[wu] & OL[wi] & cm;
+            if (MODEL == 1) {   // the diagonals: SE of the up-left cell, SW of the up-right cell
+              const unsigned seu = (OSE[wu] << 1) | (ow > 0 ? (OSE[wu - 1] >> 31) : 0u);
+              const unsigned swu = (OSW[wu] >> 1) | (ow + 1 < W ? (OSW[wu + 1] << 31) : 0u);
+              m &= OSE[wi] & OSW[wi] & ~seu & ~swu;
+            }
+            mask = m;
             scanned += (unsigned long long)__popc(cm);
           }
         }
@@ -1046,13 +1068,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const unsigned hi_bits = (2 * rhi >= 32) ? 0xFFFFFFFFu : ((1u << (2 * rhi)) - 1u);
         rowm = hi_bits & ~((1u << (2 * rlo)) - 1u);
       }
-      const unsigned valid = MODEL == 0 ? 0u : colm & rowm;
-      if (MODEL == 1 && valid) {
-        mask = edge ? life_scan_exact<RW, Cfg::ROWS>(K, rowoff, colg, rbase, pc, t2)
-                    : life_scan<RW, Cfg::ROWS>(K, rbase, pc, t2);
-        mask &= valid;
-        scanned += (unsigned long long)__popc(valid);
-      } else if (MODEL == 2 && valid) {
+      const unsigned valid = MODEL == 2 ? colm & rowm : 0u;
+      if (MODEL == 2 && valid) {
         mask = q_scan_exact<RW, Cfg::ROWS>(K, rowoff, colg, rbase, pc, t2, qn) & valid;
         scanned += (unsigned long long)__popc(valid);
       }
@@ -1074,7 +1091,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const int b = __ffs(mask) - 1;
         mask &= mask - 1;
         if (off < Cfg::LIST)
-          list[off] = MODEL == 0 ? (unsigned short)((oi << 8) | (32 * ow + b))
+          list[off] = MODEL != 2 ? (unsigned short)((oi << 8) | (32 * ow + b))
                                  : (unsigned short)(((rbase + (b >> 1)) << 8) | (pc + (b & 1)));
         ++off;
       }
@@ -1144,6 +1161,9 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         if (MODEL == 0) {
           order_update(OH, OV, OL, W, ra, ca, nka, nla, nra, nua, nda, t2);
           order_update(OH, OV, OL, W, rb, cb, nkb, nlb, nrb, nub, ndb, t2);
+        } else if (MODEL == 1) {
+          moore_order_update<RW>(OH, OV, OL, OSE, OSW, ra, ca, nka, gia, kpa, edge, rowoff, colg, t2);
+          moore_order_update<RW>(OH, OV, OL, OSE, OSW, rb, cb, nkb, gib, kpb, edge, rowoff, colg, t2);
         }
         if (FR) {   // own cells only: halo commits are repeated by the owning tile
           if (ra >= D && ra < D + g.h && ca >= D && ca < D + g.w)
@@ -1182,6 +1202,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         *kp = nk;
         C[r * RW + cc] = (unsigned short)(c16 + 1u);
         if (MODEL == 0) order_update(OH, OV, OL, W, r, cc, nk, nl, nr, nu, nd, t2);
+        if (MODEL == 1) moore_order_update<RW>(OH, OV, OL, OSE, OSW, r, cc, nk, gidx, kp, edge, rowoff, colg, t2);
         if (FR && r >= D && r < D + g.h && cc >= D && cc < D + g.w)
           write_frames(*fv, gidx, key >> 1, nk >> 1, (unsigned)nk & 1u);
       }
