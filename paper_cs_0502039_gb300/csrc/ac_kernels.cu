@@ -639,9 +639,9 @@ __global__ void __launch_bounds__(4 * LB) blocked_kernel(const LatDesc* __restri
 // side are unchanged, and between the sides they give the (tick, index) order of
 // the seam (the Life variant compares lattice indices there instead).  Counts are
 // held as 16-bit offsets from the tile centre's count.  Requires rows, cols >= 4D
-// (the region never overlaps itself).  The 4-neighbour array and the Life automaton
-// test enablement on order planes (one bit per lattice edge, see order_update and
-// moore_order_update); the q-th degree variant scans the keys of its diamond directly.
+// (the region never overlaps itself).  The 4-neighbour array, the Life automaton and
+// the q = 2 diamond test enablement on order planes (one bit per lattice edge, see
+// order_update and moore_order_update); q = 3 scans the keys of its diamond directly.
 template <int RW>
 struct TbCfg {
   static constexpr int PAIRS = RW / 2;            // dense scan (q-neighbourhood): a thread scans
@@ -662,10 +662,11 @@ struct TbCfg {
   static constexpr size_t gBytes = size_t(RW) * 4 * 2;
   static constexpr size_t mBytes = (4 + kThrMax) * 4;   // n_en[2], overflow flag, thresholds
   // order planes: 32 cells per word, one word row per region row; H, V, LV for the
-  // 4-neighbour array, and the two diagonals as well for the Moore neighbourhood
+  // 4-neighbour array, the two diagonals as well for the Moore neighbourhood, and the
+  // two edges of length 2 as well for the q = 2 diamond
   static constexpr int W = RW / 32;
   static constexpr size_t pOff = kBytes + cBytes + lBytes + gBytes + mBytes;
-  static constexpr size_t pBytes = size_t(5) * RW * W * 4;
+  static constexpr size_t pBytes = size_t(7) * RW * W * 4;
   static constexpr size_t fBytes = 64;            // snapshot-frame view (frame variant), 16-byte aligned
   static constexpr size_t fOff = (pOff + pBytes + 15) / 16 * 16;
   static constexpr size_t bytes = fOff + fBytes;
@@ -720,12 +721,37 @@ __device__ __forceinline__ void plane_flip(unsigned* P, int W, int r, int c, boo
 // committed cell flips those of its 8 edges whose order changed (its own four were set,
 // the four towards earlier cells clear).  With exact = false the region does not wrap
 // and region order is index order, so a key compare with the index tie rule decides.
-template <int RW>
+// FAR adds the q = 2 diamond's edges of length 2: H2 bit (i, j) says the cell precedes
+// (i, j+2), V2 bit (i, j) that it precedes (i+2, j) (12 edges per cell; enabled cells
+// of the diamond are more than 2 apart, so again one writer per edge and round).
+template <int RW, bool FAR>
 __device__ __forceinline__ void moore_order_update(unsigned* OH, unsigned* OV, unsigned* OL, unsigned* OSE,
-                                                   unsigned* OSW, int r, int c, unsigned long long nk, unsigned gc,
-                                                   const unsigned long long* kp, bool exact, const unsigned* rowoff,
-                                                   const unsigned* colg, unsigned long long t2) {
+                                                   unsigned* OSW, unsigned* OH2, unsigned* OV2, int r, int c,
+                                                   unsigned long long nk, unsigned gc, const unsigned long long* kp,
+                                                   bool exact, const unsigned* rowoff, const unsigned* colg,
+                                                   unsigned long long t2) {
   constexpr int W = RW / 32;
+  if (FAR) {
+    const unsigned long long kl2 = kp[-2], kr2 = kp[2], ku2 = kp[-2 * RW], kd2 = kp[2 * RW];
+    bool h2_c, h2_l, v2_c, v2_u;
+    if (exact) {
+      const unsigned r1 = rowoff[r], c1 = colg[c];
+      h2_c = precedes_exact(nk, gc, kr2, r1 + colg[c + 2]);
+      h2_l = precedes_exact(kl2, r1 + colg[c - 2], nk, gc);
+      v2_c = precedes_exact(nk, gc, kd2, rowoff[r + 2] + c1);
+      v2_u = precedes_exact(ku2, rowoff[r - 2] + c1, nk, gc);
+    } else {
+      const unsigned long long lo = nk & ~1ull;
+      h2_c = lo <= kr2;
+      h2_l = (kl2 & ~1ull) <= nk;
+      v2_c = lo <= kd2;
+      v2_u = (ku2 & ~1ull) <= nk;
+    }
+    plane_flip(OH2, W, r, c, !h2_c);
+    plane_flip(OH2, W, r, c - 2, h2_l);
+    plane_flip(OV2, W, r, c, !v2_c);
+    plane_flip(OV2, W, r - 2, c, v2_u);
+  }
   const unsigned long long kl = kp[-1], kr = kp[1], ku = kp[-RW], kd = kp[RW];
   const unsigned long long kul = kp[-RW - 1], kur = kp[-RW + 1], kdl = kp[RW - 1], kdr = kp[RW + 1];
   bool e_c, e_l, s_c, s_u, se_c, se_ul, sw_c, sw_ur;
@@ -813,8 +839,8 @@ __device__ __forceinline__ unsigned q_up(const unsigned long long* kp, int q) {
   return j;
 }
 
-// Enable test of a thread's column pair over ROWS rows: ticks compared directly, equal
-// ticks ordered by the cells' lattice indices.  Cells closer than q to the region's
+// Enable test of a thread's column pair over ROWS rows (q = 3): ticks compared directly,
+// equal ticks ordered by the cells' lattice indices.  Cells closer than q to the region's
 // edge are never valid for this model and are skipped (their diamonds leave the region).
 template <int RW, int ROWS>
 __device__ __forceinline__ unsigned q_scan_exact(const unsigned long long* K, const unsigned* rowoff,
@@ -869,6 +895,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   unsigned int* OL = OV + RW * Cfg::W;
   unsigned int* OSE = OL + RW * Cfg::W;
   unsigned int* OSW = OSE + RW * Cfg::W;
+  unsigned int* OH2 = OSW + RW * Cfg::W;
+  unsigned int* OV2 = OH2 + RW * Cfg::W;
   FrameView* fv = reinterpret_cast<FrameView*>(smem_raw + Cfg::fOff);
   static_assert(sizeof(FrameView) <= Cfg::fBytes, "frame view does not fit");
 
@@ -990,7 +1018,11 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     const unsigned* __restrict__ rates = L.rates;
     constexpr unsigned kEven = 0x55555555u, kOdd = 0xAAAAAAAAu;
     constexpr int W = Cfg::W;
-    if (MODEL == 0 || MODEL == 1) {
+    const int qn = (MODEL == 2) ? L.q : 1;     // rings lost per round
+    // order planes serve the 4-neighbour array, the Moore automaton and the q = 2 diamond
+    // (q = 3 scans its keys directly: its 12 edge directions would not fit two CTAs per SM)
+    const bool planes = MODEL != 2 || qn == 2;
+    if (planes) {
       // order planes of the loaded region; a warp covers 32 consecutive columns of one
       // row.  Relations with cells outside the loaded rectangle are never read (the
       // reads past the region's last row and column stay inside shared memory).
@@ -998,51 +1030,66 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const unsigned long long kc = K[i * RW + lj];
         const unsigned long long kr = K[i * RW + lj + 1];
         const unsigned long long kd = K[(i + 1) * RW + lj];
-        bool ph, pv, pse = false, psw = false;
-        if (MODEL == 1 && edge) {   // the Moore neighbourhood across the seam: exact order
+        bool ph, pv, pse = false, psw = false, ph2 = false, pv2 = false;
+        if (MODEL != 0 && edge) {   // wider neighbourhoods across the seam: exact order
           const unsigned gc = rowoff[i] + colg[lj], gd = rowoff[i + 1];
           ph = precedes_exact(kc, gc, kr, rowoff[i] + colg[lj + 1]);
           pv = precedes_exact(kc, gc, kd, gd + colg[lj]);
           pse = precedes_exact(kc, gc, K[(i + 1) * RW + lj + 1], gd + colg[lj + 1]);
           psw = precedes_exact(kc, gc, K[(i + 1) * RW + lj - 1], gd + colg[lj - 1]);
+          if (MODEL == 2) {
+            ph2 = precedes_exact(kc, gc, K[i * RW + lj + 2], rowoff[i] + colg[lj + 2]);
+            pv2 = precedes_exact(kc, gc, K[(i + 2) * RW + lj], rowoff[i + 2] + colg[lj]);
+          }
         } else {
           const unsigned long long lo = kc & ~1ull;
           ph = lo <= kr;
           pv = lo <= kd;
-          if (MODEL == 1) {
+          if (MODEL != 0) {
             pse = lo <= K[(i + 1) * RW + lj + 1];
             psw = lo <= K[(i + 1) * RW + lj - 1];
+          }
+          if (MODEL == 2) {
+            ph2 = lo <= K[i * RW + lj + 2];
+            pv2 = lo <= K[(i + 2) * RW + lj];
           }
         }
         const unsigned hb = __ballot_sync(kFull, ph);
         const unsigned vb = __ballot_sync(kFull, pv);
         const unsigned lb = __ballot_sync(kFull, kc < t2);
-        unsigned seb = 0u, swb = 0u;
-        if (MODEL == 1) {
+        unsigned seb = 0u, swb = 0u, h2b = 0u, v2b = 0u;
+        if (MODEL != 0) {
           seb = __ballot_sync(kFull, pse);
           swb = __ballot_sync(kFull, psw);
+        }
+        if (MODEL == 2) {
+          h2b = __ballot_sync(kFull, ph2);
+          v2b = __ballot_sync(kFull, pv2);
         }
         if (lane == 0) {
           const int wi = i * W + (lj >> 5);
           OH[wi] = hb;
           OV[wi] = vb;
           OL[wi] = lb;
-          if (MODEL == 1) {
+          if (MODEL != 0) {
             OSE[wi] = seb;
             OSW[wi] = swb;
+          }
+          if (MODEL == 2) {
+            OH2[wi] = h2b;
+            OV2[wi] = v2b;
           }
         }
       }
       __syncthreads();
     }
     int cur = 0;
-    const int qn = (MODEL == 2) ? L.q : 1;     // rings lost per round
     for (int k = 1; k <= R; ++k) {
       const int kk = k * qn;
       unsigned mask = 0;
       // the word scanned by this thread (4-neighbour array): row oi, columns 32 ow ...
       const int oi = tid / W, ow = tid % W;
-      if (MODEL == 0 || MODEL == 1) {
+      if (planes) {
         if (oi < RW && oi >= kk && oi < RH - kk) {
           const int lo = max(kk - 32 * ow, 0), hi = min(RC - kk - 32 * ow, 32);
           if (hi > lo) {
@@ -1051,10 +1098,15 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
             const unsigned h = OH[wi];
             const unsigned hl = (h << 1) | (ow > 0 ? (OH[wi - 1] >> 31) : 0u);
             unsigned m = h & ~hl & OV[wi] & ~OV[wu] & OL[wi] & cm;
-            if (MODEL == 1) {   // the diagonals: SE of the up-left cell, SW of the up-right cell
+            if (MODEL != 0) {   // the diagonals: SE of the up-left cell, SW of the up-right cell
               const unsigned seu = (OSE[wu] << 1) | (ow > 0 ? (OSE[wu - 1] >> 31) : 0u);
               const unsigned swu = (OSW[wu] >> 1) | (ow + 1 < W ? (OSW[wu + 1] << 31) : 0u);
               m &= OSE[wi] & OSW[wi] & ~seu & ~swu;
+            }
+            if (MODEL == 2) {   // q = 2: H2 of the cell two to the left, V2 of the cell two above
+              const unsigned h2 = OH2[wi];
+              const unsigned h2l = (h2 << 2) | (ow > 0 ? (OH2[wi - 1] >> 30) : 0u);
+              m &= h2 & ~h2l & OV2[wi] & ~OV2[wu - W];
             }
             mask = m;
             scanned += (unsigned long long)__popc(cm);
@@ -1068,7 +1120,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const unsigned hi_bits = (2 * rhi >= 32) ? 0xFFFFFFFFu : ((1u << (2 * rhi)) - 1u);
         rowm = hi_bits & ~((1u << (2 * rlo)) - 1u);
       }
-      const unsigned valid = MODEL == 2 ? colm & rowm : 0u;
+      const unsigned valid = planes ? 0u : colm & rowm;
       if (MODEL == 2 && valid) {
         mask = q_scan_exact<RW, Cfg::ROWS>(K, rowoff, colg, rbase, pc, t2, qn) & valid;
         scanned += (unsigned long long)__popc(valid);
@@ -1091,7 +1143,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const int b = __ffs(mask) - 1;
         mask &= mask - 1;
         if (off < Cfg::LIST)
-          list[off] = MODEL != 2 ? (unsigned short)((oi << 8) | (32 * ow + b))
+          list[off] = planes ? (unsigned short)((oi << 8) | (32 * ow + b))
                                  : (unsigned short)(((rbase + (b >> 1)) << 8) | (pc + (b & 1)));
         ++off;
       }
@@ -1162,8 +1214,11 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
           order_update(OH, OV, OL, W, ra, ca, nka, nla, nra, nua, nda, t2);
           order_update(OH, OV, OL, W, rb, cb, nkb, nlb, nrb, nub, ndb, t2);
         } else if (MODEL == 1) {
-          moore_order_update<RW>(OH, OV, OL, OSE, OSW, ra, ca, nka, gia, kpa, edge, rowoff, colg, t2);
-          moore_order_update<RW>(OH, OV, OL, OSE, OSW, rb, cb, nkb, gib, kpb, edge, rowoff, colg, t2);
+          moore_order_update<RW, false>(OH, OV, OL, OSE, OSW, OH2, OV2, ra, ca, nka, gia, kpa, edge, rowoff, colg, t2);
+          moore_order_update<RW, false>(OH, OV, OL, OSE, OSW, OH2, OV2, rb, cb, nkb, gib, kpb, edge, rowoff, colg, t2);
+        } else if (planes) {   // the q = 2 diamond
+          moore_order_update<RW, true>(OH, OV, OL, OSE, OSW, OH2, OV2, ra, ca, nka, gia, kpa, edge, rowoff, colg, t2);
+          moore_order_update<RW, true>(OH, OV, OL, OSE, OSW, OH2, OV2, rb, cb, nkb, gib, kpb, edge, rowoff, colg, t2);
         }
         if (FR) {   // own cells only: halo commits are repeated by the owning tile
           if (ra >= D && ra < D + g.h && ca >= D && ca < D + g.w)
@@ -1202,7 +1257,10 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         *kp = nk;
         C[r * RW + cc] = (unsigned short)(c16 + 1u);
         if (MODEL == 0) order_update(OH, OV, OL, W, r, cc, nk, nl, nr, nu, nd, t2);
-        if (MODEL == 1) moore_order_update<RW>(OH, OV, OL, OSE, OSW, r, cc, nk, gidx, kp, edge, rowoff, colg, t2);
+        if (MODEL == 1)
+          moore_order_update<RW, false>(OH, OV, OL, OSE, OSW, OH2, OV2, r, cc, nk, gidx, kp, edge, rowoff, colg, t2);
+        else if (MODEL == 2 && planes)
+          moore_order_update<RW, true>(OH, OV, OL, OSE, OSW, OH2, OV2, r, cc, nk, gidx, kp, edge, rowoff, colg, t2);
         if (FR && r >= D && r < D + g.h && cc >= D && cc < D + g.w)
           write_frames(*fv, gidx, key >> 1, nk >> 1, (unsigned)nk & 1u);
       }
