@@ -419,7 +419,7 @@ ac_status run_tb(ac_sim* s, long long t_end, int D, int R) {
       return fail(AC_ERR_OOM, "second state buffer (%zu cells) allocation failed", N);
     }
   }
-  const int region = ac::tb_region_for(D);
+  const int region = ac::tb_region_for_model(D, s->model, s->q);
   int tr = 0, tc = 0;
   tb_tiling(s->rows, s->cols, region, D, ac::tb_grid(region), &tr, &tc);
   ac::LatDesc d = s->host_desc(t_end, 0);
@@ -748,7 +748,7 @@ ac_status run_tb_frames(ac_sim* s, long long t_end, ac_frame_fn fn, void* user, 
   unsigned long long ev_before = 0, ev_after = 0;
   ac_status st = read_event_counter(s, &ev_before);
   if (st != AC_OK) return st;
-  const int region = ac::tb_region_for(D);
+  const int region = ac::tb_region_for_model(D, s->model, s->q);
   int tr = 0, tc = 0;
   tb_tiling(s->rows, s->cols, region, D, ac::tb_grid(region), &tr, &tc);
   const int total = tr * tc;

@@ -83,6 +83,8 @@ enum KernelKind { kKernelRound = 0, kKernelBlocked = 1 };
 // SM) or 128 (one) holds a tile and a halo of depth D around it; tile side = region - 2D.
 constexpr int kTbMaxHalo = 16;
 inline int tb_region_for(int halo) { return halo <= 12 ? 96 : 128; }
+// the q = 3 diamond's 13 order planes exist on the 128-wide region only
+inline int tb_region_for_model(int halo, int model, int q) { return (model == 2 && q == 3) ? 128 : tb_region_for(halo); }
 
 struct LaunchCfg {
   int kernel;       // KernelKind

@@ -639,15 +639,12 @@ __global__ void __launch_bounds__(4 * LB) blocked_kernel(const LatDesc* __restri
 // side are unchanged, and between the sides they give the (tick, index) order of
 // the seam (the Life variant compares lattice indices there instead).  Counts are
 // held as 16-bit offsets from the tile centre's count.  Requires rows, cols >= 4D
-// (the region never overlaps itself).  The 4-neighbour array, the Life automaton and
-// the q = 2 diamond test enablement on order planes (one bit per lattice edge, see
-// order_update and moore_order_update); q = 3 scans the keys of its diamond directly.
+// (the region never overlaps itself).  Every model tests enablement on order planes
+// (one bit per lattice edge): see order_update (4-neighbour array), moore_order_update
+// (Life automaton, q = 2 diamond) and q3_order_update (q = 3 diamond, 128-wide only).
 template <int RW>
 struct TbCfg {
-  static constexpr int PAIRS = RW / 2;            // dense scan (q-neighbourhood): a thread scans
-  static constexpr int GROUPS = 8;                // a column pair in one of 8 row bands
-  static constexpr int ROWS = RW / GROUPS;        // rows per band (12 or 16)
-  static constexpr int NT = PAIRS * GROUPS;       // 384 or 512 threads = 4 * RW
+  static constexpr int NT = 4 * RW;               // 384 or 512 threads
   static constexpr int LSTRIDE = NT / RW;         // load / store mapping: rows per column sweep
   // enabled cells form an independent set of the scanned rectangle (at most
   // (RW-2) x (RW-2) cells): the list holds every one of them, so a round always
@@ -663,10 +660,12 @@ struct TbCfg {
   static constexpr size_t mBytes = (4 + kThrMax) * 4;   // n_en[2], overflow flag, thresholds
   // order planes: 32 cells per word, one word row per region row; H, V, LV for the
   // 4-neighbour array, the two diagonals as well for the Moore neighbourhood, and the
-  // two edges of length 2 as well for the q = 2 diamond
+  // two edges of length 2 as well for the q = 2 diamond (7 planes); the q = 3 diamond
+  // (12 edge directions and LV, 13 planes) runs on the 128-wide region only
   static constexpr int W = RW / 32;
+  static constexpr int PLANES = (RW == 128) ? 13 : 7;
   static constexpr size_t pOff = kBytes + cBytes + lBytes + gBytes + mBytes;
-  static constexpr size_t pBytes = size_t(7) * RW * W * 4;
+  static constexpr size_t pBytes = size_t(PLANES) * RW * W * 4;
   static constexpr size_t fBytes = 64;            // snapshot-frame view (frame variant), 16-byte aligned
   static constexpr size_t fOff = (pOff + pBytes + 15) / 16 * 16;
   static constexpr size_t bytes = fOff + fBytes;
@@ -788,6 +787,40 @@ __device__ __forceinline__ void moore_order_update(unsigned* OH, unsigned* OV, u
   if (nk >= t2) atomicAnd(&OL[r * W + (c >> 5)], ~(1u << (c & 31)));
 }
 
+// The q = 3 diamond's 12 forward edge directions (dr, dc): the neighbours within
+// Manhattan distance 3 that come later in region order.  Plane d holds, for each cell,
+// whether it precedes its neighbour at (i + dr, j + dc); plane 12 is LV.
+__device__ __forceinline__ constexpr int q3_dr(int d) { return d < 3 ? 0 : (d < 8 ? 1 : (d < 11 ? 2 : 3)); }
+__device__ __forceinline__ constexpr int q3_dc(int d) { return d < 3 ? d + 1 : (d < 8 ? d - 5 : (d < 11 ? d - 9 : 0)); }
+
+// Order planes of the q = 3 diamond (128-wide region): a cell is enabled iff its 12 own
+// bits and LV are set and, for every direction d, the bit of the cell at (i - dr, j - dc)
+// is clear.  Enabled cells are more than 3 apart, so each edge has at most one writer
+// per round; a committed cell flips the changed bits of its 24 edges.
+template <int RW>
+__device__ __forceinline__ void q3_order_update(unsigned* OQ, int r, int c, unsigned long long nk, unsigned gc,
+                                                const unsigned long long* kp, bool exact, const unsigned* rowoff,
+                                                const unsigned* colg, unsigned long long t2) {
+  constexpr int W = RW / 32;
+#pragma unroll
+  for (int d = 0; d < 12; ++d) {
+    const int dr = q3_dr(d), dc = q3_dc(d);
+    unsigned* P = OQ + d * RW * W;
+    const unsigned long long kf = kp[dr * RW + dc], kb = kp[-dr * RW - dc];
+    bool own, back;
+    if (exact) {
+      own = precedes_exact(nk, gc, kf, rowoff[r + dr] + colg[c + dc]);
+      back = precedes_exact(kb, rowoff[r - dr] + colg[c - dc], nk, gc);
+    } else {
+      own = (nk & ~1ull) <= kf;
+      back = (kb & ~1ull) <= nk;
+    }
+    plane_flip(P, W, r, c, !own);
+    plane_flip(P, W, r - dr, c - dc, back);
+  }
+  if (nk >= t2) atomicAnd(&OQ[12 * RW * W + r * W + (c >> 5)], ~(1u << (c & 31)));
+}
+
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
@@ -839,38 +872,6 @@ __device__ __forceinline__ unsigned q_up(const unsigned long long* kp, int q) {
   return j;
 }
 
-// Enable test of a thread's column pair over ROWS rows (q = 3): ticks compared directly,
-// equal ticks ordered by the cells' lattice indices.  Cells closer than q to the region's
-// edge are never valid for this model and are skipped (their diamonds leave the region).
-template <int RW, int ROWS>
-__device__ __forceinline__ unsigned q_scan_exact(const unsigned long long* K, const unsigned* rowoff,
-                                                 const unsigned* colg, int rbase, int pc,
-                                                 unsigned long long t2, int q) {
-  unsigned mask = 0;
-  for (int i = 0; i < ROWS; ++i) {
-    const int r = rbase + i;
-    for (int e = 0; e < 2; ++e) {
-      const int c = pc + e;
-      if (r < q || r > RW - 1 - q || c < q || c > RW - 1 - q) continue;
-      const unsigned long long kc = K[r * RW + c];
-      const unsigned long long tc = kc >> 1;
-      const unsigned gc = rowoff[r] + colg[c];
-      bool ok = kc < t2;
-      for (int dr = -q; dr <= q && ok; ++dr) {
-        const int rem = q - (dr < 0 ? -dr : dr);
-        for (int dx = -rem; dx <= rem; ++dx) {
-          if (dr == 0 && dx == 0) continue;
-          const unsigned long long tn = K[(r + dr) * RW + c + dx] >> 1;
-          const unsigned gn = rowoff[r + dr] + colg[c + dx];
-          ok &= (tc < tn) || (tc == tn && gc < gn);
-        }
-      }
-      mask |= (unsigned)ok << (2 * i + e);
-    }
-  }
-  return mask;
-}
-
 // FR: snapshot frames are open (write_frames for the tile's own cells).
 // MODEL: 0 the Ising heat bath; 1 the Life-like automaton (Moore neighbourhood, birth /
 // survival masks in thr[0] / thr[1]); 2 the Ising heat bath on the q-th degree
@@ -917,8 +918,6 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int lj = tid % RW, li0 = tid / RW;                 // load / store mapping: column, first row
-  const int pc = (tid % Cfg::PAIRS) * 2;                   // scan mapping: column pair ...
-  const int rbase = 1 + Cfg::ROWS * (tid / Cfg::PAIRS);    // ... and first row of its band
   unsigned long long scanned = 0, enabled = 0, rounds_done = 0, events_total = 0;
 
   for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
@@ -1016,13 +1015,33 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     const unsigned long long t2 = L.t2;
     const uint32_t two = L.two, seed_lo = L.seed_lo, seed_hi = L.seed_hi;
     const unsigned* __restrict__ rates = L.rates;
-    constexpr unsigned kEven = 0x55555555u, kOdd = 0xAAAAAAAAu;
     constexpr int W = Cfg::W;
     const int qn = (MODEL == 2) ? L.q : 1;     // rings lost per round
-    // order planes serve the 4-neighbour array, the Moore automaton and the q = 2 diamond
-    // (q = 3 scans its keys directly: its 12 edge directions would not fit two CTAs per SM)
-    const bool planes = MODEL != 2 || qn == 2;
-    if (planes) {
+    // the q = 3 diamond has its own 13 planes and runs on the 128-wide region only (the
+    // host routes it there); a 96-wide launch of it is refused, uniformly per CTA
+    const bool q3 = MODEL == 2 && qn == 3;
+    if (q3 && RW != 128) {
+      if (tid == 0) atomicCAS(&ctr->error, 0, 1 /* AC_ERR_ARG */);
+      break;
+    }
+    unsigned* OQ = OH;   // plane d of the q = 3 diamond at OQ + d * RW * W, LV at d = 12
+    if (q3) {
+      for (int i = li0; i < RW; i += Cfg::LSTRIDE) {
+        const unsigned long long kc = K[i * RW + lj];
+        const unsigned gc = edge ? rowoff[i] + colg[lj] : 0u;
+#pragma unroll
+        for (int d = 0; d < 12; ++d) {
+          const int dr = q3_dr(d), dc = q3_dc(d);
+          const unsigned long long kn = K[(i + dr) * RW + lj + dc];
+          const bool pr = edge ? precedes_exact(kc, gc, kn, rowoff[i + dr] + colg[lj + dc]) : (kc & ~1ull) <= kn;
+          const unsigned b = __ballot_sync(kFull, pr);
+          if (lane == 0) OQ[d * RW * W + i * W + (lj >> 5)] = b;
+        }
+        const unsigned lb = __ballot_sync(kFull, kc < t2);
+        if (lane == 0) OQ[12 * RW * W + i * W + (lj >> 5)] = lb;
+      }
+      __syncthreads();
+    } else {
       // order planes of the loaded region; a warp covers 32 consecutive columns of one
       // row.  Relations with cells outside the loaded rectangle are never read (the
       // reads past the region's last row and column stay inside shared memory).
@@ -1089,7 +1108,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       unsigned mask = 0;
       // the word scanned by this thread (4-neighbour array): row oi, columns 32 ow ...
       const int oi = tid / W, ow = tid % W;
-      if (planes) {
+      {
         if (oi < RW && oi >= kk && oi < RH - kk) {
           const int lo = max(kk - 32 * ow, 0), hi = min(RC - kk - 32 * ow, 32);
           if (hi > lo) {
@@ -1103,27 +1122,28 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
               const unsigned swu = (OSW[wu] >> 1) | (ow + 1 < W ? (OSW[wu + 1] << 31) : 0u);
               m &= OSE[wi] & OSW[wi] & ~seu & ~swu;
             }
-            if (MODEL == 2) {   // q = 2: H2 of the cell two to the left, V2 of the cell two above
+            if (MODEL == 2 && !q3) {   // q = 2: H2 of the cell two to the left, V2 of the cell two above
               const unsigned h2 = OH2[wi];
               const unsigned h2l = (h2 << 2) | (ow > 0 ? (OH2[wi - 1] >> 30) : 0u);
               m &= h2 & ~h2l & OV2[wi] & ~OV2[wu - W];
+            }
+            if (q3) {   // the q = 3 diamond: its own planes, each against the cell d back
+              m = OQ[12 * RW * W + wi] & cm;
+#pragma unroll
+              for (int d = 0; d < 12; ++d) {
+                const int dr = q3_dr(d), dc = q3_dc(d);
+                const unsigned* P = OQ + d * RW * W;
+                const int wb = wi - dr * W;
+                unsigned back = P[wb];
+                if (dc > 0) back = (back << dc) | (ow > 0 ? (P[wb - 1] >> (32 - dc)) : 0u);
+                if (dc < 0) back = (back >> -dc) | (ow + 1 < W ? (P[wb + 1] << (32 + dc)) : 0u);
+                m &= P[wi] & ~back;
+              }
             }
             mask = m;
             scanned += (unsigned long long)__popc(cm);
           }
         }
-      }
-      const unsigned colm = ((pc >= kk && pc < RC - kk) ? kEven : 0u) | ((pc + 1 >= kk && pc + 1 < RC - kk) ? kOdd : 0u);
-      const int rlo = max(kk - rbase, 0), rhi = min(RH - kk - rbase, Cfg::ROWS);
-      unsigned rowm = 0u;
-      if (rhi > rlo) {
-        const unsigned hi_bits = (2 * rhi >= 32) ? 0xFFFFFFFFu : ((1u << (2 * rhi)) - 1u);
-        rowm = hi_bits & ~((1u << (2 * rlo)) - 1u);
-      }
-      const unsigned valid = planes ? 0u : colm & rowm;
-      if (MODEL == 2 && valid) {
-        mask = q_scan_exact<RW, Cfg::ROWS>(K, rowoff, colg, rbase, pc, t2, qn) & valid;
-        scanned += (unsigned long long)__popc(valid);
       }
       // exclusive prefix of the per-lane counts by an inclusive warp scan
       const int cnt = __popc(mask);
@@ -1143,8 +1163,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const int b = __ffs(mask) - 1;
         mask &= mask - 1;
         if (off < Cfg::LIST)
-          list[off] = planes ? (unsigned short)((oi << 8) | (32 * ow + b))
-                                 : (unsigned short)(((rbase + (b >> 1)) << 8) | (pc + (b & 1)));
+          list[off] = (unsigned short)((oi << 8) | (32 * ow + b));
         ++off;
       }
       __syncthreads();
@@ -1216,7 +1235,10 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         } else if (MODEL == 1) {
           moore_order_update<RW, false>(OH, OV, OL, OSE, OSW, OH2, OV2, ra, ca, nka, gia, kpa, edge, rowoff, colg, t2);
           moore_order_update<RW, false>(OH, OV, OL, OSE, OSW, OH2, OV2, rb, cb, nkb, gib, kpb, edge, rowoff, colg, t2);
-        } else if (planes) {   // the q = 2 diamond
+        } else if (q3) {
+          q3_order_update<RW>(OQ, ra, ca, nka, gia, kpa, edge, rowoff, colg, t2);
+          q3_order_update<RW>(OQ, rb, cb, nkb, gib, kpb, edge, rowoff, colg, t2);
+        } else {   // the q = 2 diamond
           moore_order_update<RW, true>(OH, OV, OL, OSE, OSW, OH2, OV2, ra, ca, nka, gia, kpa, edge, rowoff, colg, t2);
           moore_order_update<RW, true>(OH, OV, OL, OSE, OSW, OH2, OV2, rb, cb, nkb, gib, kpb, edge, rowoff, colg, t2);
         }
@@ -1259,7 +1281,9 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         if (MODEL == 0) order_update(OH, OV, OL, W, r, cc, nk, nl, nr, nu, nd, t2);
         if (MODEL == 1)
           moore_order_update<RW, false>(OH, OV, OL, OSE, OSW, OH2, OV2, r, cc, nk, gidx, kp, edge, rowoff, colg, t2);
-        else if (MODEL == 2 && planes)
+        else if (MODEL == 2 && q3)
+          q3_order_update<RW>(OQ, r, cc, nk, gidx, kp, edge, rowoff, colg, t2);
+        else if (MODEL == 2)
           moore_order_update<RW, true>(OH, OV, OL, OSE, OSW, OH2, OV2, r, cc, nk, gidx, kp, edge, rowoff, colg, t2);
         if (FR && r >= D && r < D + g.h && cc >= D && cc < D + g.w)
           write_frames(*fv, gidx, key >> 1, nk >> 1, (unsigned)nk & 1u);
