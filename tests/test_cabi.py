@@ -57,3 +57,37 @@ def test_null_handles_are_rejected(ac):
             fn(*args)
         assert ei.value.status == ac.ac.AC_ERR_ARG
     ac.ac_destroy(0)
+
+
+def test_model_and_frame_entry_points_reject_bad_arguments(ac):
+    """Argument checks of the model, frame, rate, class and time-model calls (all run
+    before any device work)."""
+    ERR = ac.ac.AC_ERR_ARG
+    bad_calls = [
+        (ac.ac_create_q, (16, 16, 0, 0.4, 1.0, 0.0, 1, 1)),          # q = 1 is ac_create
+        (ac.ac_create_q, (16, 16, 0, 0.4, 1.0, 0.0, 4, 1)),          # q above 3
+        (ac.ac_create_q, (7, 8, 0, 0.4, 1.0, 0.0, 2, 1)),            # rows < 4q
+        (ac.ac_create_q, (16, 16, 0, -1.0, 1.0, 0.0, 2, 1)),         # beta < 0
+        (ac.ac_create_life, (3, 10, 0, 0, 8, 12, 1)),                # rows < 4
+        (ac.ac_create_life, (10, 10, 0, 0, 1 << 9, 12, 1)),          # 10-bit birth mask
+        (ac.ac_time_model, (0, 64, ac.AC_LAW_EXP, 1, 10, 4)),        # dims 0
+        (ac.ac_time_model, (4, 64, ac.AC_LAW_EXP, 1, 10, 4)),        # dims 4
+        (ac.ac_time_model, (1, 1, ac.AC_LAW_EXP, 1, 10, 4)),         # n < 2
+        (ac.ac_time_model, (1, 64, 3, 1, 10, 4)),                    # unknown law
+        (ac.ac_time_model, (1, 64, ac.AC_LAW_EXP, 1, -1, 4)),        # t_end < 0
+        (ac.ac_time_model, (3, 1 << 11, ac.AC_LAW_EXP, 1, 10, 4)),   # n^3 >= 2^32 cells
+        (ac.ac_frames_configure, (0, 1 << 32, 0, 4)),                # null handle
+        (ac.ac_frames_status, (0,)),
+        (ac.ac_set_rates, (0, None)),
+        (ac.ac_class_counts, (0,)),
+        (ac.ac_run_until_ticks, (0, 1)),
+        (ac.ac_read_state, (0, None, None, None)),
+        (ac.ac_batch_create, ([], [], [], [], [])),                  # empty batch
+    ]
+    for fn, args in bad_calls:
+        with pytest.raises(ac.ACError) as ei:
+            fn(*args)
+        assert ei.value.status == ERR, (fn.__name__, args)
+    with pytest.raises(ac.ACError) as ei:
+        ac.ac_time_model(1, 64, ac.AC_LAW_EXP, 1, 10, 4, q=9)        # radius above 8
+    assert ei.value.status == ERR
