@@ -61,7 +61,7 @@ __device__ __forceinline__ Philox4 philox_event(uint32_t c0, uint32_t c1, uint32
 //   when the bit is set);  gap = floor(((33 - k) * 2^32 - f) * ln2 * 2^64 / 2^64) + 1.
 //
 // Pipe balance (measured with the exp_ticks probe on a GB300): the 32x32->64 square
-// (IMAD.WIDE) occupies the FMA-heavy pipe for several cycles, so the step's other
+// occupies the FMA-heavy pipe for several cycles, so the step's other
 // work is split: the shift amount 31 + bit comes from the integer ALU (a shift and
 // an add), the funnel shift is an ALU op, and the accumulation f' = 2 f' + amt is a
 // multiply-add on the FMA pipe -- `two` must hold 2 at run time but be opaque to the
