@@ -340,7 +340,8 @@ ac_status accumulate(ac_sim* s, const ac::DevCounters& c, float ms, bool round_k
     s->launches += 1;
   }
   if (c.error == AC_ERR_STALL) return fail(AC_ERR_STALL, "device watchdog: no progress (block %d)", c.err_block);
-  if (c.error) return fail((ac_status)c.error, "device reported error %d (count window)", c.error);
+  if (c.error == AC_ERR_STATE) return fail(AC_ERR_STATE, "device: event counts left the 16-bit window of a region");
+  if (c.error) return fail((ac_status)c.error, "device reported error %d (a q = 3 launch on a 96-wide region)", c.error);
   return AC_OK;
 }
 
