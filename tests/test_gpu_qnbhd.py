@@ -25,6 +25,7 @@ CASES = [
     (33, 47, 2, 0.3, 0.1, 3, 4, 0),
     (96, 130, 3, 0.15, -0.05, 4, 3, 1),
     (300, 250, 2, 0.25, 0.0, 5, 2, 0),
+    (300, 260, 3, 0.2, 0.0, 6, 2, 0),       # q = 3 with interior (non-wrapping) regions
 ]
 
 
