@@ -2,9 +2,9 @@
 
 Each case copies ac_oracle.c, plants one mistake (a dropped term, a wrong
 sign, a wrong index, a transposed operand, a reversed tie-break, swapped
-random words, a broken logarithm step), compiles the mutant with gcc and
-runs the pin that should reject it with the mutant loaded in place of the
-real oracle.  The mutants live in a temporary directory; the committed
+random words, a broken logarithm step, a threshold rounded instead of
+floored), compiles the mutant with gcc and runs the pin that should reject it
+with the mutant loaded in place of the real oracle.  The mutants live in a temporary directory; the committed
 oracle is never modified.
 """
 import ctypes
@@ -39,6 +39,10 @@ MUTANTS = {
     "philox_words_swapped": ("uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;",
                              "uint32_t n0 = (uint32_t)(p1 >> 32) ^ c3 ^ k0;",
                              lambda: phx.test_philox_matches_triton(7)),
+    "threshold_rounded": ("t = (uint32_t)floor(v);", "t = (uint32_t)floor(v + 0.5);",
+                          thr.test_table_is_the_floor_of_the_exact_probability),
+    "q_threshold_rounded": ("(uint32_t)floor(v) : 0xFFFFFFFFu", "(uint32_t)floor(v + 0.5) : 0xFFFFFFFFu",
+                            lambda: thr.test_q_table_is_the_floor_of_the_exact_probability(2)),
     "log_bit_dropped": ("f |= 1ull;", "f |= 0ull;", ext.test_exp_ticks_error_bound_and_positivity),
     "first_gap_from_init_block": ("philox_block(seed, (uint32_t)c, 0u, 0u, b0);\n        if (init == 1)\n            s[c] = 1;\n        else if (init == 2)\n            s[c] = -1;\n        else {\n            philox_block(seed, (uint32_t)c, 0u, 1u, ib);\n            s[c] = (ib[0] & 1u)",
                                   "philox_block(seed, (uint32_t)c, 0u, 1u, b0);\n        if (init == 1)\n            s[c] = 1;\n        else if (init == 2)\n            s[c] = -1;\n        else {\n            philox_block(seed, (uint32_t)c, 0u, 1u, ib);\n            s[c] = (ib[0] & 1u)",

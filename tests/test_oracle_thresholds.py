@@ -77,3 +77,76 @@ def test_class_counts_by_brute_force():
             j = sum(1 for d in nb if st.s[d] > 0)
             want[j + 5 * (1 if st.s[c] > 0 else 0)] += 1
         assert np.array_equal(_o.class_counts(st), want)
+
+
+# ---- the quantisation step against the exact heat-bath probability ----------
+#
+# The table is thr = min(floor(p 2^32), 2^32 - 1) with p = 1 / (1 + exp(beta dE))
+# (appendix flip probability, Sec. 2 Eq. (1) heat-bath rule).  The decimal module
+# evaluates p at 60 significant digits from the exact binary values of beta, J
+# and h, so floor(p 2^32) is known exactly wherever p 2^32 is not within the
+# binary64 evaluation error (a few 1e-6 ticks) of an integer.  A rounding or
+# ceiling quantisation fails on about half of the entries.
+
+def _exact_table(beta, J, h, M):
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    b, j_, h_ = Decimal(beta), Decimal(J), Decimal(h)
+    two32 = Decimal(2) ** 32
+    out = []
+    for sp in (0, 1):
+        s = 1 if sp else -1
+        for j in range(M + 1):
+            S = 2 * j - M
+            p = 1 / (1 + (b * 2 * s * (j_ * S + h_)).exp())
+            out.append(p * two32)
+    return out
+
+
+GRID = [(0.44, 1.0, 0.0), (0.4407, 1.0, 0.0), (0.3, 1.0, 0.0), (0.6, 1.0, 0.0), (1.0, 1.0, 0.05),
+        (0.25, -1.0, 0.4), (0.6, 0.7, -0.2), (0.37, 1.3, 0.11), (0.05, 1.0, -0.9), (2.0, 0.5, 0.01)]
+
+
+def _check_against_exact(thr, exact):
+    checked = above_half = 0
+    for got, v in zip(thr.tolist(), exact):
+        fl = int(v)                                      # v > 0: int() is floor
+        frac = float(v - fl)
+        if frac < 1e-5 or frac > 1 - 1e-5:              # binary64 may land on either side
+            assert got in (fl - 1, fl, fl + 1)
+            continue
+        assert got == min(fl, 2**32 - 1), (got, v)
+        checked += 1
+        above_half += frac > 0.5
+    return checked, above_half
+
+
+def test_table_is_the_floor_of_the_exact_probability():
+    checked = above_half = 0
+    for beta, J, h in GRID:
+        c, a = _check_against_exact(oracle.thresholds(beta, J, h), _exact_table(beta, J, h, 4))
+        checked += c
+        above_half += a
+    assert checked >= 80 and above_half >= 10      # the grid does exercise the quantisation
+
+
+def test_beta_044_table_printed_values():
+    """beta = 0.44, J = 1, h = 0, spin -1 with j up neighbours: floor(2^32 p) for
+    p = 1 / (1 + exp(-0.88 S)), S = 2j - 4, evaluated at 60 digits; spin +1 mirrors it."""
+    want = [123473849, 630459708, 2147483648, 3664507587, 4171493446]
+    thr = oracle.thresholds(0.44, 1.0, 0.0)
+    assert thr[0:5].tolist() == want and thr[5:10].tolist() == want[::-1]
+    assert oracle.thresholds_q(0.44, 1.0, 0.0, 1).tolist() == thr.tolist()
+    exact = _exact_table(0.44, 1.0, 0.0, 4)
+    assert [int(v) for v in exact[:5]] == want
+
+
+@pytest.mark.parametrize("q", [1, 2, 3])
+def test_q_table_is_the_floor_of_the_exact_probability(q):
+    M = 2 * q * (q + 1)
+    checked = above_half = 0
+    for beta, J, h in GRID[:6]:
+        c, a = _check_against_exact(oracle.thresholds_q(beta, J, h, q), _exact_table(beta, J, h, M))
+        checked += c
+        above_half += a
+    assert checked >= 0.8 * 6 * 2 * (M + 1) and above_half >= 5
