@@ -83,6 +83,21 @@ typedef struct {
 ac_status ac_create(ac_lattice lat, double beta, double J, double h, uint64_t seed, ac_sim** out);
 
 /*
+ * Create the Ising array on the q-th degree neighbourhood of Sec. 3 (q = 2 or 3):
+ * every cell within Manhattan distance q is a neighbour, M = 2q(q+1) of them.  The
+ * heat-bath rule of ac_create uses S = the sum of their spins, i.e. the table
+ * p = 1/(1 + exp(beta dE)), dE = 2 s (J S + h), thr = min(floor(p 2^32), 2^32 - 1),
+ * index j + (M+1)(s > 0) for j up neighbours; a cell may commit once its
+ * (tick, index) key is below all M neighbours' keys.  Initial state and arrivals
+ * as for ac_create.  Needs rows, cols >= 4q.  Runs on the round kernel only
+ * (temporal blocking, the region losing q rings per round; rounds per launch
+ * capped at 16 / q and min(rows, cols) / (4q), default 6); not in batches; no
+ * per-cell rates.  Observables of ac_stats keep the nearest-neighbour bonds.
+ * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
+ */
+ac_status ac_create_q(ac_lattice lat, double beta, double J, double h, int32_t q, uint64_t seed, ac_sim** out);
+
+/*
  * Create an asynchronous Life-like automaton instead of the Ising array: the
  * deterministic update of Sec. 3 (Conway's Game of Life is the paper's example)
  * under the same Poisson asynchrony, arrivals and random streams.  At an arrival
@@ -99,21 +114,6 @@ ac_status ac_create(ac_lattice lat, double beta, double J, double h, uint64_t se
  * launch capped at min(rows, cols) / 4, default 6); not in batches.
  * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
  */
-/*
- * Create the Ising array on the q-th degree neighbourhood of Sec. 3 (q = 2 or 3):
- * every cell within Manhattan distance q is a neighbour, M = 2q(q+1) of them.  The
- * heat-bath rule of ac_create uses S = the sum of their spins, i.e. the table
- * p = 1/(1 + exp(beta dE)), dE = 2 s (J S + h), thr = min(floor(p 2^32), 2^32 - 1),
- * index j + (M+1)(s > 0) for j up neighbours; a cell may commit once its
- * (tick, index) key is below all M neighbours' keys.  Initial state and arrivals
- * as for ac_create.  Needs rows, cols >= 4q.  Runs on the round kernel only
- * (temporal blocking, the region losing q rings per round; rounds per launch
- * capped at 16 / q and min(rows, cols) / (4q), default 6); not in batches; no
- * per-cell rates.  Observables of ac_stats keep the nearest-neighbour bonds.
- * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.
- */
-ac_status ac_create_q(ac_lattice lat, double beta, double J, double h, int32_t q, uint64_t seed, ac_sim** out);
-
 #define AC_LIFE_CONWAY_BIRTH (1u << 3)
 #define AC_LIFE_CONWAY_SURVIVE ((1u << 2) | (1u << 3))
 ac_status ac_create_life(ac_lattice lat, uint32_t density, uint32_t birth, uint32_t survive, uint64_t seed,
@@ -130,9 +130,13 @@ ac_status ac_set_stream(ac_sim* sim, void* cuda_stream);
  *   rounds  round kernel: synchronous rounds per launch.  1 = one global round of
  *           Fig. 3.2 per launch, with per-round enabled counts (ac_round_history).
  *           2..16 = temporal blocking: each CTA loads its tile with a halo of depth
- *           `rounds` into a 128 x 128 shared-memory region and runs `rounds` exact
- *           synchronous rounds per launch (tile side 128 - 2*rounds, Lb unused;
- *           needs rows, cols >= 4*rounds, otherwise Lb-tiles with frozen halos).
+ *           `rounds` into a shared-memory region and runs `rounds` exact
+ *           synchronous rounds per launch.  The region is 96 x 96 for rounds <= 12
+ *           (two CTAs per SM) and 128 x 128 for 13..16 (one CTA per SM); the tile
+ *           side is the region side - 2*rounds and Lb is unused.  Needs rows,
+ *           cols >= 4*rounds; otherwise Lb-tiles with frozen halos run `rounds`
+ *           rounds per launch.  When the lattice's counts are too uneven for the
+ *           kernel's 16-bit count window, the call runs one round per launch.
  *           Blocked kernel: halo refresh period in rounds (>= 1).
  *   polls   blocked kernel: halo polls before a blocked tile is left (>= 0)
  * The trajectory does not depend on any of these (Sec. 3, invariance of the
@@ -324,21 +328,32 @@ ac_status ac_thresholds(double beta, double J, double h, uint32_t thr[10]);
  * Batching.  ac_batch_create makes n independent simulations (arrays of n
  * lattices and parameters; seeds distinguish lattices, the counter carries no
  * lattice id) into out[0..n-1], each usable with every call above.
- * ac_batch_run_until advances sims[0..n-1] to t_end[i] each in ONE persistent
- * blocked-kernel launch over all their tiles, replayed from a CUDA graph that is
- * captured on the first call for that exact list of handles.  All handles must
- * share the stream of sims[0] and a tile side.  Results are bit-identical to
- * running each handle alone.  Errors as for ac_run_until_ticks.
+ * ac_batch_run_until advances sims[0..n-1] to t_end[i] each.  When every handle
+ * is configured for the round kernel with the same rounds per launch (>= 2) and
+ * fits temporal blocking, one work list holds the tiles of all handles and each
+ * temporal-blocked launch advances all of them; launches are issued in chunks of
+ * 8, replayed from a CUDA graph captured on the second call with the same list
+ * of handles, and the host reads the device counters after each chunk to see
+ * whether any arrival before t_end is left.  Otherwise the handles run in ONE
+ * cooperative blocked-kernel launch over all their tiles (tile side Lb of
+ * sims[0]), replayed from a CUDA graph captured on the first call for that list
+ * of handles.  All handles must share the stream of sims[0] and a tile side;
+ * only the 4-neighbour Ising array, without snapshot frames.  Results are
+ * bit-identical to running each handle alone.  Errors as for
+ * ac_run_until_ticks.
  */
 ac_status ac_batch_create(int32_t n, const ac_lattice* lats, const double* beta, const double* J,
                           const double* h, const uint64_t* seed, ac_sim** out);
 ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_end);
 
 /*
- * Run without allocating.  The paper has no counterpart to this entry point; it
- * exists for callers that cannot let the library call cudaMalloc: code that
- * runs while a CUDA graph is being captured, applications whose allocator owns
- * all device memory, or hosts that give the library a fixed device budget.
+ * Run without allocating.  The paper has no counterpart to this entry point.  It
+ * serves callers that cannot let the library call cudaMalloc: applications whose
+ * own memory pool has reserved the device's memory up front (a cudaMalloc from
+ * the library would fail or fragment that pool), hosts that grant a plugin a
+ * fixed device budget and account for every byte of it, and loops that must not
+ * call cudaMalloc or cudaFree at all because those calls can synchronise the
+ * whole device.
  *
  * Advances the lattice stored in the caller's DEVICE buffers to t_end with the
  * blocked persistent kernel (tile side 64), bit-identical to ac_run_until_ticks
@@ -351,12 +366,16 @@ ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_en
  * which every GPU that loads the library holds until the process exits.  The
  * call allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every call
- * shares the array and clears what must start at zero, so calls whose GPU work
- * overlaps (other streams, other threads) race and must not be issued.  The call
- * is synchronous.  Errors: AC_ERR_ARG (bad arguments, or a lattice needing more
- * scratch than the maximum: about 2000 tiles of 64 x 64, e.g. 2816 x 2816),
- * AC_ERR_STALL, AC_ERR_CUDA.
+ * device current) and caches it for the process; make that first call before any
+ * stream capture.  The cached address does not survive cudaDeviceReset or the
+ * destruction of the device's primary context: after either, do not call this
+ * entry point again in the same process.  Every call shares the array and clears
+ * what must start at zero, so calls whose GPU work overlaps (other streams, other
+ * threads) race and must not be issued.  The call is synchronous: it waits for
+ * its GPU work on `stream` and reads the device counters back before returning.
+ * Errors: AC_ERR_ARG (bad arguments, or a lattice needing more scratch than the
+ * maximum: about 2000 tiles of 64 x 64, e.g. 2816 x 2816), AC_ERR_STALL,
+ * AC_ERR_CUDA.
  */
 #define AC_STATIC_SCRATCH_BYTES (4u << 20)
 ac_status ac_run_blocked_static(int32_t rows, int32_t cols, double beta, double J, double h,

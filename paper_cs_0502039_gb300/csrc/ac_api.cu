@@ -46,6 +46,14 @@ ac_status fail(ac_status st, const char* fmt, ...) {
 constexpr double kTicksPerUnit = 4294967296.0;
 constexpr long long kTickLimit = 1ll << 61;
 
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+namespace ac {
+// Lets other translation units of the library report through ac_last_error().
+void set_last_error(const char* msg) { g_err = msg; }
+
 // Heat-bath thresholds: p = 1/(1 + exp(beta dE)), dE = 2 s (J S + h);
 // thr = min(floor(p * 2^32), 2^32 - 1), index j + 5*(s > 0), S = 2j - 4.
 void make_thresholds(double beta, double J, double h, uint32_t thr[10]) {
@@ -61,13 +69,6 @@ void make_thresholds(double beta, double J, double h, uint32_t thr[10]) {
   }
 }
 
-int ceil_div(int a, int b) { return (a + b - 1) / b; }
-
-}  // namespace
-
-namespace ac {
-// Lets other translation units of the library report through ac_last_error().
-void set_last_error(const char* msg) { g_err = msg; }
 }  // namespace ac
 
 struct ac_sim {
@@ -293,7 +294,7 @@ ac_status create_one(ac_lattice lat, double beta, double J, double h, uint64_t s
   s->cfg.refresh = 1;
   s->cfg.max_rounds = 0;
   s->cfg.watchdog_ns = 5ll * 1000 * 1000 * 1000;
-  make_thresholds(beta, J, h, s->thr);
+  ac::make_thresholds(beta, J, h, s->thr);
   const size_t N = s->ncells();
   if (cudaMalloc(&s->key, N * 8) != cudaSuccess || cudaMalloc(&s->cnt, N * 4) != cudaSuccess ||
       cudaMalloc(&s->d_events, 8) != cudaSuccess || cudaMalloc(&s->d_desc, sizeof(ac::LatDesc)) != cudaSuccess ||
@@ -900,7 +901,7 @@ ac_status ac_thresholds(double beta, double J, double h, uint32_t thr[10]) {
   if (!thr) return fail(AC_ERR_ARG, "thr is NULL");
   if (!(beta >= 0.0) || !std::isfinite(beta) || !std::isfinite(J) || !std::isfinite(h))
     return fail(AC_ERR_ARG, "beta must be finite and >= 0; J, h finite");
-  make_thresholds(beta, J, h, thr);
+  ac::make_thresholds(beta, J, h, thr);
   return AC_OK;
 }
 

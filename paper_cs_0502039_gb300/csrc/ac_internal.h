@@ -100,6 +100,10 @@ struct LaunchCfg {
 // Sets the thread-local message returned by ac_last_error() (ac_api.cu).
 void set_last_error(const char* msg);
 
+// Heat-bath threshold table of the 4-neighbour Ising array (appendix flip
+// probabilities; ac_api.cu), shared by every entry point of the library.
+void make_thresholds(double beta, double J, double h, uint32_t thr[10]);
+
 // ---- launchers (ac_kernels.cu) -------------------------------------------------
 size_t tile_smem_bytes(int lb);
 int blocked_max_ctas(int lb, int* per_sm);   // resident CTAs of the blocked kernel

@@ -1,12 +1,15 @@
 // ac_static.cu -- a run entry point that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA graph that is
-// being captured or replayed, allocators that forbid outside allocations, or
-// hosts that hand this library a fixed device budget and nothing else.  For them
+// Some callers cannot let a library call cudaMalloc: applications whose own memory
+// pool reserved the device's memory up front, hosts that give a plugin a fixed
+// device budget and nothing else, and loops that must not call cudaMalloc or
+// cudaFree because those calls can synchronise the device.  For them
 // ac_run_blocked_static() advances a lattice held in the caller's own device
 // buffers with the blocked persistent kernel, and keeps every other buffer the
 // kernel needs (lattice descriptor, counters, tile flags, edge words) in one
 // file-scope device array of fixed size, reserved when the library is loaded.
+// The array's device address is looked up once per device and cached for the
+// process; the cache does not survive cudaDeviceReset.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,18 +54,6 @@ ac_status fail_static(ac_status st, const char* fmt, ...) {
     if (e_ != cudaSuccess)                                                                    \
       return fail_static(AC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
   } while (0)
-
-// Heat-bath thresholds, as for every other entry point of the library.
-void static_thresholds(double beta, double J, double h, uint32_t thr[10]) {
-  for (int up = 0; up < 2; ++up) {
-    const double s = up ? 1.0 : -1.0;
-    for (int j = 0; j < 5; ++j) {
-      const double dE = 2.0 * s * (J * (double)(2 * j - 4) + h);
-      const double v = std::ldexp(1.0 / (1.0 + std::exp(beta * dE)), 32);
-      thr[j + 5 * up] = (v < 4294967295.0) ? (uint32_t)std::floor(v) : 0xFFFFFFFFu;
-    }
-  }
-}
 
 }  // namespace
 
@@ -125,7 +116,7 @@ extern "C" ac_status ac_run_blocked_static(int32_t rows, int32_t cols, double be
   d.tc = tc;
   d.lb = kStaticLb;
   d.tile_base = 0;
-  static_thresholds(beta, J, h, d.thr);
+  ac::make_thresholds(beta, J, h, d.thr);
   d.seed_lo = (unsigned)(seed & 0xffffffffu);
   d.seed_hi = (unsigned)(seed >> 32);
   d.t_end = t_end;

@@ -17,7 +17,12 @@ def rank_env() -> tuple[int, int, int]:
 
 
 def replica_seed(seed: int, rank: int) -> int:
-    return int(seed) + 1000 * int(rank)
+    """Seed of `rank`'s replica: the rank in bits 48..63, the seed below them, so that
+    distinct (seed, rank) pairs never share a random stream (seed < 2^48, rank < 2^16)."""
+    seed, rank = int(seed), int(rank)
+    if not (0 <= seed < (1 << 48) and 0 <= rank < (1 << 16)):
+        raise ValueError("replica seeds need 0 <= seed < 2^48 and 0 <= rank < 2^16")
+    return (rank << 48) | seed
 
 
 def shard(items, rank: int, world: int):

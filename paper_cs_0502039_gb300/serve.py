@@ -10,8 +10,12 @@ budget, so requests that arrive while others run join the next step.  Every resu
 the request's exact trajectory: lattices are independent and their trajectories do not
 depend on the schedule.
 
-Footprint of a resident lattice: 12 bytes per cell of state, twice (the round kernel's
-ping-pong buffers), plus a small per-tile overhead.
+Footprint of a resident lattice (footprint_bytes): 12 bytes per cell of state, twice
+(the round kernel's ping-pong buffers), the two sets of edge words of the tiling
+(4 Lb words per tile each), the round history of one-round-per-launch runs, and a
+2 MiB allowance for each of the handle's device allocations.  If a creation still
+fails for lack of device memory, the request goes back to the head of the queue and
+waits until resident lattices retire.
 """
 from __future__ import annotations
 
@@ -30,8 +34,16 @@ def now_wall() -> float:
     return time.perf_counter() - _T0[0]
 
 
-def footprint_bytes(rows: int, cols: int) -> int:
-    return 24 * rows * cols + 4096
+_ALLOC_SLACK = 2 << 20          # per device allocation of a handle
+_ALLOCS = 10                    # key, cnt, key2, cnt2, edge words (2), counters, events, tile flags, reductions
+_HISTORY = 1 << 19              # round history (512 KiB), only with one round per launch
+
+
+def footprint_bytes(rows: int, cols: int, Lb: int = 64, rounds: int = 8) -> int:
+    tiles = -(-rows // Lb) * -(-cols // Lb)
+    edges = 2 * tiles * 4 * Lb * 8
+    hist = _HISTORY if rounds == 1 else 0
+    return 24 * rows * cols + edges + hist + _ALLOCS * _ALLOC_SLACK
 
 
 @dataclass
@@ -74,7 +86,7 @@ class Server:
     events: int = 0
 
     def used(self) -> int:
-        return sum(footprint_bytes(j.sim.rows, j.sim.cols) for j in self.resident)
+        return sum(footprint_bytes(j.sim.rows, j.sim.cols, self.Lb, self.rounds) for j in self.resident)
 
     def submit(self, req: dict) -> None:
         self.waiting.append(req)
@@ -83,13 +95,18 @@ class Server:
         used = self.used()
         while self.waiting and len(self.resident) < self.max_batch:
             req = self.waiting[0]
-            need = footprint_bytes(req["rows"], req["cols"])
+            need = footprint_bytes(req["rows"], req["cols"], self.Lb, self.rounds)
             if self.resident and used + need > self.budget_bytes:
                 break
+            try:
+                sim = _ac.Sim(req["rows"], req["cols"], req["beta"], req.get("J", 1.0), req.get("h", 0.0),
+                              req["seed"], init=req.get("init", _ac.AC_INIT_RANDOM), kernel=self.kernel,
+                              Lb=self.Lb, rounds=self.rounds)
+            except _ac.ACError as e:
+                if e.status != _ac.AC_ERR_OOM or not self.resident:
+                    raise
+                break                   # the request stays first in the queue until lattices retire
             self.waiting.popleft()
-            sim = _ac.Sim(req["rows"], req["cols"], req["beta"], req.get("J", 1.0), req.get("h", 0.0), req["seed"],
-                          init=req.get("init", _ac.AC_INIT_RANDOM), kernel=self.kernel, Lb=self.Lb,
-                          rounds=self.rounds)
             self.resident.append(_Job(req, sim, int(req["T"] * TICKS), now))
             used += need
 

@@ -47,6 +47,14 @@ def test_two_ranks_gloo():
     assert r0[6] == list(range(11))                     # every lattice exactly once
 
 
+def test_replica_seeds_are_injective():
+    seen = {acdist.replica_seed(seed, rank) for seed in (0, 1, 999, 1000, 1001, (1 << 48) - 1) for rank in range(8)}
+    assert len(seen) == 6 * 8
+    assert acdist.replica_seed(7, 0) == 7
+    with pytest.raises(ValueError):
+        acdist.replica_seed(1 << 48, 0)
+
+
 def test_single_process_identity():
     assert acdist.reduce_run(3.5, 10) == (3.5, 10.0)
     assert acdist.shard([1, 2, 3], 0, 1) == [1, 2, 3]

@@ -1,12 +1,13 @@
 """The allocation-free run entry point gives the same lattice as the handle path.
 
 ac_run_blocked_static serves callers that cannot let the library allocate
-device memory (for example code running during CUDA graph capture, or an
-application whose own allocator owns the device).  It keeps its working buffers
-in a fixed file-scope device array.  This test feeds it a lattice held in
-torch-owned device buffers and compares, on two calls in a row, with a handle
-run through ac_run_until_ticks: bit-exact, the tolerance of every parity test
-here.  It also checks that a lattice too large for the fixed array is refused.
+device memory: an application whose own memory pool reserved the device up
+front, a host that gives the library a fixed device budget, or a loop that must
+not call cudaMalloc / cudaFree because they can synchronise the device.  It
+keeps its working buffers in a fixed file-scope device array.  This test feeds
+it a lattice held in torch-owned device buffers and compares, on two calls in a
+row, with a handle run through ac_run_until_ticks: bit-exact, the tolerance of
+every parity test here.  It also checks that a lattice too large for the fixed array is refused.
 """
 import numpy as np
 import pytest
