@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--kernel", default="round", choices=["blocked", "round"])
+    ap.add_argument("--kernel", default="round", choices=["blocked", "round", "epoch"])
     ap.add_argument("--lb", type=int, default=64)
     ap.add_argument("--rounds", type=int, default=8,
                     help="round kernel: synchronous rounds per launch (>1: temporal blocking); blocked: refresh")
@@ -222,6 +222,14 @@ def run_reference(args):
     return 0
 
 
+def kernel_id(ac, name):
+    return {"blocked": ac.AC_KERNEL_BLOCKED, "round": ac.AC_KERNEL_ROUND, "epoch": ac.AC_KERNEL_EPOCH}[name]
+
+
+def kernel_name(ac, kern):
+    return {ac.AC_KERNEL_BLOCKED: "blocked", ac.AC_KERNEL_ROUND: "round", ac.AC_KERNEL_EPOCH: "epoch"}[kern]
+
+
 def run_single(args):
     """One lattice (seed 7, random init, J = 1, h = 0) run to T with one kernel configuration:
     `warmup` untimed runs, then `steps` timed runs; reports the kernel's device time."""
@@ -230,7 +238,7 @@ def run_single(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_cs_0502039_gb300 as ac
-    kern = ac.AC_KERNEL_BLOCKED if args.kernel == "blocked" else ac.AC_KERNEL_ROUND
+    kern = kernel_id(ac, args.kernel)
     with ac.Sim(args.rows, args.cols, args.beta, 1.0, 0.0, 7, kernel=kern, Lb=args.lb, rounds=args.rounds,
                 polls=args.polls) as sim:
         for _ in range(args.warmup):
@@ -338,13 +346,13 @@ def main():
     import paper_cs_0502039_gb300 as ac
 
     w = WORKLOAD
-    kern = ac.AC_KERNEL_BLOCKED if args.kernel == "blocked" else ac.AC_KERNEL_ROUND
+    kern = kernel_id(ac, args.kernel)
     tuned = None
     if not args.no_autotune:
         from paper_cs_0502039_gb300 import autotune
         tuned = autotune.tune(w["rows"], w["cols"])
         kern, args.lb, args.rounds, args.polls = tuned["kernel"], tuned["Lb"], tuned["rounds"], tuned["polls"]
-        args.kernel = "blocked" if kern == ac.AC_KERNEL_BLOCKED else "round"
+        args.kernel = kernel_name(ac, kern)
     # weak scaling: every rank runs its own replica batch (seed offset by rank)
     from paper_cs_0502039_gb300.dist import replica_seed
     seed = replica_seed(w["seed"], rank)

@@ -64,7 +64,9 @@ typedef enum { AC_INIT_RANDOM = 0, AC_INIT_UP = 1, AC_INIT_DOWN = 2 } ac_init;
 
 typedef enum {
   AC_KERNEL_ROUND = 0,    /* (a) synchronous rounds, Fig. 3.2 */
-  AC_KERNEL_BLOCKED = 1   /* (b) blocked persistent kernel, Fig. 3.4 */
+  AC_KERNEL_BLOCKED = 1,  /* (b) blocked persistent kernel, Fig. 3.4: resident tiles, live edge words */
+  AC_KERNEL_EPOCH = 2     /* (b) blocked persistent kernel, Fig. 3.4 at tile granularity: temporal-
+                             blocked tiles ordered by per-tile epoch words in HBM */
 } ac_kernel;
 
 /* rows, cols >= 2 and rows * cols < 2^32. */
@@ -125,7 +127,7 @@ ac_status ac_set_stream(ac_sim* sim, void* cuda_stream);
 
 /*
  * Choose the kernel and its tuning for later run calls.
- *   kernel  AC_KERNEL_ROUND or AC_KERNEL_BLOCKED
+ *   kernel  AC_KERNEL_ROUND, AC_KERNEL_BLOCKED or AC_KERNEL_EPOCH
  *   Lb      tile side: 32, 64 or 128 (threads per CTA = 4 * Lb)
  *   rounds  round kernel: synchronous rounds per launch.  1 = one global round of
  *           Fig. 3.2 per launch, with per-round enabled counts (ac_round_history).
@@ -139,6 +141,17 @@ ac_status ac_set_stream(ac_sim* sim, void* cuda_stream);
  *           kernel's 16-bit count window, the call runs one round per launch.
  *           Blocked kernel: halo refresh period in rounds (>= 1).
  *   polls   blocked kernel: halo polls before a blocked tile is left (>= 0)
+ * AC_KERNEL_EPOCH takes `rounds` as the round kernel does (synchronous rounds per tile
+ * visit, the halo depth) and ignores Lb and polls.  It is one persistent launch per
+ * run call: each CTA claims (epoch, tile) work items in order; a tile's visit loads
+ * its region (tile plus halo) by bulk asynchronous copies, runs `rounds` rounds, writes
+ * the tile back and publishes the tile's epoch with a release store; a visit of epoch
+ * e starts once the tile and its 8 neighbour tiles have published epoch e (acquire
+ * loads, bounded polls, the AC_OPT_WATCHDOG_NS watchdog).  The aggregated algorithm
+ * of Fig. 3.4 with a tile per subarray and a tile's epoch as the local time its
+ * neighbours wait on.  Needs the 4-neighbour Ising array, even cols, even `rounds`
+ * (2..16) and rows, cols >= 4*rounds, and no snapshot frames; otherwise the handle
+ * runs on the round kernel with the same `rounds`.
  * The trajectory does not depend on any of these (Sec. 3, invariance of the
  * aggregated algorithm under re-partitioning); only the speed does.
  * Errors: AC_ERR_ARG, AC_ERR_OOM (edge-word reallocation), AC_ERR_CUDA.
@@ -304,13 +317,14 @@ ac_status ac_run_until_frames(ac_sim* sim, int64_t t_end, ac_frame_fn fn, void* 
 ac_status ac_frames_status(const ac_sim* sim, int64_t* next_K, int32_t* B, int64_t* dt_ticks);
 
 /* Tuning and verification options (ac_set_option):
- *   AC_OPT_WATCHDOG_NS   blocked kernel: no-progress limit in ns before the run
- *                        returns AC_ERR_STALL (default 5e9, >= 1e6)
+ *   AC_OPT_WATCHDOG_NS   blocked and epoch kernels: no-progress limit in ns before
+ *                        the run returns AC_ERR_STALL (default 5e9, >= 1e6)
  *   AC_OPT_MAX_ROUNDS    blocked kernel: cap on tile rounds per visit (0 = none)
  *   AC_OPT_DROP_PUBLISH  verification hook: 1 suppresses the publication of
- *                        boundary commits, so that a lattice of several tiles
- *                        cannot finish and the watchdog must end the run with
- *                        AC_ERR_STALL (no fault, no unbounded wait); 0 restores it. */
+ *                        boundary commits (blocked kernel) and of tile epochs (epoch
+ *                        kernel), so that a lattice of several tiles cannot finish
+ *                        and the watchdog must end the run with AC_ERR_STALL (no
+ *                        fault, no unbounded wait); 0 restores it. */
 enum { AC_OPT_WATCHDOG_NS = 1, AC_OPT_MAX_ROUNDS = 2, AC_OPT_DROP_PUBLISH = 3 };
 ac_status ac_set_option(ac_sim* sim, int32_t option, int64_t value);
 

@@ -6,7 +6,7 @@ Asynchronous Cellular Arrays".  The compute path is the hand-written sm_103a
 CUDA library ``libac.so`` behind the C ABI of ``include/ac.h``; :mod:`.ac` is
 its thin ctypes binding.
 """
-from .ac import (AC_INIT_DOWN, AC_INIT_RANDOM, AC_INIT_UP, AC_KERNEL_BLOCKED, AC_KERNEL_ROUND,  # noqa: F401
+from .ac import (AC_INIT_DOWN, AC_INIT_RANDOM, AC_INIT_UP, AC_KERNEL_BLOCKED, AC_KERNEL_EPOCH, AC_KERNEL_ROUND,  # noqa: F401
                  AC_LAW_EXP, AC_LAW_ROOT8, AC_LAW_UNIFORM, AC_LIFE_CONWAY_BIRTH, AC_LIFE_CONWAY_SURVIVE,
                  AC_MAX_FRAMES, AC_RATE_ONE, AC_OPT_DROP_PUBLISH, AC_OPT_MAX_ROUNDS, AC_OPT_WATCHDOG_NS, TICKS_PER_UNIT,
                  ACError, Sim, ac_batch_create, ac_class_counts, ac_create_life, ac_create_q, ising_q, life, ac_batch_run_until, ac_configure, ac_create, ac_destroy,

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libac.so")
 
 AC_OK, AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA, AC_ERR_STALL, AC_ERR_STATE = range(6)
 AC_INIT_RANDOM, AC_INIT_UP, AC_INIT_DOWN = 0, 1, 2
-AC_KERNEL_ROUND, AC_KERNEL_BLOCKED = 0, 1
+AC_KERNEL_ROUND, AC_KERNEL_BLOCKED, AC_KERNEL_EPOCH = 0, 1, 2
 AC_OPT_WATCHDOG_NS, AC_OPT_MAX_ROUNDS, AC_OPT_DROP_PUBLISH = 1, 2, 3
 TICKS_PER_UNIT = 1 << 32
 

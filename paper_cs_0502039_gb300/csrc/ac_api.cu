@@ -97,6 +97,8 @@ struct ac_sim {
   unsigned long long* d_hist = nullptr;     // enabled counts per synchronous round
   int hist_cap = 0;
   unsigned long long* d_red = nullptr;
+  unsigned int* d_ep = nullptr;             // epoch kernel: tile done words, per-epoch counts
+  size_t ep_cap = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   long long t_done = 0;
@@ -256,6 +258,7 @@ void free_sim(ac_sim* s) {
   cudaFree(s->d_tile_done);
   cudaFree(s->d_hist);
   cudaFree(s->d_red);
+  cudaFree(s->d_ep);
   cudaFree(s->frames);
   cudaFree(s->d_rates);
   if (s->frame_host) cudaFreeHost(s->frame_host);
@@ -465,6 +468,119 @@ ac_status run_tb(ac_sim* s, long long t_end, int D, int R) {
   }
   s->last_grid = std::min(total, ac::tb_grid(region));
   return accumulate(s, c, ms, true);
+}
+
+// Tile grid of the epoch kernel: as tb_tiling_batch (the fewest tiles of side <=
+// region - 2D, at least 2 per dimension), with columns tiled in pairs so that every
+// region row starts on an even column.  The sides stay >= D whenever rows, cols >= 4D,
+// so a region reaches into the 8 neighbour tiles only.
+void ep_tiling(int rows, int cols, int region, int halo, int* tr, int* tc) {
+  const int own = region - 2 * halo;
+  *tr = std::max(2, ceil_div(rows, own));
+  *tc = std::max(2, ceil_div(cols / 2, own / 2));
+}
+
+// The epoch kernel runs the 4-neighbour Ising array without frames, on even cols with
+// an even halo (its bulk row copies need 16-byte alignment) and rows, cols >= 4D.
+bool ep_applicable(const ac_sim* s) {
+  const int D = s->cfg.rounds;
+  return s->model == 0 && s->f_B == 0 && D >= 2 && (D & 1) == 0 && D <= ac::kTbMaxHalo && (s->cols & 1) == 0 &&
+         s->rows >= 4 * D && s->cols >= 4 * D;
+}
+
+// Epochs to run per launch: about 8.3 synchronous rounds per unit time (Sec. 4), D per
+// epoch, with a factor-2 margin; a launch that ends before its last epoch found
+// nothing left is followed by another one.
+int ep_epochs(double span, int D, int total) {
+  const double e = 2.0 * (9.0 * std::ceil(span) + 16.0) / D + 8.0;
+  const int cap = (int)std::min<long long>(4096, ((1ll << 31) - 1) / std::max(1, total) - 1);
+  return std::max(1, std::min(cap, (int)e));
+}
+
+ac_status ensure_ep_words(unsigned int** buf, size_t* cap, size_t words) {
+  if (words <= *cap) return AC_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  if (cudaMalloc(buf, words * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AC_ERR_OOM, "epoch kernel words: cudaMalloc of %zu bytes failed", words * 4);
+  }
+  *cap = words;
+  return AC_OK;
+}
+
+ac_status run_ep(ac_sim* s, long long t_end) {
+  const int D = s->cfg.rounds;
+  const size_t N = s->ncells();
+  if (!s->key2) {
+    if (cudaMalloc(&s->key2, N * 8) != cudaSuccess || cudaMalloc(&s->cnt2, N * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AC_ERR_OOM, "second state buffer (%zu cells) allocation failed", N);
+    }
+  }
+  const int region = ac::tb_region_for(D);
+  int tr = 0, tc = 0;
+  ep_tiling(s->rows, s->cols, region, D, &tr, &tc);
+  const int total = tr * tc;
+  const double span = (double)(t_end - s->t_done) / kTicksPerUnit;
+  const int E = ep_epochs(span, D, total);
+  ac_status st = ensure_ep_words(&s->d_ep, &s->ep_cap, (size_t)total + 2 * (size_t)E);
+  if (st != AC_OK) return st;
+  ac::EpArgs ep{};
+  ep.done = s->d_ep;
+  ep.ep_done = s->d_ep + total;
+  ep.ep_live = s->d_ep + total + E;
+  ep.max_epochs = E;
+  ep.watchdog_ns = s->cfg.watchdog_ns;
+  ac::DevCounters c0{};
+  c0.stop_epoch = ~0u;
+  ac::DevCounters sum{};
+  AC_CUDA(cudaEventRecord(s->ev0, s->stream));
+  long long epochs_total = 0;
+  for (int launch = 0;; ++launch) {
+    ac::LatDesc d = s->host_desc(t_end, 0);
+    d.tr = tr;
+    d.tc = tc;
+    d.cpair = 1;
+    AC_CUDA(cudaMemcpyAsync(s->d_desc, &d, sizeof d, cudaMemcpyHostToDevice, s->stream));
+    AC_CUDA(cudaMemcpyAsync(s->d_ctr, &c0, sizeof c0, cudaMemcpyHostToDevice, s->stream));
+    AC_CUDA(cudaMemsetAsync(s->d_ep, 0, ((size_t)total + 2 * (size_t)E) * 4, s->stream));
+    AC_CUDA(ac::launch_ep(s->d_desc, 1, total, region, D, D, s->d_ctr, ep, s->stream, 0));
+    ac::DevCounters c{};
+    AC_CUDA(cudaMemcpyAsync(&c, s->d_ctr, sizeof c, cudaMemcpyDeviceToHost, s->stream));
+    AC_CUDA(cudaStreamSynchronize(s->stream));
+    sum.events += c.events;
+    sum.rounds += c.rounds;
+    sum.scanned += c.scanned;
+    sum.enabled += c.enabled;
+    // every CTA's claims beyond its last item: exactly one that found nothing left
+    const int grid = (int)std::min<long long>((long long)total * E, ac::tb_grid(region));
+    sum.visits += c.next_item > (unsigned)grid ? c.next_item - (unsigned)grid : 0u;
+    sum.polls += c.polls;
+    sum.launched += 1;
+    if (c.error) {
+      sum.error = c.error;
+      sum.err_block = c.err_block;
+      break;
+    }
+    // the state after `done` epochs is in the second buffer when `done` is odd
+    const unsigned done = (c.stop_epoch != ~0u) ? c.stop_epoch : (unsigned)E;
+    if (done & 1u) {
+      std::swap(s->key, s->key2);
+      std::swap(s->cnt, s->cnt2);
+    }
+    epochs_total += done;
+    if (c.stop_epoch != ~0u) break;
+    if ((double)epochs_total * D > 64.0 * (9.0 * std::ceil(span) + 16.0) + 4096.0)
+      return fail(AC_ERR_STALL, "epoch kernel: no completion after %lld epochs", epochs_total);
+  }
+  AC_CUDA(cudaEventRecord(s->ev1, s->stream));
+  AC_CUDA(cudaEventSynchronize(s->ev1));
+  float ms = 0.f;
+  AC_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+  s->last_grid = std::min(total * E, ac::tb_grid(region));
+  return accumulate(s, sum, ms, true);
 }
 
 ac_status run_round(ac_sim* s, long long t_end) {
@@ -697,7 +813,16 @@ ac_status run_core(ac_sim* sim, long long t_end) {
   unsigned long long before = 0, after = 0;
   ac_status st = read_event_counter(sim, &before);
   if (st != AC_OK) return st;
-  st = (sim->cfg.kernel == ac::kKernelRound) ? run_round(sim, t_end) : run_blocked(sim, t_end);
+  if (sim->cfg.kernel == ac::kKernelEpoch && ep_applicable(sim)) {
+    bool fits = false;
+    st = tb_counts_fit(sim, t_end, &fits);
+    if (st != AC_OK) return st;
+    // counts too uneven for the 16-bit window: the round kernel's exact fallback
+    st = fits ? run_ep(sim, t_end) : run_round(sim, t_end);
+  } else {
+    // the epoch kernel's other cases (frames, odd sizes or halos) run on the round kernel
+    st = (sim->cfg.kernel != ac::kKernelBlocked) ? run_round(sim, t_end) : run_blocked(sim, t_end);
+  }
   if (st != AC_OK) return st;
   st = read_event_counter(sim, &after);
   if (st != AC_OK) return st;
@@ -854,7 +979,7 @@ ac_status run_frames(ac_sim* s, long long t_end, ac_frame_fn fn, void* user, int
   }
   // the temporal-blocked kernel slides the window frame by frame (run_tb_frames); the
   // other kernels run whole windows: to the cap, then every open frame is complete
-  if (t_end > s->t_done && s->cfg.kernel == ac::kKernelRound && (s->model != 0 || tb_applicable(s))) {
+  if (t_end > s->t_done && s->cfg.kernel != ac::kKernelBlocked && (s->model != 0 || tb_applicable(s))) {
     int D = 0, R = 0;
     tb_depth(s, &D, &R);
     bool fits = false;
@@ -977,8 +1102,8 @@ ac_status ac_set_stream(ac_sim* sim, void* stream) {
 
 ac_status ac_configure(ac_sim* sim, int32_t kernel, int32_t Lb, int32_t rounds, int32_t polls) {
   if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
-  if (kernel != AC_KERNEL_ROUND && kernel != AC_KERNEL_BLOCKED)
-    return fail(AC_ERR_ARG, "kernel must be AC_KERNEL_ROUND or AC_KERNEL_BLOCKED");
+  if (kernel != AC_KERNEL_ROUND && kernel != AC_KERNEL_BLOCKED && kernel != AC_KERNEL_EPOCH)
+    return fail(AC_ERR_ARG, "kernel must be AC_KERNEL_ROUND, AC_KERNEL_BLOCKED or AC_KERNEL_EPOCH");
   if (Lb != 32 && Lb != 64 && Lb != 128) return fail(AC_ERR_ARG, "Lb must be 32, 64 or 128");
   if (rounds < 1 || rounds > 1 << 20) return fail(AC_ERR_ARG, "rounds must be in [1, 2^20]");
   if (polls < 0 || polls > 1 << 20) return fail(AC_ERR_ARG, "polls must be in [0, 2^20]");
@@ -987,7 +1112,7 @@ ac_status ac_configure(ac_sim* sim, int32_t kernel, int32_t Lb, int32_t rounds, 
   sim->cfg.kernel = kernel;
   sim->cfg.lb = Lb;
   sim->cfg.threads = 4 * Lb;
-  if (kernel == AC_KERNEL_ROUND) {
+  if (kernel != AC_KERNEL_BLOCKED) {
     sim->cfg.rounds = rounds;
   } else {
     sim->cfg.refresh = rounds;
@@ -1188,7 +1313,7 @@ ac_status ac_stats(const ac_sim* sim, ac_stats_t* o) {
   o->kernel = sim->cfg.kernel;
   o->Lb = sim->cfg.lb;
   o->threads = sim->cfg.threads;
-  o->rounds_per_launch = sim->cfg.kernel == ac::kKernelRound ? sim->cfg.rounds : sim->cfg.refresh;
+  o->rounds_per_launch = sim->cfg.kernel != ac::kKernelBlocked ? sim->cfg.rounds : sim->cfg.refresh;
   o->grid = sim->last_grid;
   o->ctas_per_sm = sim->ctas_per_sm;
   return AC_OK;

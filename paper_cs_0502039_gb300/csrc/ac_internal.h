@@ -13,7 +13,8 @@ namespace ac {
 //   cnt[c] = number of committed arrivals of cell c
 // Tiling: tr x tc tiles; tile (i, j) covers rows [r0(i), r0(i)+h(i)) with
 // r0(i) = i*(rows/tr) + min(i, rows%tr), h(i) = rows/tr + (i < rows%tr), and the
-// same for columns; every tile side is <= lb.
+// same for columns (with cpair = 1, the same in units of two columns: every tile
+// column start and width is even); every tile side is <= lb.
 // Edge words: pub[(ti*tc + tj)*4*lb + e*lb + p] is the key of the tile's boundary
 // cell p on edge e (0 top row, 1 bottom row, 2 left column, 3 right column).
 // Threshold table capacity: 10 entries for the 4-neighbour array, 2 (M + 1) for the
@@ -30,6 +31,7 @@ struct LatDesc {
   unsigned long long* events;  // per-lattice committed-arrival counter
   int rows, cols;
   int tr, tc;
+  int cpair;                 // 1: columns are tiled in pairs (every tile column start and width even)
   int lb;
   int tile_base;             // first tile of this lattice in the launch's work list
   unsigned int thr[kThrMax]; // flip thresholds, index j + 5*(s > 0) (q-th degree neighbourhood:
@@ -75,9 +77,25 @@ struct DevCounters {
   unsigned int blocks_done;     // temporal-blocked kernel: CTAs finished in the current launch
   unsigned long long kmin[3];   // temporal-blocked kernel with frames: smallest output key of a
                                 // launch (mod-3 ring like active; the host presets all to ~0)
+  unsigned int next_item;       // epoch kernel: next work item to claim
+  unsigned int stop_epoch;      // epoch kernel: epochs after which no arrival before t_end is left
+                                // (the host presets ~0)
 };
 
-enum KernelKind { kKernelRound = 0, kKernelBlocked = 1 };
+// Epoch kernel (the persistent temporal-blocked kernel): per-tile and per-epoch words.
+//   done[tile]        epochs the tile has completed (release / acquire)
+//   ep_done[e]        tiles that completed epoch e
+//   ep_live[e]        tiles with an arrival before t_end left after epoch e
+// All zero before a launch; ep_done and ep_live hold max_epochs entries.
+struct EpArgs {
+  unsigned int* done;
+  unsigned int* ep_done;
+  unsigned int* ep_live;
+  int max_epochs;
+  long long watchdog_ns;
+};
+
+enum KernelKind { kKernelRound = 0, kKernelBlocked = 1, kKernelEpoch = 2 };
 
 // Temporal-blocked round kernel: a shared-memory region of side 96 (two CTAs per
 // SM) or 128 (one) holds a tile and a halo of depth D around it; tile side = region - 2D.
@@ -131,6 +149,16 @@ cudaError_t launch_pack(const LatDesc* host_desc, const int8_t* s_in, const long
 // halo = q * rounds.
 cudaError_t launch_tb(const LatDesc* d_desc, int nlat, int total_tiles, int region, int halo, int rounds,
                       DevCounters* ctr, cudaStream_t s, bool frames = false, int model = 0);
+// One launch of the epoch kernel: the temporal-blocked tile visit of launch_tb run as a
+// persistent dataflow over (epoch, tile) work items.  Each item advances one tile by
+// `rounds` synchronous rounds; it starts once the tile and its 8 neighbours have
+// completed the previous epoch (done words, release / acquire), and the kernel ends
+// when an epoch leaves no arrival before t_end (ctr->stop_epoch) or after
+// ep.max_epochs epochs.  State of epoch e is in key / cnt for even e, key2 / cnt2 for
+// odd e.  Needs even cols, even halo, a cpair tiling whose tile sides are >= halo, and
+// 16-byte aligned key buffers (the region rows are loaded by bulk asynchronous copies).
+cudaError_t launch_ep(const LatDesc* d_desc, int nlat, int total_tiles, int region, int halo, int rounds,
+                      DevCounters* ctr, const EpArgs& ep, cudaStream_t s, int model = 0);
 // Frames [K, K + count) were just opened: write each cell's spin into those whose tick
 // lies before the cell's next arrival (later commits write the others).
 cudaError_t launch_frames_fill(const LatDesc* host_desc, long long K, int count, cudaStream_t s);

@@ -136,10 +136,12 @@ __device__ __forceinline__ Geom tile_geom(const LatDesc& L, int t) {
   int q = L.rows / L.tr, rm = L.rows - q * L.tr;
   g.r0 = g.ti * q + min(g.ti, rm);
   g.h = q + (g.ti < rm);
-  q = L.cols / L.tc;
-  rm = L.cols - q * L.tc;
-  g.c0 = g.tj * q + min(g.tj, rm);
-  g.w = q + (g.tj < rm);
+  const int cu = L.cpair ? 2 : 1;      // column unit: pairs keep every start and width even
+  const int cn = L.cols / cu;
+  q = cn / L.tc;
+  rm = cn - q * L.tc;
+  g.c0 = cu * (g.tj * q + min(g.tj, rm));
+  g.w = cu * (q + (g.tj < rm));
   return g;
 }
 
@@ -827,6 +829,45 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// ---- epoch kernel: bulk asynchronous copies (the TMA unit) completing on an mbarrier,
+// and the release / acquire words that order tiles across CTAs.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// global -> shared, `bytes` a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// orders this thread's earlier generic-proxy accesses before its later async-proxy ones
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ int wrap_index(int x, int n, int& shift, int up_shift) {
   // x in [-n, 2n): wrapped index; shift = +up_shift if x came from below 0, -up_shift if >= n
   if (x < 0) {
@@ -872,13 +913,120 @@ __device__ __forceinline__ unsigned q_up(const unsigned long long* kp, int q) {
   return j;
 }
 
+// ---- epoch kernel control (one thread claims and publishes; threads 0..8 check the
+// nine dependencies of an item)
+
+// tile of work item k: epoch k / total, position k % total in the work list, rotated
+// by half the list on odd epochs
+__device__ __forceinline__ int ep_tile(unsigned k, int total, int* epoch) {
+  const int e = (int)(k / (unsigned)total);
+  const int j = (int)(k - (unsigned)e * (unsigned)total);
+  *epoch = e;
+  return (e & 1) ? (j + total / 2) % total : j;
+}
+
+// done word of dependency n (0..8: the tile and its 8 neighbours on the torus of
+// tiles) of item k, and the epoch it must have reached; nullptr for epoch 0
+__device__ __forceinline__ const unsigned* ep_dep(const LatDesc* lats, int nlat, int total, const EpArgs& ep,
+                                                  unsigned k, int n, unsigned* need) {
+  int epoch;
+  const int tile = ep_tile(k, total, &epoch);
+  *need = (unsigned)epoch;
+  if (epoch == 0) return nullptr;
+  const LatDesc& L = lats[find_lattice(lats, nlat, tile)];
+  const int t = tile - L.tile_base;
+  int ti = t / L.tc + n / 3 - 1, tj = t % L.tc + n % 3 - 1;
+  ti = ti < 0 ? ti + L.tr : (ti >= L.tr ? ti - L.tr : ti);
+  tj = tj < 0 ? tj + L.tc : (tj >= L.tc ? tj - L.tc : tj);
+  return ep.done + L.tile_base + ti * L.tc + tj;
+}
+
+// claim the next item (~0: none left, an error was reported, or the run has finished)
+__device__ __forceinline__ unsigned ep_claim(DevCounters* ctr, const EpArgs& ep, int total) {
+  if (*(volatile int*)&ctr->error != 0) return ~0u;
+  const unsigned k = atomicAdd(&ctr->next_item, 1u);
+  const unsigned e = k / (unsigned)total;
+  if (e >= (unsigned)ep.max_epochs || e >= *(volatile unsigned*)&ctr->stop_epoch) return ~0u;
+  return k;
+}
+
+// publish item k: its tile has completed epoch e + 1 (its stores precede this call on the
+// CTA's barrier; fence, then release); the last tile of an epoch decides whether any
+// arrival before t_end is left anywhere
+__device__ __forceinline__ void ep_publish(const LatDesc* lats, int nlat, int total, const EpArgs& ep,
+                                           DevCounters* ctr, unsigned k, bool live) {
+  int epoch;
+  const int tile = ep_tile(k, total, &epoch);
+  __threadfence();
+  // (the verification hook that suppresses edge publication also withholds the epoch
+  // words, so that the neighbours' bounded waits and the watchdog end the run)
+  if (!lats[find_lattice(lats, nlat, tile)].drop_publish) st_release_u32(&ep.done[tile], (unsigned)epoch + 1u);
+  if (live) atomicAdd(&ep.ep_live[epoch], 1u);
+  __threadfence();
+  if (atomicAdd(&ep.ep_done[epoch], 1u) == (unsigned)total - 1u) {
+    __threadfence();
+    if (*(volatile unsigned*)&ep.ep_live[epoch] == 0u) atomicMin(&ctr->stop_epoch, (unsigned)epoch + 1u);
+  }
+}
+
+// threads 0..8: wait until dependency `tid` of item k is met -- bounded polls, then sleeps,
+// a %globaltimer watchdog, and an early exit when another CTA has reported an error.
+// Returns true if the wait gave up.
+__device__ __forceinline__ bool ep_wait(const LatDesc* lats, int nlat, int total, const EpArgs& ep, DevCounters* ctr,
+                                     unsigned k, int tid) {
+  unsigned need;
+  const unsigned* f = ep_dep(lats, nlat, total, ep, k, tid, &need);
+  if (f == nullptr) return false;
+  unsigned long long t0 = 0;
+  unsigned n = 0;
+  bool gave_up = false;
+  for (; ld_acquire_u32(f) < need; ++n) {
+    if (n < 32) continue;
+    __nanosleep(n < 256 ? 64 : 512);
+    if (*(volatile int*)&ctr->error != 0) {
+      gave_up = true;
+      break;
+    }
+    const unsigned long long now = global_ns();
+    if (t0 == 0) {
+      t0 = now;
+    } else if (now - t0 > (unsigned long long)ep.watchdog_ns) {
+      atomicCAS(&ctr->error, 0, 4 /* AC_ERR_STALL */);
+      atomicExch(&ctr->err_block, (int)blockIdx.x);
+      gave_up = true;
+      break;
+    }
+  }
+  if (n) atomicAdd(&ctr->polls, (unsigned long long)n);
+  return gave_up;
+}
+
 // FR: snapshot frames are open (write_frames for the tile's own cells).
 // MODEL: 0 the Ising heat bath; 1 the Life-like automaton (Moore neighbourhood, birth /
 // survival masks in thr[0] / thr[1]); 2 the Ising heat bath on the q-th degree
 // neighbourhood (radius L.q; the region shrinks by q rings per round).
-template <int RW, bool FR, int MODEL>
+// EP: the epoch kernel.  Instead of one pass over the tiles per launch, a persistent
+// grid claims (epoch, tile) work items in increasing order from ctr->next_item.  Item
+// (e, t) advances tile t from the state of epoch e (buffer e & 1) to that of epoch
+// e + 1 (the other buffer), exactly what launch e of the launch variant does for it.
+// Its region covers the tile and parts of its 8 neighbour tiles, so it waits until
+// all 9 have published done >= e (acquire), and publishes done = e + 1 (release) after
+// its stores.  This is the aggregated algorithm of Fig. 3.4 with a tile per subarray
+// and a tile's completed epoch as the local time its neighbours wait on.  Every item
+// waits only on items claimed before it, so the schedule cannot deadlock, whatever
+// the number of resident CTAs.  Within an epoch, items go in work-list order, rotated
+// by half the list on odd epochs, so that an item's dependencies were claimed about
+// half an epoch earlier.  Region rows arrive by bulk asynchronous copies (the TMA
+// unit, through L2, never a stale L1 line); counts are read with ld.global.cg.
+// The control work is overlapped with the region load: while a visit's rows are in
+// flight, thread 0 publishes the CTA's previous item and claims the next one, whose
+// nine dependencies threads 0..8 check once; only if that check fails does the CTA
+// publish at once and wait at the end of the visit (so it never waits on itself).
+template <int RW, bool FR, int MODEL, bool EP>
 __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
-    tb_kernel(const LatDesc* __restrict__ lats, int nlat, int total_tiles, int D, int R, DevCounters* ctr) {
+    tb_kernel(const LatDesc* __restrict__ lats, int nlat, int total_tiles, int D, int R, DevCounters* ctr,
+              EpArgs ep) {
+  static_assert(!(EP && FR), "the epoch kernel does not write snapshot frames");
   using Cfg = TbCfg<RW>;
   constexpr int NT = Cfg::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -900,27 +1048,71 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   unsigned int* OV2 = OH2 + RW * Cfg::W;
   FrameView* fv = reinterpret_cast<FrameView*>(smem_raw + Cfg::fOff);
   static_assert(sizeof(FrameView) <= Cfg::fBytes, "frame view does not fit");
+  // the epoch kernel keeps its mbarrier and the claimed item where the frame view sits
+  unsigned long long* ep_bar = reinterpret_cast<unsigned long long*>(smem_raw + Cfg::fOff);
+  unsigned int* ep_ctl = reinterpret_cast<unsigned int*>(smem_raw + Cfg::fOff + 8);
+  // ep_ctl: [0] next item, [1] its dependencies were met at the early check,
+  //         [2] current item, [3] previous item not yet published, [4] its live flag,
+  //         [5] 0x10 | phase of a region load whose wait timed out (0: none)
 
-  // this launch's number, advanced by the last CTA of the previous launch
-  const unsigned launch_idx = *(volatile unsigned*)&ctr->seq;
-  const int parity = (int)(launch_idx & 1u);
-  if (launch_idx > 0) {
-    // nothing left, or an earlier launch of this call hit the count window (its output
-    // is not a consistent state, so no later launch may build on it): uniform exit
-    if (*(volatile unsigned*)&ctr->active[(launch_idx + 2) % 3] == 0u || *(volatile int*)&ctr->error != 0)
-      return;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctr->active[(launch_idx + 1) % 3] = 0u;
-    if (FR) ctr->kmin[(launch_idx + 1) % 3] = ~0ull;
-    atomicAdd(&ctr->launched, 1u);
-  }
   const int tid = threadIdx.x;
+  // this launch's number, advanced by the last CTA of the previous launch
+  unsigned launch_idx = 0;
+  int parity = 0;
+  if constexpr (!EP) {
+    launch_idx = *(volatile unsigned*)&ctr->seq;
+    parity = (int)(launch_idx & 1u);
+    if (launch_idx > 0) {
+      // nothing left, or an earlier launch of this call hit the count window (its output
+      // is not a consistent state, so no later launch may build on it): uniform exit
+      if (*(volatile unsigned*)&ctr->active[(launch_idx + 2) % 3] == 0u || *(volatile int*)&ctr->error != 0)
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctr->active[(launch_idx + 1) % 3] = 0u;
+      if (FR) ctr->kmin[(launch_idx + 1) % 3] = ~0ull;
+      atomicAdd(&ctr->launched, 1u);
+    }
+  } else {
+    if (tid == 0) {
+      mbar_init(ep_bar);
+      ep_ctl[0] = ep_claim(ctr, ep, total_tiles);
+      ep_ctl[1] = 0u;
+      ep_ctl[3] = ~0u;
+      ep_ctl[5] = 0u;
+    }
+    __syncthreads();
+  }
   const int lane = tid & 31;
   const int lj = tid % RW, li0 = tid / RW;                 // load / store mapping: column, first row
   unsigned long long scanned = 0, enabled = 0, rounds_done = 0, events_total = 0;
+  unsigned ep_phase = 0;                                   // epoch kernel: mbarrier phase of the next load
 
-  for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+  for (int tile_it = blockIdx.x;; tile_it += gridDim.x) {
+    int tile = tile_it;
+    if constexpr (EP) {
+      // the item claimed during the previous visit (or before the first one)
+      const unsigned k = ep_ctl[0];
+      if (k == ~0u) break;
+      if (!ep_ctl[1]) {
+        // its dependencies were not all met at the early check: publish the previous
+        // item first (it may be one of them), then wait
+        if (tid == 0 && ep_ctl[3] != ~0u) {
+          ep_publish(lats, nlat, total_tiles, ep, ctr, ep_ctl[3], ep_ctl[4] != 0u);
+          ep_ctl[3] = ~0u;
+        }
+        // a wait that gives up has reported the error: the visit still runs (on a state
+        // that is undefined from now on), and the next claim finds the error and ends the loop
+        if (tid < 9) ep_wait(lats, nlat, total_tiles, ep, ctr, k, tid);
+        __syncthreads();
+      }
+      int epoch;
+      tile = ep_tile(k, total_tiles, &epoch);
+      parity = epoch & 1;
+      if (tid == 0) ep_ctl[2] = k;
+    } else {
+      if (tile >= total_tiles) break;
+    }
     const LatDesc& L = lats[find_lattice(lats, nlat, tile)];
     const Geom g = tile_geom(L, tile - L.tile_base);
     // in registers: the copies below are asm statements that clobber memory
@@ -935,7 +1127,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     // the region wraps across the torus seam (small tiles of interior positions can too)
     const bool edge = (g.r0 < D) || (g.r0 + g.h + D > Lrows) || (g.c0 < D) || (g.c0 + g.w + D > Lcols);
     // counts are kept as 16-bit offsets from a window start taken at the tile centre
-    const unsigned ccen = __ldg(&cnt_in[(size_t)(g.r0 + g.h / 2) * Lcols + g.c0 + g.w / 2]);
+    const size_t ci = (size_t)(g.r0 + g.h / 2) * Lcols + g.c0 + g.w / 2;
+    const unsigned ccen = EP ? __ldcg(&cnt_in[ci]) : __ldg(&cnt_in[ci]);
     const unsigned base = ccen > 32768u ? ccen - 32768u : 0u;
     const unsigned cap = 65535u - (unsigned)R;
 
@@ -950,6 +1143,46 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     const int gc = wrap_index(g.c0 - D + lj, Lcols, shc, 2);
     bool over = false;
     __syncthreads();
+    if constexpr (EP) {
+      // one warp issues the region's rows as bulk copies: one per row, two where the
+      // row crosses the torus seam (even cols, an even region start and an even width
+      // keep every source, destination and size a multiple of 16 bytes)
+      if (tid < 32) {
+        if (tid == 0) mbar_expect_tx(ep_bar, (unsigned)(RH * RC) * 8u);
+        __syncwarp();
+        fence_proxy_async();
+        int shx;
+        const int x0 = wrap_index(g.c0 - D, Lcols, shx, 2);
+        const int n1 = min(RC, Lcols - x0);
+        for (int i = tid; i < RH; i += 32) {
+          int shr;
+          const int gr = wrap_index(g.r0 - D + i, Lrows, shr, 2);
+          const unsigned long long* src = key_in + (size_t)gr * (size_t)Lcols;
+          bulk_load(&K[i * RW], src + x0, (unsigned)n1 * 8u, ep_bar);
+          if (n1 < RC) bulk_load(&K[i * RW + n1], src, (unsigned)(RC - n1) * 8u, ep_bar);
+        }
+        // while the rows are in flight: publish the previous item, claim the next one and
+        // check its dependencies once
+        unsigned kn = ~0u;
+        if (tid == 0) {
+          if (ep_ctl[3] != ~0u) {
+            ep_publish(lats, nlat, total_tiles, ep, ctr, ep_ctl[3], ep_ctl[4] != 0u);
+            ep_ctl[3] = ~0u;
+          }
+          kn = ep_claim(ctr, ep, total_tiles);
+          ep_ctl[0] = kn;
+        }
+        kn = __shfl_sync(kFull, kn, 0);
+        bool met = true;
+        if (kn != ~0u && tid < 9) {
+          unsigned need;
+          const unsigned* f = ep_dep(lats, nlat, total_tiles, ep, kn, tid, &need);
+          met = (f == nullptr) || ld_acquire_u32(f) >= need;
+        }
+        met = __all_sync(kFull, met);
+        if (tid == 0) ep_ctl[1] = met ? 1u : 0u;
+      }
+    }
     // the thread's own-tile cells' count offsets at load (the write-back uses the same
     // column and rows, so its difference is the tile's committed arrivals)
     unsigned own_before = 0;
@@ -965,8 +1198,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const int i = li0 + Cfg::LSTRIDE * m;
         if (i < RH) {
           const uint32_t gi = (uint32_t)gr * (uint32_t)Lcols + (uint32_t)gc;   // rows * cols < 2^32
-          cp_async8(&K[i * RW + lj], &key_in[gi]);
-          cvs[m] = cnt_in[gi];
+          if constexpr (!EP) cp_async8(&K[i * RW + lj], &key_in[gi]);
+          cvs[m] = EP ? __ldcg(&cnt_in[gi]) : cnt_in[gi];
         }
         gr += Cfg::LSTRIDE;
         if (gr >= Lrows) gr -= Lrows;
@@ -990,8 +1223,30 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       thr[tid - RW] = L.thr[tid - RW];
     }
     if (over) atomicOr(s_over, 1u);
-    cp_async_wait_all();
-    __syncthreads();
+    if constexpr (EP) {
+      // the region's bulk copies: bounded wait on the mbarrier phase of this load
+      bool late = false;
+      unsigned long long t0 = 0;
+      for (unsigned n = 0; !mbar_try_wait(ep_bar, ep_phase); ++n) {
+        if ((n & 1023u) != 1023u) continue;
+        const unsigned long long now = global_ns();
+        if (t0 == 0) {
+          t0 = now;
+        } else if (now - t0 > 2000000000ull) {
+          late = true;
+          break;
+        }
+      }
+      if (late) {   // reported; the copies of this phase are waited on again before the CTA exits
+        atomicCAS(&ctr->error, 0, 4 /* AC_ERR_STALL */);
+        ep_ctl[5] = 0x10u | ep_phase;
+      }
+      ep_phase ^= 1u;
+      __syncthreads();
+    } else {
+      cp_async_wait_all();
+      __syncthreads();
+    }
     if (edge && MODEL == 0) {   // halo cells from across the torus seam: key +-2 (one tick of tie order)
       if (lj < RC) {
         for (int i = li0; i < RH; i += Cfg::LSTRIDE) {
@@ -1327,7 +1582,16 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       events_total += ev;
     }
     const int any_live = __syncthreads_or(live);
-    if (tid == 0 && any_live) atomicAdd(&ctr->active[launch_idx % 3], 1u);
+    if constexpr (EP) {
+      // the tile's stores are done (the barrier above); its epoch is published during the
+      // next visit's load, or before the CTA waits or exits
+      if (tid == 0) {
+        ep_ctl[3] = ep_ctl[2];
+        ep_ctl[4] = any_live ? 1u : 0u;
+      }
+    } else {
+      if (tid == 0 && any_live) atomicAdd(&ctr->active[launch_idx % 3], 1u);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) scanned += __shfl_down_sync(kFull, scanned, o);
   if (lane == 0) {
@@ -1338,12 +1602,21 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   if (tid == 0) {
     atomicAdd(&ctr->enabled, enabled);
     atomicAdd(&ctr->rounds, rounds_done);
-    // the last CTA of this launch advances the launch number for the next one
-    __threadfence();
-    if (atomicAdd(&ctr->blocks_done, 1u) == gridDim.x - 1u) {
-      ctr->blocks_done = 0u;
+    if constexpr (EP) {
+      if (ep_ctl[3] != ~0u) ep_publish(lats, nlat, total_tiles, ep, ctr, ep_ctl[3], ep_ctl[4] != 0u);
+      if (ep_ctl[5]) {   // a region load timed out: wait once more (bounded) for its copies
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try_wait(ep_bar, ep_ctl[5] & 1u) && global_ns() - t0 < 2000000000ull) {
+        }
+      }
+    } else {
+      // the last CTA of this launch advances the launch number for the next one
       __threadfence();
-      atomicExch(&ctr->seq, launch_idx + 1u);
+      if (atomicAdd(&ctr->blocks_done, 1u) == gridDim.x - 1u) {
+        ctr->blocks_done = 0u;
+        __threadfence();
+        atomicExch(&ctr->seq, launch_idx + 1u);
+      }
     }
   }
 }
@@ -1666,13 +1939,30 @@ cudaError_t tb_launch_rw(const LatDesc* d, int nlat, int total, int halo, int ro
                          cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW, FR, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TbCfg<RW>::bytes);
+    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW, FR, MODEL, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TbCfg<RW>::bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int grid = std::min(total, tb_grid(RW));
-  tb_kernel<RW, FR, MODEL><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds, ctr);
+  tb_kernel<RW, FR, MODEL, false><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds, ctr,
+                                                                                EpArgs{});
+  return cudaGetLastError();
+}
+
+template <int RW, int MODEL>
+cudaError_t ep_launch_rw(const LatDesc* d, int nlat, int total, int halo, int rounds, DevCounters* ctr,
+                         const EpArgs& ep, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW, false, MODEL, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TbCfg<RW>::bytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int grid = std::min(total * ep.max_epochs, tb_grid(RW));
+  tb_kernel<RW, false, MODEL, true><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds,
+                                                                                  ctr, ep);
   return cudaGetLastError();
 }
 
@@ -1700,6 +1990,18 @@ cudaError_t launch_tb(const LatDesc* d, int nlat, int total, int region, int hal
   switch (region) {
     case 96: return tb_launch_model<96>(d, nlat, total, halo, rounds, ctr, s, frames, model);
     case 128: return tb_launch_model<128>(d, nlat, total, halo, rounds, ctr, s, frames, model);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_ep(const LatDesc* d, int nlat, int total, int region, int halo, int rounds, DevCounters* ctr,
+                      const EpArgs& ep, cudaStream_t s, int model) {
+  if (halo < 2 || (halo & 1) || rounds < 1 || rounds > halo || 4 * halo >= region || total < 1 ||
+      ep.max_epochs < 1 || (long long)total * ep.max_epochs >= (1ll << 31) || model != 0)
+    return cudaErrorInvalidValue;
+  switch (region) {
+    case 96: return ep_launch_rw<96, 0>(d, nlat, total, halo, rounds, ctr, ep, s);
+    case 128: return ep_launch_rw<128, 0>(d, nlat, total, halo, rounds, ctr, ep, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -53,7 +53,8 @@ def _check_checkpoint(sim, cp, what):
 
 
 @pytest.mark.parametrize("beta", ["0.30", "0.4407", "0.60"])
-@pytest.mark.parametrize("kernel,rounds", [(ac.AC_KERNEL_ROUND, 6), (ac.AC_KERNEL_ROUND, 8), (ac.AC_KERNEL_BLOCKED, 1)])
+@pytest.mark.parametrize("kernel,rounds", [(ac.AC_KERNEL_ROUND, 6), (ac.AC_KERNEL_ROUND, 8), (ac.AC_KERNEL_BLOCKED, 1),
+                                           (ac.AC_KERNEL_EPOCH, 8), (ac.AC_KERNEL_EPOCH, 10)])
 def test_4096_runs_match_oracle(beta, kernel, rounds):
     g = _golden("ising4096_b" + beta)
     with ac.Sim(g["rows"], g["cols"], g["beta"], g["J"], g["h"], g["seed"], init=g["init"], kernel=kernel,
@@ -96,7 +97,8 @@ def test_16384_prefix_and_cross_kernel():
     g = _golden("ising16384_T1")
     cp = g["checkpoints"][0]
     results = {}
-    for name, kernel, rounds in (("round", ac.AC_KERNEL_ROUND, 8), ("blocked", ac.AC_KERNEL_BLOCKED, 1)):
+    for name, kernel, rounds in (("round", ac.AC_KERNEL_ROUND, 8), ("blocked", ac.AC_KERNEL_BLOCKED, 1),
+                                 ("epoch", ac.AC_KERNEL_EPOCH, 8)):
         with ac.Sim(g["rows"], g["cols"], g["beta"], g["J"], g["h"], g["seed"], init=g["init"], kernel=kernel,
                     Lb=64, rounds=rounds) as sim:
             sim.run_until(1)
@@ -112,4 +114,4 @@ def test_16384_prefix_and_cross_kernel():
             assert abs(st["total_counts"] / N - 20.0) < 0.01
             # low temperature, positive field, all-up start: the lattice stays almost all up
             assert st["sum_s"] / N > 0.99
-    assert results["round"] == results["blocked"]
+    assert results["round"] == results["blocked"] == results["epoch"]

@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-ROUND, BLOCKED = ac.AC_KERNEL_ROUND, ac.AC_KERNEL_BLOCKED
+ROUND, BLOCKED, EPOCH = ac.AC_KERNEL_ROUND, ac.AC_KERNEL_BLOCKED, ac.AC_KERNEL_EPOCH
 
 # (rows, cols, beta, J, h, seed, T, init): degenerate tori, ragged tiles, several tiles
 CASES = [
@@ -43,6 +43,9 @@ CONFIGS = [
     (ROUND, 32, 1, 0), (ROUND, 64, 1, 0), (ROUND, 32, 5, 0), (ROUND, 128, 3, 0), (ROUND, 64, 2, 0),
     (ROUND, 64, 8, 0), (ROUND, 64, 12, 0), (ROUND, 64, 13, 0), (ROUND, 64, 16, 0),
     (BLOCKED, 32, 1, 8), (BLOCKED, 64, 1, 8), (BLOCKED, 128, 1, 8), (BLOCKED, 32, 4, 0),
+    # the epoch kernel (even halos; odd cols, small tori and the odd halo 5 take its round-kernel fallback)
+    (EPOCH, 64, 2, 0), (EPOCH, 64, 6, 0), (EPOCH, 64, 8, 0), (EPOCH, 64, 12, 0), (EPOCH, 64, 14, 0),
+    (EPOCH, 64, 16, 0), (EPOCH, 64, 5, 0),
 ]
 
 
@@ -81,11 +84,23 @@ def test_stats_observables_and_checksum():
     assert stats["total_counts"] == int(ref.n.astype(np.int64).sum())
 
 
-@pytest.mark.parametrize("kernel", [ROUND, BLOCKED])
+@pytest.mark.parametrize("case", [(300, 250, 8), (64, 64, 16), (130, 66, 4), (96, 200, 2)], ids=str)
+def test_epoch_kernel_runs_its_own_path(case):
+    """The epoch kernel is the path taken (one launch per run call, tile visits counted)
+    and matches the oracle; several tiles, the torus seams in both directions."""
+    rows, cols, rounds = case
+    ref = oracle_state(rows, cols, 0.44, 1.0, 0.0, 3, 4)
+    s, t, n, stats = lib_state(rows, cols, 0.44, 1.0, 0.0, 3, 4, 0, EPOCH, 64, rounds, 0)
+    assert_same(ref, s, t, n, f"epoch kernel {rows}x{cols} rounds={rounds}")
+    assert stats["kernel"] == EPOCH and stats["visits"] > 0 and stats["launches"] >= 1
+    assert stats["rounds_per_launch"] == rounds
+
+
+@pytest.mark.parametrize("kernel", [ROUND, BLOCKED, EPOCH])
 def test_run_splitting_and_checkpoint_resume(kernel):
     rows, cols, beta, seed = 70, 90, 0.44, 13
     ref = oracle_state(rows, cols, beta, 1.0, 0.0, seed, 6)
-    with ac.Sim(rows, cols, beta, 1.0, 0.0, seed, kernel=kernel, Lb=32) as a:
+    with ac.Sim(rows, cols, beta, 1.0, 0.0, seed, kernel=kernel, Lb=32, rounds=1 if kernel == BLOCKED else 4) as a:
         a.run_until_ticks(2 * T32 + 777)
         a.run_until(4)
         s, t, n = a.read_state()
@@ -135,6 +150,21 @@ def test_watchdog_reports_stall_without_fault():
     ref = oracle_state(64, 64, 0.44, 1.0, 0.0, 1, 2)
     s, t, n, _ = lib_state(64, 64, 0.44, 1.0, 0.0, 1, 2, kernel=BLOCKED, Lb=32)
     assert_same(ref, s, t, n, "after a stall")
+
+
+def test_epoch_watchdog_reports_stall_without_fault():
+    """The epoch kernel with its epoch words withheld: every tile of the second epoch
+    waits on neighbours that never publish, so the bounded waits and the watchdog end
+    the run with AC_ERR_STALL; the device stays usable."""
+    with ac.Sim(256, 256, 0.44, 1.0, 0.0, 1, kernel=EPOCH, rounds=8) as sim:
+        sim.set_option(ac.AC_OPT_WATCHDOG_NS, 50_000_000)
+        sim.set_option(ac.AC_OPT_DROP_PUBLISH, 1)
+        with pytest.raises(ac.ACError) as ei:
+            sim.run_until(20)
+        assert ei.value.status == ac.ac.AC_ERR_STALL
+    ref = oracle_state(256, 256, 0.44, 1.0, 0.0, 1, 2)
+    s, t, n, _ = lib_state(256, 256, 0.44, 1.0, 0.0, 1, 2, kernel=EPOCH, rounds=8)
+    assert_same(ref, s, t, n, "after an epoch-kernel stall")
 
 
 def test_invalid_arguments_are_rejected():
