@@ -61,7 +61,9 @@ def parse():
                     choices=["ising4096", "batch", "serve", "frames", "configs", "efficiency", "life", "rates",
                              "qnbhd", "sizes"],
                     help="ising4096: the headline step; batch: the 512-lattice batch only; serve: the request stream")
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the replayed request stream")
+    ap.add_argument("--serve-seconds", type=float, default=None,
+                    help="length of the replayed request stream (default 60 s for --workload serve, 10 s in the "
+                         "default run)")
     ap.add_argument("--single", action="store_true",
                     help="one lattice, one kernel configuration (the profiling case); prints one JSON line")
     ap.add_argument("--rows", type=int, default=4096)
@@ -318,10 +320,11 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         import paper_cs_0502039_gb300 as ac
+        fixed = args.rounds if args.no_autotune else None
         if args.workload == "batch":
-            res = batch_measurement(ac, args.rounds, args.lb)
+            res = batch_measurement(ac, fixed, args.lb)
         elif args.workload == "serve":
-            res = serve_measurement(ac, args.serve_seconds, args.rounds, args.lb)
+            res = serve_measurement(ac, args.serve_seconds or 60.0, fixed, args.lb)
         else:
             res = frames_measurement(ac, args.rounds, args.lb)
         print(json.dumps({"workload": args.workload, **res}), flush=True)
@@ -349,8 +352,9 @@ def main():
     kern = kernel_id(ac, args.kernel)
     tuned = None
     if not args.no_autotune:
+        # the step's own batch (three 4096^2 lattices), timed to T = 10 per candidate
         from paper_cs_0502039_gb300 import autotune
-        tuned = autotune.tune(w["rows"], w["cols"])
+        tuned = autotune.tune_batch([(w["rows"], w["cols"], b) for b in w["betas"]], T=10.0)
         kern, args.lb, args.rounds, args.polls = tuned["kernel"], tuned["Lb"], tuned["rounds"], tuned["polls"]
         args.kernel = kernel_name(ac, kern)
     # weak scaling: every rank runs its own replica batch (seed offset by rank)
@@ -361,9 +365,11 @@ def main():
     handles = [s.handle for s in sims]
     t_end = [w["T"] * T32] * len(sims)
 
-    # the step's lattices run as one batch (one work list of all their tiles; measured 1.4 %
-    # faster than one run after another) unless --per-lattice
+    # the step's lattices run as one batch (one work list of all their tiles) or one after
+    # another, as the autotuner found faster (--per-lattice: one after another)
     batched = kern == ac.AC_KERNEL_BLOCKED or not args.per_lattice
+    if tuned is not None and not tuned.get("batched", True):
+        batched = False
 
     def step():
         for s in sims:
@@ -430,12 +436,15 @@ def main():
 
     # roofline of the dominant kernel: algorithmic bytes per launch / its CUDA-event duration
     peak, peak_src = measured_peaks()
-    kern_launch_ms = kern_ms / args.steps if kern == ac.AC_KERNEL_BLOCKED else kern_ms / args.steps
+    kern_launch_ms = kern_ms / args.steps
     achieved = BYTES_PER_EVENT * ev_per_step_rank / (kern_launch_ms / 1000.0) / 1e9
+    region = 96 if args.rounds <= 12 and args.lb != 128 else 128
     if kern == ac.AC_KERNEL_BLOCKED:
         kname = f"blocked_kernel<{args.lb}>"
+    elif kern == ac.AC_KERNEL_EPOCH:
+        kname = f"tb_kernel<{region},EP> rounds={args.rounds}" + (" batched" if batched else "")
     elif args.rounds > 1:
-        kname = f"tb_kernel<{96 if args.rounds <= 12 else 128}> rounds={args.rounds}" + (" batched" if batched else "")
+        kname = f"tb_kernel<{region}> rounds={args.rounds}" + (" batched" if batched else "")
     else:
         kname = f"round_kernel<{args.lb}>"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -469,20 +478,34 @@ def main():
             init_state.append(host)
         outs = [(torch.empty(N, dtype=torch.int8).pin_memory(), torch.empty(N, dtype=torch.int64).pin_memory(),
                  torch.empty(N, dtype=torch.int32).pin_memory()) for _ in sims]
+        # lattices run one after another on a compute stream; their pinned-host loads and reads
+        # go on a copy stream, so that lattice i+1 is loaded and lattice i-1 read back while
+        # lattice i runs (the handle's own transfers never overlap its own runs)
+        compute, copy = torch.cuda.Stream(), torch.cuda.Stream()
+        for s in sims:
+            ac.ac_set_stream(s.handle, compute.cuda_stream)
+        views = [(hs.numpy(), ht.numpy(), hn.numpy().view(np.uint32)) for hs, ht, hn in init_state]
+        oviews = [(a.numpy(), b.numpy(), c.numpy().view(np.uint32)) for a, b, c in outs]
+
+        def e2e_run(steps):
+            """`steps` steps as one stream of (step, lattice) jobs: while job j runs, job j+1 is loaded
+            and job j-1 read back; every job's load and read is inside the timed region."""
+            jobs = [i for _ in range(steps) for i in range(len(sims))]
+            ac.ac_load_state_async(sims[jobs[0]].handle, *views[jobs[0]], 0, copy.cuda_stream)
+            for j, i in enumerate(jobs):
+                if j + 1 < len(jobs):
+                    # the next job's handle (another lattice, or this step's first one again) was
+                    # read back in an earlier job; its load waits on the device for that read
+                    ac.ac_load_state_async(sims[jobs[j + 1]].handle, *views[jobs[j + 1]], 0, copy.cuda_stream)
+                sims[i].run_until_ticks(t_end[i])
+                ac.ac_read_state_async(sims[i].handle, *oviews[i], copy.cuda_stream)
+            copy.synchronize()
+
+        e2e_run(1)                        # untimed: events and staging of the asynchronous path
         sync_all()
         e_steps = max(1, min(args.steps, 3))
         t0 = time.perf_counter()
-        for _ in range(e_steps):
-            for s, (hs, ht, hn) in zip(sims, init_state):
-                # the loaded state (time 0) replaces the handle's state and its time
-                ac.ac_load_state(s.handle, hs.numpy(), ht.numpy(), hn.numpy().view(np.uint32), 0)
-            if batched:
-                ac.ac_batch_run_until(handles, t_end)
-            else:
-                for s in sims:
-                    s.run_until_ticks(t_end[0])
-            for s, (os_, ot, on) in zip(sims, outs):
-                ac.ac_read_state(s.handle, os_.numpy(), ot.numpy(), on.numpy().view(np.uint32))
+        e2e_run(e_steps)
         torch.cuda.synchronize()
         e_dt = time.perf_counter() - t0
         # the trajectory is deterministic: every step commits the device-timed step's arrivals;
@@ -501,13 +524,18 @@ def main():
         # per lattice and direction: spins int8 + ticks int64 + counts uint32 = 13 bytes per cell
         e2e = {"value": e_ev / e_dt, "unit": "events/s", "h2d_bytes_per_step": 13 * N * len(sims),
                "d2h_bytes_per_step": 13 * N * len(sims), "steps": e_steps,
-               "path": "ac_load_state(host) + run + ac_read_state(host) per lattice"}
+               "path": "per lattice and step: ac_load_state_async (pinned host, copy stream), ac_run_until_ticks "
+                       "(compute stream), ac_read_state_async (pinned host, copy stream); the steps' lattices form one "
+                       "stream of jobs, the next job loading and the previous one reading back while a job runs",
+               "over_device": (e_ev / e_dt) / value}
+        for s in sims:
+            ac.ac_set_stream(s.handle, None)
 
     extra, batch, served = {}, None, None
     if rank == 0 and not args.no_extra:
         extra = side_measurements(ac, w, seed)
         batch = batch_measurement(ac)
-        served = serve_measurement(ac, seconds=args.serve_seconds)
+        served = serve_measurement(ac, seconds=args.serve_seconds or 10.0)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -525,7 +553,10 @@ def main():
                           "J": w["J"], "h": w["h"], "seed": w["seed"], "T": w["T"], "init": "random",
                           "kernel": kname, "Lb": args.lb, "polls": args.polls, "rounds": args.rounds,
                           "autotuned": None if tuned is None else {k: tuned[k] for k in ("kernel", "Lb", "rounds",
-                                                                                       "polls", "events_per_s")},
+                                                                                       "polls", "batched",
+                                                                                       "events_per_s", "measured")
+                                                                  if k in tuned},
+                          "batched": batched,
                           "events_per_step": ev_all / args.steps,
                           "l2": "state 3 x 201 MB > 129 MB L2 (no flush)",
                           "parallelism": f"replicas x{world}"},
@@ -540,17 +571,23 @@ def main():
     return 0
 
 
-def batch_measurement(ac, rounds=8, lb=64):
+def batch_measurement(ac, rounds=None, lb=64):
     """512 independent lattices (L log-uniform in [32, 1024], beta ~ U[0.3, 0.6], seeds 0..511) run
-    to T = 100: one batched call (one work list of all tiles, launches replayed from a captured
-    graph) against 512 plain per-lattice run calls on the same GPU."""
-    from paper_cs_0502039_gb300 import workloads
+    to T = 100: one batched call (one work list of all tiles) against 512 plain per-lattice run
+    calls on the same GPU, both with the configuration the autotuner picks for this batch (or
+    `rounds` rounds per launch of the round kernel).  Every lattice's state fingerprint must be
+    the same in both modes."""
+    from paper_cs_0502039_gb300 import autotune, workloads
     ws = workloads.batch_workload()
+    if rounds is None:
+        cfg = autotune.tune_batch([(w["rows"], w["cols"], w["beta"]) for w in ws], T=5.0, batched_only=True)
+    else:
+        cfg = dict(kernel=ac.AC_KERNEL_ROUND, Lb=lb, rounds=rounds, polls=8)
     handles = ac.ac_batch_create([(w["rows"], w["cols"], w["init"]) for w in ws], [w["beta"] for w in ws],
                                  [w["J"] for w in ws], [w["h"] for w in ws], [w["seed"] for w in ws])
     sims = [ac.Sim(w["rows"], w["cols"], w["beta"], w["J"], w["h"], w["seed"], handle=h) for w, h in zip(ws, handles)]
     for s in sims:
-        s.configure(ac.AC_KERNEL_ROUND, lb, rounds, 8)
+        s.configure(cfg["kernel"], cfg["Lb"], cfg["rounds"], max(cfg["polls"], 0))
     t_end = [int(w["T"] * T32) for w in ws]
     import torch
 
@@ -558,7 +595,10 @@ def batch_measurement(ac, rounds=8, lb=64):
         for w, s in zip(ws, sims):
             s.reset(w["seed"], w["init"])
 
-    out = {"lattices": len(ws), "cells": sum(w["rows"] * w["cols"] for w in ws), "T": ws[0]["T"]}
+    out = {"lattices": len(ws), "cells": sum(w["rows"] * w["cols"] for w in ws), "T": ws[0]["T"],
+           "config": {"kernel": kernel_name(ac, cfg["kernel"]), "Lb": cfg["Lb"], "rounds": cfg["rounds"],
+                      "tuned": rounds is None}}
+    prints = {}
     for mode in ("batched", "plain"):
         times = []
         for rep in range(3):          # rep 0 warms up (and, for batched, captures the graph)
@@ -572,43 +612,66 @@ def batch_measurement(ac, rounds=8, lb=64):
                     s.run_until_ticks(te)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
-        ev = sum(s.stats()["events"] for s in sims)
+        st = [s.stats() for s in sims]
+        prints[mode] = [(x["checksum"], x["total_counts"], x["sum_s"], x["sum_bonds"]) for x in st]
+        ev = sum(x["events"] for x in st)
         out[mode] = {"events": ev, "seconds": min(times[1:]), "events_per_s": ev / min(times[1:])}
+    same = sum(a == b for a, b in zip(prints["batched"], prints["plain"]))
+    out["per_lattice_equal"] = f"{same}/{len(ws)}"
+    if same != len(ws):
+        raise RuntimeError(f"batched and plain runs differ on {len(ws) - same} lattices")
     out["batched_over_plain"] = out["batched"]["events_per_s"] / out["plain"]["events_per_s"]
     for s in sims:
         s.close()
     return out
 
 
-def serve_measurement(ac, seconds=10.0, rounds=8, lb=64):
+def serve_measurement(ac, seconds=10.0, rounds=None, lb=64):
     """Continuous batching: a Poisson request stream (200 requests/s, L log-uniform in [64, 2048],
     beta ~ U[0.25, 0.7], T ~ U[10, 200], seed = request id) replayed in real time; latency is
-    request arrival -> result ready.  Baseline: the same requests run one after another, each
-    with a plain run call (its own launches), on the same GPU."""
+    request arrival -> result ready.  Then the same request set with every request visible at
+    once (the server's capacity), and, as the baseline, the same request set run one request
+    after another, each with its own plain run call, on the same GPU.  The configuration is
+    the autotuner's for a batch of the stream's first 64 lattices (or `rounds` rounds per
+    launch of the round kernel)."""
+    from paper_cs_0502039_gb300 import autotune
     from paper_cs_0502039_gb300 import serve as srv_mod
     from paper_cs_0502039_gb300 import workloads
     reqs = workloads.serve_requests(rate=200.0, duration=seconds)
-    results, wall, server = srv_mod.serve(reqs, budget_bytes=64 << 30, slice_T=10.0, rounds=rounds, Lb=lb,
-                                          realtime=True)
+    if rounds is None:
+        cfg = autotune.tune_batch([(r["rows"], r["cols"], r["beta"]) for r in reqs[:64]], T=5.0, batched_only=True)
+    else:
+        cfg = dict(kernel=ac.AC_KERNEL_ROUND, Lb=lb, rounds=rounds, polls=8)
+    kw = dict(budget_bytes=64 << 30, slice_T=10.0, kernel=cfg["kernel"], rounds=cfg["rounds"], Lb=cfg["Lb"])
+    results, wall, server = srv_mod.serve(reqs, realtime=True, **kw)
     lat = sorted(r.latency for r in results)
     ev = sum(r.events for r in results)
     span = max(r.finished for r in results) - min(r.arrival for r in results)
-    out = {"requests": len(reqs), "completed": len(results), "wall_s": wall, "events": ev,
-           "events_per_s": ev / span, "p50_latency_s": lat[len(lat) // 2],
+    out = {"requests": len(reqs), "seconds": seconds, "rate_per_s": 200.0, "completed": len(results), "wall_s": wall,
+           "config": {"kernel": kernel_name(ac, cfg["kernel"]), "Lb": cfg["Lb"], "rounds": cfg["rounds"]},
+           "events": ev, "events_per_s": ev / span, "p50_latency_s": lat[len(lat) // 2],
            "p99_latency_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "steps": server.steps,
            "offered_events_per_s": sum(r["rows"] * r["cols"] * r["T"] for r in reqs) / seconds}
-    # serial per-request baseline on a sample (first 100 requests, timed end to end)
-    sample = reqs[:100]
+    # capacity: the same requests, all visible at t = 0
+    sat, sat_wall, sat_server = srv_mod.serve(reqs, realtime=False, **kw)
+    sat_ev = sum(r.events for r in sat)
+    if [(r.id, r.checksum) for r in sat] != [(r.id, r.checksum) for r in results]:
+        raise RuntimeError("the saturated serve run differs from the real-time one")
+    out["saturated"] = {"events": sat_ev, "wall_s": sat_wall, "events_per_s": sat_ev / sat_wall,
+                        "steps": sat_server.steps}
+    # serial per-request baseline over the same request set, timed end to end
+    import torch
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     sev = 0
-    for r in sample:
+    for r in reqs:
         with ac.Sim(r["rows"], r["cols"], r["beta"], r["J"], r["h"], r["seed"], init=r["init"],
-                    kernel=ac.AC_KERNEL_ROUND, Lb=lb, rounds=rounds) as s:
+                    kernel=cfg["kernel"], Lb=cfg["Lb"], rounds=cfg["rounds"]) as s:
             s.run_until(r["T"])
             sev += s.stats()["events"]
     dt = time.perf_counter() - t0
-    out["serial_sample"] = {"requests": len(sample), "events_per_s": sev / dt, "seconds": dt}
-    out["served_over_serial"] = out["events_per_s"] / out["serial_sample"]["events_per_s"]
+    out["serial"] = {"requests": len(reqs), "events": sev, "events_per_s": sev / dt, "seconds": dt}
+    out["capacity_over_serial"] = out["saturated"]["events_per_s"] / out["serial"]["events_per_s"]
     return out
 
 
@@ -867,6 +930,7 @@ def side_measurements(ac, w, seed):
     """Single-lattice numbers for each kernel (beta = 0.4407 lattice, one run each)."""
     res = {}
     configs = [("round_r1_lb64", ac.AC_KERNEL_ROUND, 64, 1, 0), ("round_r8_lb64", ac.AC_KERNEL_ROUND, 64, 8, 0),
+               ("blocked_epoch_r8", ac.AC_KERNEL_EPOCH, 64, 8, 0), ("blocked_epoch_r10", ac.AC_KERNEL_EPOCH, 64, 10, 0),
                ("blocked_lb32", ac.AC_KERNEL_BLOCKED, 32, 1, 8), ("blocked_lb64", ac.AC_KERNEL_BLOCKED, 64, 1, 8),
                ("blocked_lb128", ac.AC_KERNEL_BLOCKED, 128, 1, 8)]
     for name, kern, lb, rounds, polls in configs:
@@ -878,7 +942,8 @@ def side_measurements(ac, w, seed):
             st = s.stats()
         res[name] = {"events": st["events"], "device_ms": st["device_ms"],
                      "events_per_s": st["events"] / (st["device_ms"] / 1000.0),
-                     "hbm_frac_effective": BYTES_PER_EVENT * st["events"] / (st["device_ms"] / 1000.0) / 1e9 / 6787.9,
+                     "hbm_frac_effective": BYTES_PER_EVENT * st["events"] / (st["device_ms"] / 1000.0) / 1e9
+                     / measured_peaks()[0],
                      "launches": st["launches"], "enabled_frac": st["enabled_frac_mean"],
                      "visits": st["visits"], "polls": st["polls"], "grid": st["grid"]}
     return res

@@ -134,15 +134,17 @@ ac_status ac_set_stream(ac_sim* sim, void* cuda_stream);
  *           2..16 = temporal blocking: each CTA loads its tile with a halo of depth
  *           `rounds` into a shared-memory region and runs `rounds` exact
  *           synchronous rounds per launch.  The region is 96 x 96 for rounds <= 12
- *           (two CTAs per SM) and 128 x 128 for 13..16 (one CTA per SM); the tile
- *           side is the region side - 2*rounds and Lb is unused.  Needs rows,
+ *           (384 threads per CTA, two CTAs per SM) and 128 x 128 for 13..16 (512
+ *           threads, one CTA per SM); Lb = 128 selects the 128-wide region for any
+ *           rounds, other Lb values are unused.  The tile side is the region side
+ *           - 2*rounds.  Needs rows,
  *           cols >= 4*rounds; otherwise Lb-tiles with frozen halos run `rounds`
  *           rounds per launch.  When the lattice's counts are too uneven for the
  *           kernel's 16-bit count window, the call runs one round per launch.
  *           Blocked kernel: halo refresh period in rounds (>= 1).
  *   polls   blocked kernel: halo polls before a blocked tile is left (>= 0)
- * AC_KERNEL_EPOCH takes `rounds` as the round kernel does (synchronous rounds per tile
- * visit, the halo depth) and ignores Lb and polls.  It is one persistent launch per
+ * AC_KERNEL_EPOCH takes `rounds` and Lb as the round kernel does (synchronous rounds
+ * per tile visit, the halo depth; Lb = 128 for the 128-wide region) and ignores polls.  It is one persistent launch per
  * run call: each CTA claims (epoch, tile) work items in order; a tile's visit loads
  * its region (tile plus halo) by bulk asynchronous copies, runs `rounds` rounds, writes
  * the tile back and publishes the tile's epoch with a release store; a visit of epoch
@@ -188,6 +190,32 @@ ac_status ac_read_state_device(const ac_sim* sim, int8_t* s_dev, int64_t* t_dev,
  */
 ac_status ac_load_state(ac_sim* sim, const int8_t* s, const int64_t* t, const uint32_t* n,
                         int64_t t_done);
+
+/*
+ * Asynchronous state transfers (checkpoint/resume and end-to-end runs that overlap
+ * copies with compute).  Both enqueue their work on `stream` (a cudaStream_t, NULL
+ * for the legacy default stream) after all earlier work of the handle, and return
+ * without waiting.  Host buffers should be pinned (cudaHostAlloc, or torch
+ * pin_memory) for the copies to run asynchronously; they must stay valid until the
+ * work on `stream` has completed.
+ *
+ * ac_load_state_async: as ac_load_state -- copy into the handle's staging buffers,
+ *   validate on the device (every s +-1, every t in [max(t_done, 1), 2^61)), and only
+ *   then replace the state -- but the outcome is known on the device only.  The
+ *   handle's next call that uses its state (run, read, load, stats, class counts,
+ *   reset, rates, frames, batch) first waits on the host for the load; if validation
+ *   failed, that call returns AC_ERR_ARG naming the first bad cell and the state and
+ *   time are left as they were.  The staging buffers are the second state buffer of
+ *   the handle, so a transfer never overlaps the handle's own runs, only other
+ *   handles' work.
+ * ac_read_state_async: as ac_read_state into host arrays (any pointer may be NULL);
+ *   the arrays hold the state once `stream` reaches this point.  The handle's next
+ *   device work waits for the read on the device.
+ * Errors: AC_ERR_ARG, AC_ERR_OOM (staging or events), AC_ERR_CUDA.
+ */
+ac_status ac_load_state_async(ac_sim* sim, const int8_t* s, const int64_t* t, const uint32_t* n, int64_t t_done,
+                              void* stream);
+ac_status ac_read_state_async(const ac_sim* sim, int8_t* s, int64_t* t, uint32_t* n, void* stream);
 
 typedef struct {
   uint64_t events;          /* arrivals committed by run calls since create/load */
@@ -343,8 +371,12 @@ ac_status ac_thresholds(double beta, double J, double h, uint32_t thr[10]);
  * lattices and parameters; seeds distinguish lattices, the counter carries no
  * lattice id) into out[0..n-1], each usable with every call above.
  * ac_batch_run_until advances sims[0..n-1] to t_end[i] each.  When every handle
- * is configured for the round kernel with the same rounds per launch (>= 2) and
- * fits temporal blocking, one work list holds the tiles of all handles and each
+ * is configured for the epoch kernel with the same rounds and fits it, ONE
+ * persistent epoch-kernel launch covers the tiles of all handles (each tile waits
+ * only on its own lattice's neighbour tiles; a further launch follows only if the
+ * launch's epoch budget ran out first).  Otherwise, when every handle is configured
+ * for the round or epoch kernel with the same rounds per launch (>= 2) and fits
+ * temporal blocking, one work list holds the tiles of all handles and each
  * temporal-blocked launch advances all of them; launches are issued in chunks of
  * 8, replayed from a CUDA graph captured on the second call with the same list
  * of handles, and the host reads the device counters after each chunk to see

@@ -55,7 +55,7 @@ EXPORTS = ["ac_create", "ac_set_stream", "ac_configure", "ac_run_until", "ac_run
            "ac_destroy", "ac_last_error", "ac_thresholds", "ac_reset", "ac_set_option", "ac_batch_create", "ac_batch_run_until",
            "ac_dev_exp_ticks", "ac_dev_philox", "ac_run_blocked_static", "ac_frames_configure",
            "ac_run_until_frames", "ac_frames_status", "ac_time_model", "ac_create_life", "ac_set_rates",
-           "ac_create_q", "ac_class_counts"]
+           "ac_create_q", "ac_class_counts", "ac_load_state_async", "ac_read_state_async"]
 
 AC_RATE_ONE = 1 << 20
 
@@ -83,6 +83,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ac_read_state": ([P, P, P, P], I32),
         "ac_read_state_device": ([P, P, P, P], I32),
         "ac_load_state": ([P, P, P, P, I64], I32),
+        "ac_load_state_async": ([P, P, P, P, I64, P], I32),
+        "ac_read_state_async": ([P, P, P, P, P], I32),
         "ac_stats": ([P, ctypes.POINTER(ac_stats_t)], I32),
         "ac_round_history": ([P, P, I32, ctypes.POINTER(I32)], I32),
         "ac_destroy": ([P], None),
@@ -191,6 +193,21 @@ def ac_read_state_device(sim: int, s_ptr: int | None, t_ptr: int | None, n_ptr: 
 def ac_load_state(sim: int, s: np.ndarray, t: np.ndarray, n: np.ndarray, t_done: int) -> None:
     _check(_lib.ac_load_state(sim, _np_ptr(s, np.int8), _np_ptr(t, np.int64), _np_ptr(n, np.uint32),
                               int(t_done)))
+
+
+def ac_load_state_async(sim: int, s: np.ndarray, t: np.ndarray, n: np.ndarray, t_done: int, stream) -> None:
+    """Enqueue a state load on `stream` (a cudaStream_t as an int, or None); the host arrays (pinned
+    for a truly asynchronous copy) must stay alive until the stream has passed this point."""
+    _check(_lib.ac_load_state_async(sim, _np_ptr(s, np.int8), _np_ptr(t, np.int64), _np_ptr(n, np.uint32),
+                                    int(t_done), stream))
+
+
+def ac_read_state_async(sim: int, s: np.ndarray | None, t: np.ndarray | None, n: np.ndarray | None,
+                        stream) -> None:
+    """Enqueue a state read into host arrays on `stream`; they hold the state once the stream is done."""
+    _check(_lib.ac_read_state_async(sim, None if s is None else _np_ptr(s, np.int8),
+                                    None if t is None else _np_ptr(t, np.int64),
+                                    None if n is None else _np_ptr(n, np.uint32), stream))
 
 
 def ac_stats(sim: int) -> dict:

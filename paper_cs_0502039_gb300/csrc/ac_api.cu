@@ -44,6 +44,9 @@ ac_status fail(ac_status st, const char* fmt, ...) {
   } while (0)
 
 constexpr double kTicksPerUnit = 4294967296.0;
+// grid of the state-transfer kernels of the asynchronous loads and reads: they run beside
+// another handle's persistent kernel, so they stay on a few SMs
+constexpr int kAsyncBlocks = 152;
 constexpr long long kTickLimit = 1ll << 61;
 
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
@@ -100,6 +103,11 @@ struct ac_sim {
   unsigned int* d_ep = nullptr;             // epoch kernel: tile done words, per-epoch counts
   size_t ep_cap = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // asynchronous state transfers (ac_load_state_async / ac_read_state_async) on a caller's stream
+  cudaEvent_t ev_work = nullptr, ev_load = nullptr, ev_read = nullptr;
+  unsigned long long* h_bad = nullptr;      // pinned: validation result of the pending load
+  bool load_pending = false, read_pending = false;
+  long long load_t_done = 0;
 
   long long t_done = 0;
   // snapshot frames (Fig. 3.7): f_B slots of ncells() spins; frames [f_K, f_K + f_B) open
@@ -180,6 +188,10 @@ struct BatchRunner {
   cudaGraph_t graph = nullptr;
   ac::LaunchCfg cfg{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // epoch-kernel batches: tile done words and per-epoch counts
+  bool ep = false;
+  unsigned int* d_ep = nullptr;
+  size_t ep_cap = 0;
   // temporal-blocked batches: per-lattice count ranges, a captured chunk of launches
   bool tb = false;
   int region = 0, halo = 0, calls = 0;
@@ -205,6 +217,7 @@ void free_runner(BatchRunner* r) {
   if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
   if (r->chunk_graph) cudaGraphDestroy(r->chunk_graph);
   if (r->d_range) cudaFree(r->d_range);
+  if (r->d_ep) cudaFree(r->d_ep);
   delete r;
 }
 
@@ -245,6 +258,13 @@ ac_status alloc_edges(ac_sim* s) {
 
 void free_sim(ac_sim* s) {
   if (!s) return;
+  // asynchronous transfers still in flight on a caller's stream use the handle's buffers
+  if (s->load_pending) cudaEventSynchronize(s->ev_load);
+  if (s->read_pending) cudaEventSynchronize(s->ev_read);
+  if (s->ev_work) cudaEventDestroy(s->ev_work);
+  if (s->ev_load) cudaEventDestroy(s->ev_load);
+  if (s->ev_read) cudaEventDestroy(s->ev_read);
+  if (s->h_bad) cudaFreeHost(s->h_bad);
   cudaFree(s->key);
   cudaFree(s->cnt);
   cudaFree(s->key2);
@@ -424,7 +444,7 @@ ac_status run_tb(ac_sim* s, long long t_end, int D, int R) {
       return fail(AC_ERR_OOM, "second state buffer (%zu cells) allocation failed", N);
     }
   }
-  const int region = ac::tb_region_for_model(D, s->model, s->q);
+  const int region = ac::tb_region_for_model(D, s->model, s->q, s->cfg.lb == 128);
   int tr = 0, tc = 0;
   tb_tiling(s->rows, s->cols, region, D, ac::tb_grid(region), &tr, &tc);
   ac::LatDesc d = s->host_desc(t_end, 0);
@@ -510,7 +530,28 @@ ac_status ensure_ep_words(unsigned int** buf, size_t* cap, size_t words) {
   return AC_OK;
 }
 
-ac_status run_ep(ac_sim* s, long long t_end) {
+// Count margin of the 16-bit window for a call of `span` time units: a cell commits about
+// `span` arrivals (Poisson), with a wide margin (the same test as tb_counts_fit).
+unsigned count_window_limit(double span) {
+  const double margin = 2.0 * span + 64.0 * std::sqrt(span + 1.0) + 64.0;
+  return margin >= 30000.0 ? 0u : (unsigned)(30000.0 - margin);
+}
+
+// Zero the counters of an epoch-kernel launch and mark no epoch as the last (device-side
+// writes only: nothing waits for a copy engine that other streams' transfers may occupy).
+ac_status reset_ep_counters(ac::DevCounters* d_ctr, unsigned* d_ep, size_t ep_words, cudaStream_t st) {
+  AC_CUDA(cudaMemsetAsync(d_ctr, 0, sizeof(ac::DevCounters), st));
+  AC_CUDA(cudaMemsetAsync(&d_ctr->stop_epoch, 0xFF, sizeof(unsigned), st));
+  AC_CUDA(cudaMemsetAsync(d_ep, 0, ep_words * 4, st));
+  return AC_OK;
+}
+
+// One run call on the epoch kernel.  The count check runs on the device: the count-range
+// kernel writes the lattice's (min, max) and the epoch kernel refuses to start when they
+// could leave the 16-bit window, in which case *fallback is set and the state is untouched.
+// Only the counters are read back, once per launch.
+ac_status run_ep(ac_sim* s, long long t_end, bool* fallback) {
+  *fallback = false;
   const int D = s->cfg.rounds;
   const size_t N = s->ncells();
   if (!s->key2) {
@@ -519,22 +560,26 @@ ac_status run_ep(ac_sim* s, long long t_end) {
       return fail(AC_ERR_OOM, "second state buffer (%zu cells) allocation failed", N);
     }
   }
-  const int region = ac::tb_region_for(D);
+  const int region = ac::tb_region_for(D, s->cfg.lb == 128);
   int tr = 0, tc = 0;
   ep_tiling(s->rows, s->cols, region, D, &tr, &tc);
   const int total = tr * tc;
   const double span = (double)(t_end - s->t_done) / kTicksPerUnit;
   const int E = ep_epochs(span, D, total);
-  ac_status st = ensure_ep_words(&s->d_ep, &s->ep_cap, (size_t)total + 2 * (size_t)E);
+  const size_t words = (size_t)total + 2 * (size_t)E;
+  ac_status st = ensure_ep_words(&s->d_ep, &s->ep_cap, words);
   if (st != AC_OK) return st;
+  unsigned* d_range = reinterpret_cast<unsigned*>(s->d_red);
   ac::EpArgs ep{};
   ep.done = s->d_ep;
   ep.ep_done = s->d_ep + total;
   ep.ep_live = s->d_ep + total + E;
   ep.max_epochs = E;
   ep.watchdog_ns = s->cfg.watchdog_ns;
-  ac::DevCounters c0{};
-  c0.stop_epoch = ~0u;
+  ep.range = d_range;
+  ep.nrange = 1;
+  ep.limit = count_window_limit(span);
+  const int grid = (int)std::min<long long>((long long)total * E, ac::tb_grid(region));
   ac::DevCounters sum{};
   AC_CUDA(cudaEventRecord(s->ev0, s->stream));
   long long epochs_total = 0;
@@ -543,19 +588,30 @@ ac_status run_ep(ac_sim* s, long long t_end) {
     d.tr = tr;
     d.tc = tc;
     d.cpair = 1;
-    AC_CUDA(cudaMemcpyAsync(s->d_desc, &d, sizeof d, cudaMemcpyHostToDevice, s->stream));
-    AC_CUDA(cudaMemcpyAsync(s->d_ctr, &c0, sizeof c0, cudaMemcpyHostToDevice, s->stream));
-    AC_CUDA(cudaMemsetAsync(s->d_ep, 0, ((size_t)total + 2 * (size_t)E) * 4, s->stream));
+    AC_CUDA(ac::launch_store_desc(d, s->d_desc, s->stream));
+    st = reset_ep_counters(s->d_ctr, s->d_ep, words, s->stream);
+    if (st != AC_OK) return st;
+    if (launch == 0) {
+      AC_CUDA(cudaMemsetAsync(d_range, 0xFF, 4, s->stream));
+      AC_CUDA(cudaMemsetAsync(d_range + 1, 0, 4, s->stream));
+      AC_CUDA(ac::launch_count_range(&d, d_range, s->stream));
+    } else {
+      ep.nrange = 0;    // the first launch checked the window for the whole call
+    }
     AC_CUDA(ac::launch_ep(s->d_desc, 1, total, region, D, D, s->d_ctr, ep, s->stream, 0));
     ac::DevCounters c{};
     AC_CUDA(cudaMemcpyAsync(&c, s->d_ctr, sizeof c, cudaMemcpyDeviceToHost, s->stream));
     AC_CUDA(cudaStreamSynchronize(s->stream));
+    if (c.error == ac::kEpWindow) {
+      if (launch != 0) return fail(AC_ERR_STATE, "epoch kernel: count check refused a later launch");
+      *fallback = true;
+      return AC_OK;
+    }
     sum.events += c.events;
     sum.rounds += c.rounds;
     sum.scanned += c.scanned;
     sum.enabled += c.enabled;
     // every CTA's claims beyond its last item: exactly one that found nothing left
-    const int grid = (int)std::min<long long>((long long)total * E, ac::tb_grid(region));
     sum.visits += c.next_item > (unsigned)grid ? c.next_item - (unsigned)grid : 0u;
     sum.polls += c.polls;
     sum.launched += 1;
@@ -579,8 +635,12 @@ ac_status run_ep(ac_sim* s, long long t_end) {
   AC_CUDA(cudaEventSynchronize(s->ev1));
   float ms = 0.f;
   AC_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
-  s->last_grid = std::min(total * E, ac::tb_grid(region));
-  return accumulate(s, sum, ms, true);
+  s->last_grid = grid;
+  st = accumulate(s, sum, ms, true);
+  if (st != AC_OK) return st;
+  s->events += sum.events;
+  s->t_done = t_end;
+  return AC_OK;
 }
 
 ac_status run_round(ac_sim* s, long long t_end) {
@@ -809,20 +869,152 @@ ac_status batch_run_tb(int32_t n, ac_sim* const* sims, const int64_t* t_end, Bat
   return AC_OK;
 }
 
+// Batched epoch kernel: one persistent launch over the tiles of every handle (one work
+// list; each lattice's tiles wait only on that lattice's neighbour tiles), so all
+// lattices advance by the same epochs of D rounds.
+ac_status batch_run_ep(int32_t n, ac_sim* const* sims, const int64_t* t_end, BatchRunner* R) {
+  const cudaStream_t stream = R->stream;
+  for (int i = 0; i < n; ++i) {
+    ac_sim* s = sims[i];
+    if (!s->key2) {
+      if (cudaMalloc(&s->key2, s->ncells() * 8) != cudaSuccess || cudaMalloc(&s->cnt2, s->ncells() * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AC_ERR_OOM, "second state buffer allocation failed (handle %d)", i);
+      }
+    }
+  }
+  const int D = R->halo;
+  int base = 0;
+  double span = 0.0;
+  std::vector<int> tiles_tr(n), tiles_tc(n);
+  for (int i = 0; i < n; ++i) {
+    ep_tiling(sims[i]->rows, sims[i]->cols, R->region, D, &tiles_tr[i], &tiles_tc[i]);
+    base += tiles_tr[i] * tiles_tc[i];
+    span = std::max(span, (double)(t_end[i] - sims[i]->t_done) / kTicksPerUnit);
+  }
+  const int total = base;
+  // the 16-bit count window must hold every region of every lattice for the whole call
+  auto fill_desc = [&]() {
+    int b = 0;
+    for (int i = 0; i < n; ++i) {
+      R->h_desc[i] = sims[i]->host_desc(t_end[i], b);
+      R->h_desc[i].tr = tiles_tr[i];
+      R->h_desc[i].tc = tiles_tc[i];
+      R->h_desc[i].cpair = 1;
+      b += tiles_tr[i] * tiles_tc[i];
+    }
+  };
+  fill_desc();
+  AC_CUDA(cudaMemcpyAsync(R->d_desc, R->h_desc, sizeof(ac::LatDesc) * n, cudaMemcpyHostToDevice, stream));
+  std::vector<unsigned> range(2 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    range[2 * i] = 0xFFFFFFFFu;
+    range[2 * i + 1] = 0u;
+  }
+  AC_CUDA(cudaMemcpyAsync(R->d_range, range.data(), range.size() * 4, cudaMemcpyHostToDevice, stream));
+  size_t max_cells = 0;
+  for (int i = 0; i < n; ++i) max_cells = std::max(max_cells, sims[i]->ncells());
+  AC_CUDA(ac::launch_count_range_batch(R->d_desc, n, max_cells, R->d_range, stream));
+  AC_CUDA(cudaMemcpyAsync(range.data(), R->d_range, range.size() * 4, cudaMemcpyDeviceToHost, stream));
+  std::vector<unsigned long long> before(n), after(n);
+  for (int i = 0; i < n; ++i)
+    AC_CUDA(cudaMemcpyAsync(&before[i], sims[i]->d_events, 8, cudaMemcpyDeviceToHost, stream));
+  AC_CUDA(cudaStreamSynchronize(stream));
+  const double margin = 2.0 * span + 64.0 * std::sqrt(span + 1.0) + 64.0;
+  for (int i = 0; i < n; ++i) {
+    if ((double)(range[2 * i + 1] - range[2 * i]) + margin >= 30000.0) {
+      // very uneven counts (loaded states only): run every handle on its own, exactly
+      for (int k = 0; k < n; ++k) {
+        ac_status st = ac_run_until_ticks(sims[k], t_end[k]);
+        if (st != AC_OK) return st;
+      }
+      return AC_OK;
+    }
+  }
+  const int E = ep_epochs(span, D, total);
+  ac_status st = ensure_ep_words(&R->d_ep, &R->ep_cap, (size_t)total + 2 * (size_t)E);
+  if (st != AC_OK) return st;
+  ac::EpArgs ep{};
+  ep.done = R->d_ep;
+  ep.ep_done = R->d_ep + total;
+  ep.ep_live = R->d_ep + total + E;
+  ep.max_epochs = E;
+  ep.watchdog_ns = sims[0]->cfg.watchdog_ns;
+  ac::DevCounters c0{};
+  c0.stop_epoch = ~0u;
+  ac::DevCounters sum{};
+  AC_CUDA(cudaEventRecord(R->ev0, stream));
+  long long epochs_total = 0;
+  const int grid = (int)std::min<long long>((long long)total * E, ac::tb_grid(R->region));
+  for (;;) {
+    AC_CUDA(cudaMemcpyAsync(R->d_ctr, &c0, sizeof c0, cudaMemcpyHostToDevice, stream));
+    AC_CUDA(cudaMemsetAsync(R->d_ep, 0, ((size_t)total + 2 * (size_t)E) * 4, stream));
+    AC_CUDA(ac::launch_ep(R->d_desc, n, total, R->region, D, D, R->d_ctr, ep, stream, 0));
+    ac::DevCounters c{};
+    AC_CUDA(cudaMemcpyAsync(&c, R->d_ctr, sizeof c, cudaMemcpyDeviceToHost, stream));
+    AC_CUDA(cudaStreamSynchronize(stream));
+    sum.rounds += c.rounds;
+    sum.scanned += c.scanned;
+    sum.enabled += c.enabled;
+    sum.visits += c.next_item > (unsigned)grid ? c.next_item - (unsigned)grid : 0u;
+    sum.polls += c.polls;
+    sum.launched += 1;
+    if (c.error) {
+      sum.error = c.error;
+      sum.err_block = c.err_block;
+      break;
+    }
+    const unsigned done = (c.stop_epoch != ~0u) ? c.stop_epoch : (unsigned)E;
+    if (done & 1u) {
+      for (int i = 0; i < n; ++i) {
+        std::swap(sims[i]->key, sims[i]->key2);
+        std::swap(sims[i]->cnt, sims[i]->cnt2);
+      }
+      fill_desc();
+      AC_CUDA(cudaMemcpyAsync(R->d_desc, R->h_desc, sizeof(ac::LatDesc) * n, cudaMemcpyHostToDevice, stream));
+    }
+    epochs_total += done;
+    if (c.stop_epoch != ~0u) break;
+    if ((double)epochs_total * D > 64.0 * (9.0 * std::ceil(span) + 16.0) + 4096.0)
+      return fail(AC_ERR_STALL, "batched epoch kernel: no completion after %lld epochs", epochs_total);
+  }
+  AC_CUDA(cudaEventRecord(R->ev1, stream));
+  for (int i = 0; i < n; ++i)
+    AC_CUDA(cudaMemcpyAsync(&after[i], sims[i]->d_events, 8, cudaMemcpyDeviceToHost, stream));
+  AC_CUDA(cudaStreamSynchronize(stream));
+  float ms = 0.f;
+  AC_CUDA(cudaEventElapsedTime(&ms, R->ev0, R->ev1));
+  if (sum.error == AC_ERR_STALL) return fail(AC_ERR_STALL, "batched epoch kernel: device watchdog (block %d)", sum.err_block);
+  if (sum.error) return fail((ac_status)sum.error, "batched epoch kernel: device error %d", sum.error);
+  for (int i = 0; i < n; ++i) {
+    ac_sim* s = sims[i];
+    s->events += after[i] - before[i];
+    s->t_done = t_end[i];
+    s->launches += sum.launched;
+    s->device_ms += ms;
+    s->last_grid = grid;
+  }
+  sims[0]->rounds += sum.rounds;
+  sims[0]->scanned += sum.scanned;
+  sims[0]->enabled += sum.enabled;
+  sims[0]->visits += sum.visits;
+  sims[0]->polls += sum.polls;
+  return AC_OK;
+}
+
 ac_status run_core(ac_sim* sim, long long t_end) {
+  if (sim->cfg.kernel == ac::kKernelEpoch && ep_applicable(sim)) {
+    bool fallback = false;
+    ac_status st = run_ep(sim, t_end, &fallback);
+    // counts too uneven for the 16-bit window (nothing was run): the round kernel's exact
+    // one-round path below
+    if (st != AC_OK || !fallback) return st;
+  }
   unsigned long long before = 0, after = 0;
   ac_status st = read_event_counter(sim, &before);
   if (st != AC_OK) return st;
-  if (sim->cfg.kernel == ac::kKernelEpoch && ep_applicable(sim)) {
-    bool fits = false;
-    st = tb_counts_fit(sim, t_end, &fits);
-    if (st != AC_OK) return st;
-    // counts too uneven for the 16-bit window: the round kernel's exact fallback
-    st = fits ? run_ep(sim, t_end) : run_round(sim, t_end);
-  } else {
-    // the epoch kernel's other cases (frames, odd sizes or halos) run on the round kernel
-    st = (sim->cfg.kernel != ac::kKernelBlocked) ? run_round(sim, t_end) : run_blocked(sim, t_end);
-  }
+  // the epoch kernel's other cases (frames, odd sizes or halos) run on the round kernel
+  st = (sim->cfg.kernel != ac::kKernelBlocked) ? run_round(sim, t_end) : run_blocked(sim, t_end);
   if (st != AC_OK) return st;
   st = read_event_counter(sim, &after);
   if (st != AC_OK) return st;
@@ -841,6 +1033,48 @@ void frames_off(ac_sim* s) {
 
 // Hand frame f_K to fn (a device pointer, or a copy in the pinned host buffer) and
 // retire it.  The frame is complete: every cell's tick is above K dt.
+// Asynchronous transfers: a pending load is waited for (on the host: its validation result
+// decides whether the handle's time changes) and a pending read is ordered before the
+// handle's next device work (on the device) by every call that uses the handle's state.
+ac_status settle_async(ac_sim* s) {
+  if (s->load_pending) {
+    s->load_pending = false;
+    AC_CUDA(cudaEventSynchronize(s->ev_load));
+    if (*s->h_bad != ~0ull)
+      return fail(AC_ERR_ARG,
+                  "asynchronous load: cell %llu has a spin other than +-1 or a tick outside [max(t_done, 1), 2^61); "
+                  "the state was left unchanged", *s->h_bad);
+    s->t_done = s->load_t_done;
+    frames_off(s);
+  }
+  if (s->read_pending) {
+    s->read_pending = false;
+    AC_CUDA(cudaStreamWaitEvent(s->stream, s->ev_read, 0));
+  }
+  return AC_OK;
+}
+
+ac_status ensure_async(ac_sim* s) {
+  if (!s->ev_work) {
+    if (cudaEventCreateWithFlags(&s->ev_work, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_load, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_read, cudaEventDisableTiming) != cudaSuccess)
+      return fail(AC_ERR_CUDA, "cudaEventCreate failed");
+  }
+  if (!s->h_bad && cudaHostAlloc(&s->h_bad, sizeof(unsigned long long), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    s->h_bad = nullptr;
+    return fail(AC_ERR_OOM, "pinned host word allocation failed");
+  }
+  return AC_OK;
+}
+
+#define AC_SETTLE(sim)                            \
+  do {                                            \
+    ac_status st_ = settle_async(sim);            \
+    if (st_ != AC_OK) return st_;                 \
+  } while (0)
+
 ac_status deliver_frame(ac_sim* s, ac_frame_fn fn, void* user, int on_host) {
   const size_t N = s->ncells();
   const int8_t* slot = s->frames + (size_t)(s->f_K % s->f_B) * N;
@@ -875,7 +1109,7 @@ ac_status run_tb_frames(ac_sim* s, long long t_end, ac_frame_fn fn, void* user, 
   unsigned long long ev_before = 0, ev_after = 0;
   ac_status st = read_event_counter(s, &ev_before);
   if (st != AC_OK) return st;
-  const int region = ac::tb_region_for_model(D, s->model, s->q);
+  const int region = ac::tb_region_for_model(D, s->model, s->q, s->cfg.lb == 128);
   int tr = 0, tc = 0;
   tb_tiling(s->rows, s->cols, region, D, ac::tb_grid(region), &tr, &tc);
   const int total = tr * tc;
@@ -1124,6 +1358,7 @@ ac_status ac_configure(ac_sim* sim, int32_t kernel, int32_t Lb, int32_t rounds, 
 
 ac_status ac_run_until_ticks(ac_sim* sim, int64_t t_end) {
   if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  AC_SETTLE(sim);
   if (t_end < sim->t_done) return fail(AC_ERR_ARG, "t_end %lld is below the previous t_end %lld",
                                        (long long)t_end, sim->t_done);
   if (t_end >= kTickLimit) return fail(AC_ERR_ARG, "t_end must be < 2^61");
@@ -1133,6 +1368,7 @@ ac_status ac_run_until_ticks(ac_sim* sim, int64_t t_end) {
 
 ac_status ac_set_rates(ac_sim* sim, const uint32_t* m) {
   if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  AC_SETTLE(sim);
   if (sim->t_done != 0) return fail(AC_ERR_STATE, "rates are set at time 0 (before the first run or after ac_reset)");
   if (sim->model != 0) return fail(AC_ERR_ARG, "per-cell rates apply to the Ising array");
   const size_t N = sim->ncells();
@@ -1155,6 +1391,7 @@ ac_status ac_set_rates(ac_sim* sim, const uint32_t* m) {
 
 ac_status ac_frames_configure(ac_sim* sim, int64_t dt_ticks, int64_t K0, int32_t B) {
   if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  AC_SETTLE(sim);
   if (B == 0) {
     frames_off(sim);
     return AC_OK;
@@ -1183,6 +1420,7 @@ ac_status ac_frames_configure(ac_sim* sim, int64_t dt_ticks, int64_t K0, int32_t
 
 ac_status ac_run_until_frames(ac_sim* sim, int64_t t_end, ac_frame_fn fn, void* user, int32_t on_host) {
   if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  AC_SETTLE(sim);
   if (sim->f_B <= 0) return fail(AC_ERR_ARG, "no frames configured (ac_frames_configure)");
   if (t_end < sim->t_done) return fail(AC_ERR_ARG, "t_end %lld is below the previous t_end %lld",
                                        (long long)t_end, sim->t_done);
@@ -1231,6 +1469,7 @@ ac_status ac_read_state(const ac_sim* csim, int8_t* s, int64_t* t, uint32_t* n) 
   if (!csim) return fail(AC_ERR_ARG, "sim is NULL");
   ac_sim* sim = const_cast<ac_sim*>(csim);   // staging buffers only; the state is not modified
   const size_t N = sim->ncells();
+  AC_SETTLE(sim);
   if (s || t) {
     ac_status st = ensure_staging(sim);
     if (st != AC_OK) return st;
@@ -1247,6 +1486,7 @@ ac_status ac_read_state(const ac_sim* csim, int8_t* s, int64_t* t, uint32_t* n) 
 
 ac_status ac_read_state_device(const ac_sim* sim, int8_t* s, int64_t* t, uint32_t* n) {
   if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  AC_SETTLE(const_cast<ac_sim*>(sim));
   const ac::LatDesc d = sim->host_desc(sim->t_done, 0);
   AC_CUDA(ac::launch_unpack(&d, s, (long long*)t, n, sim->stream));
   AC_CUDA(cudaStreamSynchronize(sim->stream));
@@ -1256,6 +1496,7 @@ ac_status ac_read_state_device(const ac_sim* sim, int8_t* s, int64_t* t, uint32_
 ac_status ac_load_state(ac_sim* sim, const int8_t* s, const int64_t* t, const uint32_t* n,
                         int64_t t_done) {
   if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  AC_SETTLE(sim);
   if (!s || !t || !n) return fail(AC_ERR_ARG, "s, t and n are required");
   if (t_done < 0 || t_done >= kTickLimit) return fail(AC_ERR_ARG, "t_done out of range");
   const size_t N = sim->ncells();
@@ -1283,8 +1524,65 @@ ac_status ac_load_state(ac_sim* sim, const int8_t* s, const int64_t* t, const ui
   return AC_OK;
 }
 
+ac_status ac_load_state_async(ac_sim* sim, const int8_t* s, const int64_t* t, const uint32_t* n, int64_t t_done,
+                              void* stream) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  if (!s || !t || !n) return fail(AC_ERR_ARG, "s, t and n are required");
+  if (t_done < 0 || t_done >= kTickLimit) return fail(AC_ERR_ARG, "t_done out of range");
+  AC_SETTLE(sim);
+  ac_status st = ensure_staging(sim);
+  if (st == AC_OK) st = ensure_async(sim);
+  if (st != AC_OK) return st;
+  const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const size_t N = sim->ncells();
+  // the staging buffers are the handle's second state buffer: start after its earlier work
+  AC_CUDA(cudaEventRecord(sim->ev_work, sim->stream));
+  AC_CUDA(cudaStreamWaitEvent(cs, sim->ev_work, 0));
+  AC_CUDA(cudaMemcpyAsync(sim->stage8, s, N, cudaMemcpyHostToDevice, cs));
+  AC_CUDA(cudaMemcpyAsync(sim->key2, t, N * 8, cudaMemcpyHostToDevice, cs));
+  AC_CUDA(cudaMemcpyAsync(sim->cnt2, n, N * 4, cudaMemcpyHostToDevice, cs));
+  unsigned long long* d_bad = sim->d_red + 12;
+  AC_CUDA(cudaMemsetAsync(d_bad, 0xFF, 8, cs));
+  AC_CUDA(ac::launch_validate(sim->stage8, (const long long*)sim->key2, N, std::max<long long>(t_done, 1),
+                              kTickLimit, d_bad, cs, kAsyncBlocks));
+  AC_CUDA(cudaMemcpyAsync(sim->h_bad, d_bad, 8, cudaMemcpyDeviceToHost, cs));
+  const ac::LatDesc d = sim->host_desc(t_done, 0);
+  AC_CUDA(ac::launch_pack_checked(&d, sim->stage8, (const long long*)sim->key2, sim->cnt2, d_bad, cs, kAsyncBlocks));
+  AC_CUDA(cudaEventRecord(sim->ev_load, cs));
+  // no device-side wait on the handle's stream here: other handles may share that stream
+  // and must not wait for this load; the handle's next call waits for it (settle_async)
+  sim->load_pending = true;
+  sim->load_t_done = t_done;
+  return AC_OK;
+}
+
+ac_status ac_read_state_async(const ac_sim* csim, int8_t* s, int64_t* t, uint32_t* n, void* stream) {
+  if (!csim) return fail(AC_ERR_ARG, "sim is NULL");
+  ac_sim* sim = const_cast<ac_sim*>(csim);   // staging buffers and events only; the state is not modified
+  AC_SETTLE(sim);
+  ac_status st = ensure_staging(sim);
+  if (st == AC_OK) st = ensure_async(sim);
+  if (st != AC_OK) return st;
+  const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const size_t N = sim->ncells();
+  AC_CUDA(cudaEventRecord(sim->ev_work, sim->stream));
+  AC_CUDA(cudaStreamWaitEvent(cs, sim->ev_work, 0));
+  if (s || t) {
+    const ac::LatDesc d = sim->host_desc(sim->t_done, 0);
+    AC_CUDA(ac::launch_unpack(&d, s ? sim->stage8 : nullptr, t ? (long long*)sim->key2 : nullptr, nullptr, cs,
+                              kAsyncBlocks));
+    if (s) AC_CUDA(cudaMemcpyAsync(s, sim->stage8, N, cudaMemcpyDeviceToHost, cs));
+    if (t) AC_CUDA(cudaMemcpyAsync(t, sim->key2, N * 8, cudaMemcpyDeviceToHost, cs));
+  }
+  if (n) AC_CUDA(cudaMemcpyAsync(n, sim->cnt, N * 4, cudaMemcpyDeviceToHost, cs));
+  AC_CUDA(cudaEventRecord(sim->ev_read, cs));
+  sim->read_pending = true;
+  return AC_OK;
+}
+
 ac_status ac_stats(const ac_sim* sim, ac_stats_t* o) {
   if (!sim || !o) return fail(AC_ERR_ARG, "sim and out are required");
+  AC_SETTLE(const_cast<ac_sim*>(sim));
   std::memset(o, 0, sizeof *o);
   unsigned long long r[4] = {0, 0, 0, 0};
   const ac::LatDesc d = sim->host_desc(sim->t_done, 0);
@@ -1333,6 +1631,7 @@ ac_status ac_round_history(const ac_sim* sim, uint64_t* counts, int32_t cap, int
 
 ac_status ac_class_counts(const ac_sim* sim, uint64_t counts[10]) {
   if (!sim || !counts) return fail(AC_ERR_ARG, "sim and counts are required");
+  AC_SETTLE(const_cast<ac_sim*>(sim));
   if (sim->model != 0) return fail(AC_ERR_ARG, "classes are defined for the 4-neighbour Ising array");
   const ac::LatDesc d = sim->host_desc(sim->t_done, 0);
   AC_CUDA(cudaMemsetAsync(sim->d_red, 0, 10 * sizeof(unsigned long long), sim->stream));
@@ -1344,6 +1643,7 @@ ac_status ac_class_counts(const ac_sim* sim, uint64_t counts[10]) {
 
 ac_status ac_reset(ac_sim* sim, uint64_t seed, int32_t init) {
   if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  AC_SETTLE(sim);
   if (init < AC_INIT_RANDOM || init > AC_INIT_DOWN) return fail(AC_ERR_ARG, "bad init mode");
   sim->seed = seed;
   sim->init = init;
@@ -1415,6 +1715,7 @@ ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_en
   if (n <= 0 || !sims || !t_end) return fail(AC_ERR_ARG, "n > 0, sims and t_end are required");
   for (int i = 0; i < n; ++i) {
     if (!sims[i]) return fail(AC_ERR_ARG, "sims[%d] is NULL", i);
+    AC_SETTLE(sims[i]);
     if (sims[i]->f_B > 0) return fail(AC_ERR_ARG, "sims[%d] has snapshot frames: run it with ac_run_until_frames", i);
     if (sims[i]->model != 0) return fail(AC_ERR_ARG, "sims[%d] is not the 4-neighbour Ising array: batches hold those only", i);
     if (sims[i]->cfg.lb != sims[0]->cfg.lb) return fail(AC_ERR_ARG, "all handles must share a tile side");
@@ -1425,16 +1726,21 @@ ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_en
       if (sims[k] == sims[i]) return fail(AC_ERR_ARG, "handle %d appears twice", i);
   }
   std::vector<ac_sim*> keyv(sims, sims + n);
-  bool want_tb = true;
+  bool want_ep = true;
   for (int i = 0; i < n; ++i)
-    want_tb = want_tb && sims[i]->cfg.kernel == ac::kKernelRound && sims[i]->cfg.rounds == sims[0]->cfg.rounds &&
+    want_ep = want_ep && sims[i]->cfg.kernel == ac::kKernelEpoch && sims[i]->cfg.rounds == sims[0]->cfg.rounds &&
+              ep_applicable(sims[i]);
+  // epoch-kernel handles that cannot run on it run on the temporal-blocked round kernel
+  bool want_tb = !want_ep;
+  for (int i = 0; i < n; ++i)
+    want_tb = want_tb && sims[i]->cfg.kernel != ac::kKernelBlocked && sims[i]->cfg.rounds == sims[0]->cfg.rounds &&
               tb_applicable(sims[i]);
   BatchRunner* R = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_batch_mu);
     auto it = g_runners.find(keyv);
     if (it != g_runners.end()) {
-      if (it->second->tb != want_tb) {
+      if (it->second->tb != want_tb || it->second->ep != want_ep) {
         free_runner(it->second);
         g_runners.erase(it);
       } else {
@@ -1442,13 +1748,14 @@ ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_en
       }
     }
   }
-  if (want_tb) {
+  if (want_tb || want_ep) {
     if (!R) {
       R = new BatchRunner();
       R->sims = keyv;
-      R->tb = true;
+      R->tb = want_tb;
+      R->ep = want_ep;
       R->halo = sims[0]->cfg.rounds;
-      R->region = ac::tb_region_for(R->halo);
+      R->region = ac::tb_region_for(R->halo, sims[0]->cfg.lb == 128);
       R->lb = sims[0]->cfg.lb;
       if (sims[0]->stream == nullptr) {
         if (cudaStreamCreate(&R->own_stream) != cudaSuccess) {
@@ -1471,7 +1778,7 @@ ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_en
       std::lock_guard<std::mutex> lk(g_batch_mu);
       g_runners[keyv] = R;
     }
-    return batch_run_tb(n, sims, t_end, R);
+    return want_ep ? batch_run_ep(n, sims, t_end, R) : batch_run_tb(n, sims, t_end, R);
   }
   if (!R) {
     R = new BatchRunner();

@@ -87,22 +87,32 @@ struct DevCounters {
 //   ep_done[e]        tiles that completed epoch e
 //   ep_live[e]        tiles with an arrival before t_end left after epoch e
 // All zero before a launch; ep_done and ep_live hold max_epochs entries.
+// range: nrange (min, max) count pairs from count_range kernels; if any max - min >= limit
+// the kernel does no work and reports kEpWindow (the 16-bit count window of a region could
+// overflow during the call; the caller falls back to the exact one-round kernel).
 struct EpArgs {
   unsigned int* done;
   unsigned int* ep_done;
   unsigned int* ep_live;
   int max_epochs;
   long long watchdog_ns;
+  const unsigned int* range;
+  int nrange;
+  unsigned int limit;
 };
+constexpr int kEpWindow = 6;   // DevCounters::error of an epoch-kernel launch refused by the count check
 
 enum KernelKind { kKernelRound = 0, kKernelBlocked = 1, kKernelEpoch = 2 };
 
 // Temporal-blocked round kernel: a shared-memory region of side 96 (two CTAs per
 // SM) or 128 (one) holds a tile and a halo of depth D around it; tile side = region - 2D.
 constexpr int kTbMaxHalo = 16;
-inline int tb_region_for(int halo) { return halo <= 12 ? 96 : 128; }
+// wide = true selects the 128-wide region (512 threads, one CTA per SM) for any halo.
+inline int tb_region_for(int halo, bool wide = false) { return (halo <= 12 && !wide) ? 96 : 128; }
 // the q = 3 diamond's 13 order planes exist on the 128-wide region only
-inline int tb_region_for_model(int halo, int model, int q) { return (model == 2 && q == 3) ? 128 : tb_region_for(halo); }
+inline int tb_region_for_model(int halo, int model, int q, bool wide = false) {
+  return (model == 2 && q == 3) ? 128 : tb_region_for(halo, wide);
+}
 
 struct LaunchCfg {
   int kernel;       // KernelKind
@@ -136,8 +146,10 @@ cudaError_t launch_blocked(const LatDesc* d_desc, int nlat, int total_tiles, con
 cudaError_t launch_reduce(const LatDesc* host_desc, unsigned long long* d_out4, cudaStream_t s);
 cudaError_t launch_count_range(const LatDesc* host_desc, unsigned* d_out2, cudaStream_t s);
 cudaError_t launch_class_counts(const LatDesc* host_desc, unsigned long long* d_out10, cudaStream_t s);
+// max_blocks > 0 caps the grid (grid-stride loops): the asynchronous transfers run these
+// kernels beside another handle's persistent kernel on a few SMs only
 cudaError_t launch_unpack(const LatDesc* host_desc, int8_t* s_out, long long* t_out,
-                          unsigned int* n_out, cudaStream_t st);
+                          unsigned int* n_out, cudaStream_t st, int max_blocks = 0);
 cudaError_t launch_pack(const LatDesc* host_desc, const int8_t* s_in, const long long* t_in,
                         const unsigned int* n_in, cudaStream_t st);
 // Launch of the temporal-blocked round kernel.  The launch number (which fixes the
@@ -159,6 +171,9 @@ cudaError_t launch_tb(const LatDesc* d_desc, int nlat, int total_tiles, int regi
 // 16-byte aligned key buffers (the region rows are loaded by bulk asynchronous copies).
 cudaError_t launch_ep(const LatDesc* d_desc, int nlat, int total_tiles, int region, int halo, int rounds,
                       DevCounters* ctr, const EpArgs& ep, cudaStream_t s, int model = 0);
+// Stores a descriptor into device memory by a one-thread kernel (a launch parameter, no copy
+// engine: the copy engines may be busy with other streams' transfers).
+cudaError_t launch_store_desc(const LatDesc& d, LatDesc* out, cudaStream_t s);
 // Frames [K, K + count) were just opened: write each cell's spin into those whose tick
 // lies before the cell's next arrival (later commits write the others).
 cudaError_t launch_frames_fill(const LatDesc* host_desc, long long K, int count, cudaStream_t s);
@@ -166,7 +181,11 @@ cudaError_t launch_count_range_batch(const LatDesc* d_desc, int nlat, size_t max
                                      cudaStream_t s);
 int tb_grid(int region);   // resident CTAs of the temporal-blocked kernel
 cudaError_t launch_validate(const int8_t* s_in, const long long* t_in, size_t N, long long tmin, long long tmax,
-                            unsigned long long* d_first_bad, cudaStream_t st);
+                            unsigned long long* d_first_bad, cudaStream_t st, int max_blocks = 0);
+// launch_pack that writes nothing unless *d_bad == ~0 (device-side validation result)
+cudaError_t launch_pack_checked(const LatDesc* host_desc, const int8_t* s_in, const long long* t_in,
+                                const unsigned int* n_in, const unsigned long long* d_bad, cudaStream_t st,
+                                int max_blocks = 0);
 cudaError_t launch_exp_ticks(const uint32_t* x, unsigned long long* out, long long n, cudaStream_t s);
 cudaError_t launch_philox(unsigned long long seed, const uint32_t* c, const uint32_t* k, uint32_t w2,
                           uint32_t* out4, long long n, cudaStream_t s);

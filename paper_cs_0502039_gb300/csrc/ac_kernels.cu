@@ -1074,9 +1074,15 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       atomicAdd(&ctr->launched, 1u);
     }
   } else {
+    // the count check of the call: every lattice's count range must fit the 16-bit window
+    // (a refused launch claims no item: the work loop below then ends at once)
+    bool wide = false;
+    for (int i = tid; i < ep.nrange; i += NT) wide |= ep.range[2 * i + 1] - ep.range[2 * i] >= ep.limit;
+    wide = __syncthreads_or(wide) != 0;
     if (tid == 0) {
       mbar_init(ep_bar);
-      ep_ctl[0] = ep_claim(ctr, ep, total_tiles);
+      if (wide && blockIdx.x == 0) atomicCAS(&ctr->error, 0, kEpWindow);
+      ep_ctl[0] = wide ? ~0u : ep_claim(ctr, ep, total_tiles);
       ep_ctl[1] = 0u;
       ep_ctl[3] = ~0u;
       ep_ctl[5] = 0u;
@@ -1269,7 +1275,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     // ---- R synchronous rounds over the shrinking region
     const unsigned long long t2 = L.t2;
     const uint32_t two = L.two, seed_lo = L.seed_lo, seed_hi = L.seed_hi;
-    const unsigned* __restrict__ rates = L.rates;
+    // (the per-cell rate array is read through the descriptor at each commit: a pointer kept
+    // in registers across the commit loop costs spills)
     constexpr int W = Cfg::W;
     const int qn = (MODEL == 2) ? L.q : 1;     // rings lost per round
     // the q = 3 diamond has its own 13 planes and runs on the 128-wide region only (the
@@ -1472,9 +1479,9 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const Philox4 pa = philox_event(gia, base + c16a + 1u, 0u, seed_lo, seed_hi);
         const Philox4 pb = philox_event(gib, base + c16b + 1u, 0u, seed_lo, seed_hi);
         unsigned long long gapa = exp_ticks(pa.x, two), gapb = exp_ticks(pb.x, two);
-        if (rates) {
-          gapa = rated_gap(gapa, rates[gia]);
-          gapb = rated_gap(gapb, rates[gib]);
+        if (L.rates) {
+          gapa = rated_gap(gapa, L.rates[gia]);
+          gapb = rated_gap(gapb, L.rates[gib]);
         }
         const unsigned nsa = MODEL == 1 ? (tha >> moore_live<RW>(kpa)) & 1u : spa ^ (pa.y < tha ? 1u : 0u);
         const unsigned nsb = MODEL == 1 ? (thb >> moore_live<RW>(kpb)) & 1u : spb ^ (pb.y < thb ? 1u : 0u);
@@ -1529,7 +1536,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
           ns = sp ^ (b.y < thr[j + 5u * sp] ? 1u : 0u);
         }
         unsigned long long gap = exp_ticks(b.x, two);
-        if (rates) gap = rated_gap(gap, rates[gidx]);
+        if (L.rates) gap = rated_gap(gap, L.rates[gidx]);
         const unsigned long long nk = (key & ~1ull) + (gap << 1) + ns;
         *kp = nk;
         C[r * RW + cc] = (unsigned short)(c16 + 1u);
@@ -1744,6 +1751,18 @@ __global__ void pack_kernel(LatDesc L, const int8_t* s, const long long* t, cons
   }
 }
 
+// pack_kernel behind a device-side check: nothing is written unless *bad is still ~0 (the
+// validation of the staged state, asynchronous loads)
+__global__ void pack_checked_kernel(LatDesc L, const int8_t* s, const long long* t, const unsigned* n,
+                                    const unsigned long long* bad) {
+  if (*(volatile const unsigned long long*)bad != ~0ull) return;
+  const size_t N = (size_t)L.rows * L.cols;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+    L.key[c] = ((unsigned long long)t[c] << 1) | (s[c] > 0 ? 1ull : 0ull);
+    L.cnt[c] = n[c];
+  }
+}
+
 // first cell (lowest index) whose spin is not +-1 or whose tick is outside [tmin, tmax)
 __global__ void validate_kernel(const int8_t* s, const long long* t, size_t N, long long tmin, long long tmax,
                                 unsigned long long* first_bad) {
@@ -1920,9 +1939,11 @@ cudaError_t launch_count_range_batch(const LatDesc* d, int nlat, size_t max_cell
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(const LatDesc* h, int8_t* so, long long* to, unsigned* no, cudaStream_t st) {
+cudaError_t launch_unpack(const LatDesc* h, int8_t* so, long long* to, unsigned* no, cudaStream_t st,
+                          int max_blocks) {
   const size_t N = (size_t)h->rows * h->cols;
-  unpack_kernel<<<grid_for(N, 256), 256, 0, st>>>(*h, so, to, no);
+  const int g = max_blocks > 0 ? std::min(grid_for(N, 256), max_blocks) : grid_for(N, 256);
+  unpack_kernel<<<g, 256, 0, st>>>(*h, so, to, no);
   return cudaGetLastError();
 }
 
@@ -1994,6 +2015,13 @@ cudaError_t launch_tb(const LatDesc* d, int nlat, int total, int region, int hal
   }
 }
 
+__global__ void store_desc_kernel(LatDesc d, LatDesc* out) { *out = d; }
+
+cudaError_t launch_store_desc(const LatDesc& d, LatDesc* out, cudaStream_t s) {
+  store_desc_kernel<<<1, 1, 0, s>>>(d, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ep(const LatDesc* d, int nlat, int total, int region, int halo, int rounds, DevCounters* ctr,
                       const EpArgs& ep, cudaStream_t s, int model) {
   if (halo < 2 || (halo & 1) || rounds < 1 || rounds > halo || 4 * halo >= region || total < 1 ||
@@ -2033,9 +2061,18 @@ int tb_grid(int region) {
   return sms * (region <= 96 ? TbCfg<96>::MIN_CTAS : TbCfg<128>::MIN_CTAS);
 }
 
+cudaError_t launch_pack_checked(const LatDesc* h, const int8_t* si, const long long* ti, const unsigned* ni,
+                                const unsigned long long* d_bad, cudaStream_t st, int max_blocks) {
+  const size_t N = (size_t)h->rows * h->cols;
+  const int g = max_blocks > 0 ? std::min(grid_for(N, 256), max_blocks) : grid_for(N, 256);
+  pack_checked_kernel<<<g, 256, 0, st>>>(*h, si, ti, ni, d_bad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_validate(const int8_t* s_in, const long long* t_in, size_t N, long long tmin, long long tmax,
-                            unsigned long long* d_first_bad, cudaStream_t st) {
-  validate_kernel<<<grid_for(N, 256), 256, 0, st>>>(s_in, t_in, N, tmin, tmax, d_first_bad);
+                            unsigned long long* d_first_bad, cudaStream_t st, int max_blocks) {
+  const int g = max_blocks > 0 ? std::min(grid_for(N, 256), max_blocks) : grid_for(N, 256);
+  validate_kernel<<<g, 256, 0, st>>>(s_in, t_in, N, tmin, tmax, d_first_bad);
   return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ from paper_cs_0502039_gb300 import autotune  # noqa: E402
 def test_tune_small_class(tmp_path):
     path = str(tmp_path / "tune.json")
     entry = autotune.tune(200, 180, T=1.0, cache_path=path)
-    assert entry["kernel"] in (ac.AC_KERNEL_ROUND, ac.AC_KERNEL_BLOCKED)
+    assert entry["kernel"] in (ac.AC_KERNEL_ROUND, ac.AC_KERNEL_BLOCKED, ac.AC_KERNEL_EPOCH)
     assert entry["events_per_s"] > 0 and len(entry["measured"]) == len(autotune.CANDIDATES)
     cached = json.load(open(path))
     assert autotune.class_key(200, 180) in cached
@@ -26,3 +26,26 @@ def test_tune_small_class(tmp_path):
     with ac.Sim(200, 180, 0.44, 1.0, 0.0, 3) as sim:
         autotune.apply(sim, entry)
         sim.run_until(1)
+
+
+def test_beta_buckets_are_separate_classes(tmp_path):
+    path = str(tmp_path / "tune.json")
+    few = [c for c in autotune.CANDIDATES if c["kernel"] != ac.AC_KERNEL_BLOCKED][:3]
+    hot = autotune.tune(128, 128, T=1.0, cache_path=path, beta=0.3, candidates=few)
+    cold = autotune.tune(128, 128, T=1.0, cache_path=path, beta=0.6, candidates=few)
+    cached = json.load(open(path))
+    assert autotune.class_key(128, 128, 0.3) in cached and autotune.class_key(128, 128, 0.6) in cached
+    assert len(hot["measured"]) == len(cold["measured"]) == 3
+
+
+def test_tune_batch_agrees_on_every_lattice(tmp_path):
+    """Every batch candidate must reach the same per-lattice fingerprints (the batch runs
+    inside tune_batch raise otherwise); the choice is cached per batch class."""
+    path = str(tmp_path / "tune.json")
+    lats = [(64, 64, 0.3), (96, 130, 0.44), (200, 180, 0.6), (40, 72, 0.5)]
+    entry = autotune.tune_batch(lats, T=1.0, cache_path=path)
+    assert entry["kernel"] in (ac.AC_KERNEL_ROUND, ac.AC_KERNEL_EPOCH)
+    assert len(entry["measured"]) == len(autotune.BATCH_CANDIDATES)
+    assert autotune.batch_key(lats) in json.load(open(path))
+    only = autotune.tune_batch(lats, T=1.0, cache_path=path, batched_only=True)
+    assert only["batched"] and len(only["measured"]) == sum(c["batched"] for c in autotune.BATCH_CANDIDATES)

@@ -32,7 +32,8 @@ def _make(ws, kernel, rounds):
 
 
 @pytest.mark.parametrize("kernel,rounds", [(ac.AC_KERNEL_ROUND, 8), (ac.AC_KERNEL_ROUND, 4),
-                                           (ac.AC_KERNEL_BLOCKED, 1)])
+                                           (ac.AC_KERNEL_BLOCKED, 1), (ac.AC_KERNEL_EPOCH, 8),
+                                           (ac.AC_KERNEL_EPOCH, 4)])
 def test_batch_equals_oracle_and_alone(kernel, rounds):
     ws = workloads.batch_workload(n=10, lmin=32, lmax=200, T=3)
     sims = _make(ws, kernel, rounds)
@@ -51,10 +52,11 @@ def test_batch_equals_oracle_and_alone(kernel, rounds):
             s.close()
 
 
-def test_batch_with_different_horizons_and_sizes():
+@pytest.mark.parametrize("kernel", [ac.AC_KERNEL_ROUND, ac.AC_KERNEL_EPOCH])
+def test_batch_with_different_horizons_and_sizes(kernel):
     ws = workloads.batch_workload(n=6, lmin=40, lmax=300, T=4, seed=99)
     horizons = [int((1 + i) * T32) + 3 * i for i in range(len(ws))]
-    sims = _make(ws, ac.AC_KERNEL_ROUND, 8)
+    sims = _make(ws, kernel, 8)
     try:
         ac.ac_batch_run_until([s.handle for s in sims], horizons)
         for w, s, te in zip(ws, sims, horizons):
@@ -69,7 +71,7 @@ def test_batch_with_different_horizons_and_sizes():
 def test_served_jobs_equal_alone():
     reqs = workloads.serve_requests(rate=400.0, duration=0.06, lmin=64, lmax=320, tmin=2.0, tmax=9.0)
     assert len(reqs) >= 10
-    results, wall, server = srv_mod.serve(reqs, budget_bytes=8 << 20, slice_T=2.0, realtime=False)
+    results, wall, server = srv_mod.serve(reqs, budget_bytes=128 << 20, slice_T=2.0, realtime=False)
     assert len(results) == len(reqs)
     assert server.steps > 1
     for req, res in zip(sorted(reqs, key=lambda r: r["id"]), results):

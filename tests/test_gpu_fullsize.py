@@ -75,7 +75,7 @@ def test_4096_life_matches_oracle(rounds):
             _check_checkpoint(sim, cp, f"life rounds={rounds} T={cp['T']}")
 
 
-@pytest.mark.parametrize("kernel,rounds", [(ac.AC_KERNEL_BLOCKED, 1), (ac.AC_KERNEL_ROUND, 6)])
+@pytest.mark.parametrize("kernel,rounds", [(ac.AC_KERNEL_BLOCKED, 1), (ac.AC_KERNEL_ROUND, 6), (ac.AC_KERNEL_EPOCH, 8)])
 def test_4096_batched_run_matches_oracle(kernel, rounds):
     """The three temperatures in one batched call: one graph-captured blocked launch, or one work
     list of all tiles for the temporal-blocked round kernel (replayed launch chunks)."""
