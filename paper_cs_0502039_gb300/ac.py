@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libac.so")
+# AC_LIB_PATH selects another build of the library (the bounds-checked libac_check.so)
+LIB_PATH = os.environ.get("AC_LIB_PATH") or os.path.join(_PKG, "libac.so")
 
 AC_OK, AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA, AC_ERR_STALL, AC_ERR_STATE = range(6)
 AC_INIT_RANDOM, AC_INIT_UP, AC_INIT_DOWN = 0, 1, 2

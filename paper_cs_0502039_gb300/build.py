@@ -1,7 +1,10 @@
 """Build libac.so in-tree for GB300 (sm_103a) with nvcc.
 
-The two translation units (kernels, host runtime) are compiled in parallel and
-linked into ``paper_cs_0502039_gb300/libac.so`` (cudart linked statically).
+The translation units (kernels, host runtime, allocation-free entry, time-only model) are
+compiled in parallel and linked into ``paper_cs_0502039_gb300/libac.so`` (cudart linked
+statically).  The same sources are also built with ``-DAC_CHECK`` into ``libac_check.so``:
+the bounds-checked variant whose kernels check every index they compute and report a
+violation as AC_ERR_STATE (the tests load it in a subprocess through AC_LIB_PATH).
 """
 import os
 import subprocess
@@ -11,13 +14,14 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libac.so")
+LIB_CHECK = os.path.join(PKG, "libac_check.so")
 SOURCES = ["ac_kernels.cu", "ac_api.cu", "ac_static.cu", "ac_time.cu"]
 HEADERS = ["ac_device.cuh", "ac_internal.h"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I", INCLUDE, "-I", CSRC]
+VARIANTS = ((LIB, os.path.join(PKG, "_build"), []), (LIB_CHECK, os.path.join(PKG, "_build_check"), ["-DAC_CHECK"]))
 
 
 def _nvcc():
@@ -27,37 +31,38 @@ def _nvcc():
     return "nvcc"
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, "ac.h")]
+    t = os.path.getmtime(lib)
+    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, "ac.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
+    todo = [v for v in VARIANTS if force or _stale(v[0])]
+    if not todo:
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     procs = []
-    objs = []
-    for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        objs.append(obj)
-        cmd = [nvcc, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
-        if verbose:
-            print(" ".join(cmd), flush=True)
-        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    for lib, bdir, extra in todo:
+        os.makedirs(bdir, exist_ok=True)
+        for src in SOURCES:
+            obj = os.path.join(bdir, src.replace(".cu", ".o"))
+            cmd = [nvcc, *extra, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+            if verbose:
+                print(" ".join(cmd), flush=True)
+            procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     for cmd, p in procs:
         out, _ = p.communicate()
         if p.returncode != 0:
             sys.stderr.write(out.decode(errors="replace"))
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", *objs, "-o", tmp]
-    subprocess.run(link, check=True)
-    os.replace(tmp, LIB)
+    for lib, bdir, _ in todo:
+        objs = [os.path.join(bdir, src.replace(".cu", ".o")) for src in SOURCES]
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", *objs, "-o", tmp], check=True)
+        os.replace(tmp, lib)
     return LIB
 
 

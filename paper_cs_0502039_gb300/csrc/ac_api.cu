@@ -347,7 +347,20 @@ ac_status create_one(ac_lattice lat, double beta, double J, double h, uint64_t s
   return AC_OK;
 }
 
+// Bounds-checked build: AC_ERR_STATE if the kernels recorded an index violation since the
+// last check (a no-op in the production build).
+ac_status check_bounds() {
+#ifdef AC_CHECK
+  unsigned long long word = 0;
+  AC_CUDA(ac::read_check_word(&word));
+  if (word) return fail(AC_ERR_STATE, "bounds check: site %llu, index %llu", word >> 40, word & 0xFFFFFFFFFFull);
+#endif
+  return AC_OK;
+}
+
 ac_status accumulate(ac_sim* s, const ac::DevCounters& c, float ms, bool round_kernel) {
+  const ac_status bc = check_bounds();
+  if (bc != AC_OK) return bc;
   s->rounds += c.rounds;
   s->scanned += c.scanned;
   s->enabled += c.enabled;
@@ -866,7 +879,7 @@ ac_status batch_run_tb(int32_t n, ac_sim* const* sims, const int64_t* t_end, Bat
   sims[0]->rounds += c.rounds;
   sims[0]->scanned += c.scanned;
   sims[0]->enabled += c.enabled;
-  return AC_OK;
+  return check_bounds();
 }
 
 // Batched epoch kernel: one persistent launch over the tiles of every handle (one work
@@ -999,7 +1012,7 @@ ac_status batch_run_ep(int32_t n, ac_sim* const* sims, const int64_t* t_end, Bat
   sims[0]->enabled += sum.enabled;
   sims[0]->visits += sum.visits;
   sims[0]->polls += sum.polls;
-  return AC_OK;
+  return check_bounds();
 }
 
 ac_status run_core(ac_sim* sim, long long t_end) {
@@ -1874,7 +1887,7 @@ ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_en
   sims[0]->enabled += c.enabled;
   sims[0]->visits += c.visits;
   sims[0]->polls += c.polls;
-  return AC_OK;
+  return check_bounds();
 }
 
 ac_status ac_dev_exp_ticks(const uint32_t* x, uint64_t* out, int64_t n) {
