@@ -900,8 +900,10 @@ def configs_measurement():
     from paper_cs_0502039_gb300 import autotune
     R, B = ac.AC_KERNEL_ROUND, ac.AC_KERNEL_BLOCKED
 
-    def measure(rows, cols, init, seed, beta, h, T, kern, lb, rounds, polls, warm_T):
+    def measure(rows, cols, init, seed, beta, h, T, kern, lb, rounds, polls, warm_T, early=0):
         with ac.Sim(rows, cols, beta, 1.0, h, seed, init=init, kernel=kern, Lb=lb, rounds=rounds, polls=polls) as s:
+            if early:
+                s.set_option(ac.AC_OPT_EARLY_REJECT, 1)
             s.run_until(warm_T)
             s.reset(seed, init)
             torch.cuda.synchronize()
@@ -910,7 +912,8 @@ def configs_measurement():
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
             st = s.stats()
-        return {"kernel": "blocked" if kern == B else "round", "Lb": lb, "rounds": rounds, "polls": polls,
+        return {"kernel": kernel_name(ac, kern), "Lb": lb, "rounds": rounds, "polls": polls,
+                "early_reject": bool(early), "early_commits": st["early_commits"], "launches": st["launches"],
                 "events": st["events"], "device_ms": st["device_ms"], "wall_ms": 1000 * wall,
                 "events_per_s": st["events"] / (st["device_ms"] / 1000.0),
                 "hbm_frac_effective": BYTES_PER_EVENT * st["events"] / (st["device_ms"] / 1000.0) / 1e9
@@ -922,6 +925,10 @@ def configs_measurement():
     cfgs = [(tuned["kernel"], tuned["Lb"], tuned["rounds"], tuned["polls"]), (R, 64, 6, 0),
             (B, 32, 1, 8), (B, 64, 1, 8), (B, 128, 1, 8)]
     out["c3"] = [measure(16384, 16384, 1, 3, 1.0, 0.05, 20, k, lb, r, p, 1) for k, lb, r, p in cfgs]
+    # BKL on / off: the one-round kernel (one synchronous round of Fig. 3.2 per launch) with and
+    # without early commits of certain rejections
+    out["c3_bkl"] = [measure(16384, 16384, 1, 3, 1.0, 0.05, 20, R, 64, 1, 0, 1, early) for early in (0, 1)]
+    out["c2_bkl"] = [measure(4096, 4096, 0, 7, 0.4407, 0.0, 50, R, 64, 1, 0, 1, early) for early in (0, 1)]
     out["c3_autotuned"] = {k: tuned[k] for k in ("kernel", "Lb", "rounds", "polls")}
     return out
 

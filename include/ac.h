@@ -238,6 +238,8 @@ typedef struct {
   int32_t kernel, Lb, threads, rounds_per_launch;
   int32_t grid;             /* CTAs of the last launch */
   int32_t ctas_per_sm;      /* blocked kernel: resident CTAs per SM */
+  uint64_t early_commits;   /* one-round kernel with AC_OPT_EARLY_REJECT: arrivals committed
+                               early as certain rejections */
 } ac_stats_t;
 
 /* Statistics and observables of the handle (runs a reduction on the device). */
@@ -352,8 +354,25 @@ ac_status ac_frames_status(const ac_sim* sim, int64_t* next_K, int32_t* B, int64
  *                        boundary commits (blocked kernel) and of tile epochs (epoch
  *                        kernel), so that a lattice of several tiles cannot finish
  *                        and the watchdog must end the run with AC_ERR_STALL (no
- *                        fault, no unbounded wait); 0 restores it. */
-enum { AC_OPT_WATCHDOG_NS = 1, AC_OPT_MAX_ROUNDS = 2, AC_OPT_DROP_PUBLISH = 3 };
+ *                        fault, no unbounded wait); 0 restores it.
+ *   AC_OPT_EARLY_REJECT  1: the round kernel with rounds = 1 (one synchronous round of
+ *                        Fig. 3.2 per launch) also commits, out of (tick, index) order,
+ *                        every pending arrival that is a rejection whatever the spins of
+ *                        the neighbours that precede it turn out to be -- the observation
+ *                        behind the BKL algorithm of Sec. 3 that at low temperature most
+ *                        arrivals change nothing.  Such an arrival keeps the cell's spin,
+ *                        so no neighbour's decision depends on its order; the trajectory is
+ *                        unchanged.  The neighbours that do not precede the cell keep their
+ *                        spins until after its arrival, so the number j of up neighbours at
+ *                        the arrival lies in [their up count, that + the number that
+ *                        precede it]; the arrival is a certain rejection iff
+ *                        u >= thr[j + 5 (s > 0)] for every such j.  A per-cell byte (rows *
+ *                        cols bytes of device memory, allocated on first use) caches the j
+ *                        at which the pending arrival would flip; it is refilled at the
+ *                        start of each run call and kept by the commits (one extra
+ *                        Philox block per arrival).  The Ising array only; other kernels
+ *                        ignore the option.  0 (default) turns it off. */
+enum { AC_OPT_WATCHDOG_NS = 1, AC_OPT_MAX_ROUNDS = 2, AC_OPT_DROP_PUBLISH = 3, AC_OPT_EARLY_REJECT = 4 };
 ac_status ac_set_option(ac_sim* sim, int32_t option, int64_t value);
 
 /* Free all memory of the handle (NULL is ignored). */

@@ -19,7 +19,7 @@ LIB_PATH = os.environ.get("AC_LIB_PATH") or os.path.join(_PKG, "libac.so")
 AC_OK, AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA, AC_ERR_STALL, AC_ERR_STATE = range(6)
 AC_INIT_RANDOM, AC_INIT_UP, AC_INIT_DOWN = 0, 1, 2
 AC_KERNEL_ROUND, AC_KERNEL_BLOCKED, AC_KERNEL_EPOCH = 0, 1, 2
-AC_OPT_WATCHDOG_NS, AC_OPT_MAX_ROUNDS, AC_OPT_DROP_PUBLISH = 1, 2, 3
+AC_OPT_WATCHDOG_NS, AC_OPT_MAX_ROUNDS, AC_OPT_DROP_PUBLISH, AC_OPT_EARLY_REJECT = 1, 2, 3, 4
 TICKS_PER_UNIT = 1 << 32
 
 _STATUS = {AC_ERR_ARG: "AC_ERR_ARG", AC_ERR_OOM: "AC_ERR_OOM", AC_ERR_CUDA: "AC_ERR_CUDA",
@@ -45,7 +45,7 @@ class ac_stats_t(ctypes.Structure):
                 ("total_counts", ctypes.c_uint64), ("t_done", ctypes.c_int64),
                 ("kernel", ctypes.c_int32), ("Lb", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("rounds_per_launch", ctypes.c_int32), ("grid", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("early_commits", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

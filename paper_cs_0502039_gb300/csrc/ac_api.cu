@@ -102,6 +102,8 @@ struct ac_sim {
   unsigned long long* d_red = nullptr;
   unsigned int* d_ep = nullptr;             // epoch kernel: tile done words, per-epoch counts
   size_t ep_cap = 0;
+  unsigned char* d_fmask = nullptr;         // early commits of certain rejections: flip masks
+  bool early_reject = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // asynchronous state transfers (ac_load_state_async / ac_read_state_async) on a caller's stream
   cudaEvent_t ev_work = nullptr, ev_load = nullptr, ev_read = nullptr;
@@ -121,7 +123,7 @@ struct ac_sim {
   long long f_dt = 0, f_K = 0;
   // accumulated statistics
   unsigned long long events = 0, rounds = 0, launches = 0, scanned = 0, enabled = 0, visits = 0,
-                     polls = 0, global_rounds = 0, enabled_r1 = 0;
+                     polls = 0, global_rounds = 0, enabled_r1 = 0, early = 0;
   double device_ms = 0.0;
   int last_grid = 0, ctas_per_sm = 0;
   int drop_publish = 0;
@@ -279,6 +281,7 @@ void free_sim(ac_sim* s) {
   cudaFree(s->d_hist);
   cudaFree(s->d_red);
   cudaFree(s->d_ep);
+  cudaFree(s->d_fmask);
   cudaFree(s->frames);
   cudaFree(s->d_rates);
   if (s->frame_host) cudaFreeHost(s->frame_host);
@@ -366,6 +369,7 @@ ac_status accumulate(ac_sim* s, const ac::DevCounters& c, float ms, bool round_k
   s->enabled += c.enabled;
   s->visits += c.visits;
   s->polls += c.polls;
+  s->early += c.early;
   s->device_ms += ms;
   if (round_kernel) {
     s->launches += c.launched;
@@ -656,7 +660,58 @@ ac_status run_ep(ac_sim* s, long long t_end, bool* fallback) {
   return AC_OK;
 }
 
+// One synchronous round per launch with early commits of certain rejections (the one-round
+// kernel's exact path, AC_OPT_EARLY_REJECT): the flip masks of the cells' pending arrivals
+// are filled at the start of the call and kept by the commits.
+ac_status run_round_er(ac_sim* s, long long t_end) {
+  const size_t N = s->ncells();
+  if (!s->d_fmask && cudaMalloc(&s->d_fmask, N) != cudaSuccess) {
+    cudaGetLastError();
+    s->d_fmask = nullptr;
+    return fail(AC_ERR_OOM, "flip masks (%zu bytes) allocation failed", N);
+  }
+  const int total = s->tiles();
+  ac::LatDesc d = s->host_desc(t_end, 0);
+  d.fmask = s->d_fmask;
+  AC_CUDA(cudaMemcpyAsync(s->d_desc, &d, sizeof d, cudaMemcpyHostToDevice, s->stream));
+  AC_CUDA(cudaMemsetAsync(s->d_ctr, 0, sizeof(ac::DevCounters), s->stream));
+  AC_CUDA(ac::launch_publish(s->d_desc, 1, total, s->cfg.lb, 0, s->stream));
+  AC_CUDA(cudaEventRecord(s->ev0, s->stream));
+  AC_CUDA(ac::launch_fmask(&d, s->stream));
+  const double span = (double)(t_end - s->t_done) / kTicksPerUnit;
+  int chunk = (int)std::min(4096.0, 9.0 * std::ceil(span) + 16.0);
+  int launch_idx = 0, parity = 0;
+  unsigned active = 1;
+  for (;;) {
+    for (int i = 0; i < chunk; ++i) {
+      AC_CUDA(ac::launch_round_er(s->d_desc, 1, total, s->cfg.lb, parity, launch_idx, s->d_ctr, s->stream));
+      parity ^= 1;
+      ++launch_idx;
+    }
+    AC_CUDA(cudaMemcpyAsync(&active, &s->d_ctr->active[(launch_idx - 1) % 3], sizeof active,
+                            cudaMemcpyDeviceToHost, s->stream));
+    AC_CUDA(cudaStreamSynchronize(s->stream));
+    if (active == 0) break;
+    if ((double)launch_idx > 64.0 * (9.0 * std::ceil(span) + 16.0) + 4096.0)
+      return fail(AC_ERR_STALL, "round kernel: no completion after %d launches", launch_idx);
+    chunk = 16;
+  }
+  AC_CUDA(cudaEventRecord(s->ev1, s->stream));
+  ac::DevCounters c{};
+  AC_CUDA(cudaMemcpyAsync(&c, s->d_ctr, sizeof c, cudaMemcpyDeviceToHost, s->stream));
+  AC_CUDA(cudaStreamSynchronize(s->stream));
+  float ms = 0.f;
+  AC_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+  s->last_grid = total;
+  const int saved = s->cfg.rounds;
+  s->cfg.rounds = 0;   // not the plain synchronous rounds: no round history or Sec. 4 efficiency
+  const ac_status st = accumulate(s, c, ms, true);
+  s->cfg.rounds = saved;
+  return st;
+}
+
 ac_status run_round(ac_sim* s, long long t_end) {
+  if (s->model == 0 && s->early_reject && s->cfg.rounds == 1) return run_round_er(s, t_end);
   if (s->model != 0) {
     // the Life automaton and the q-th degree neighbourhood run on the temporal-blocked
     // kernel only (their enable tests need the diagonal / farther cells the region holds)
@@ -1627,6 +1682,7 @@ ac_status ac_stats(const ac_sim* sim, ac_stats_t* o) {
   o->rounds_per_launch = sim->cfg.kernel != ac::kKernelBlocked ? sim->cfg.rounds : sim->cfg.refresh;
   o->grid = sim->last_grid;
   o->ctas_per_sm = sim->ctas_per_sm;
+  o->early_commits = sim->early;
   return AC_OK;
 }
 
@@ -1668,7 +1724,7 @@ ac_status ac_reset(ac_sim* sim, uint64_t seed, int32_t init) {
   sim->t_done = 0;
   frames_off(sim);
   sim->events = sim->rounds = sim->launches = sim->scanned = sim->enabled = sim->visits = sim->polls = 0;
-  sim->global_rounds = sim->enabled_r1 = 0;
+  sim->global_rounds = sim->enabled_r1 = sim->early = 0;
   sim->device_ms = 0.0;
   drop_runners_of(sim);
   return AC_OK;
@@ -1687,6 +1743,10 @@ ac_status ac_set_option(ac_sim* sim, int32_t option, int64_t value) {
       break;
     case AC_OPT_DROP_PUBLISH:
       sim->drop_publish = value ? 1 : 0;
+      break;
+    case AC_OPT_EARLY_REJECT:
+      if (value && sim->model != 0) return fail(AC_ERR_ARG, "early rejection applies to the Ising array");
+      sim->early_reject = value != 0;
       break;
     default:
       return fail(AC_ERR_ARG, "unknown option %d", option);

@@ -59,6 +59,9 @@ struct LatDesc {
   // per-cell rates (law (A) of Sec. 2): cell c's gaps are max(1, floor(e * rates[c] / 2^20))
   // for the rate-1 gap e, i.e. rate 2^20 / rates[c]; nullptr = every cell at rate 1
   const unsigned* rates;
+  // early commits of certain rejections (one-round kernel): flip mask of each cell's pending
+  // arrival, bit j set iff it flips with j up neighbours; nullptr = off
+  unsigned char* fmask;
 };
 
 // Device counters of one run call (zeroed by the host before the call).
@@ -77,6 +80,7 @@ struct DevCounters {
   unsigned int blocks_done;     // temporal-blocked kernel: CTAs finished in the current launch
   unsigned long long kmin[3];   // temporal-blocked kernel with frames: smallest output key of a
                                 // launch (mod-3 ring like active; the host presets all to ~0)
+  unsigned long long early;     // one-round kernel: arrivals committed early as certain rejections
   unsigned int next_item;       // epoch kernel: next work item to claim
   unsigned int stop_epoch;      // epoch kernel: epochs after which no arrival before t_end is left
                                 // (the host presets ~0)
@@ -136,6 +140,11 @@ void make_thresholds(double beta, double J, double h, uint32_t thr[10]);
 size_t tile_smem_bytes(int lb);
 int blocked_max_ctas(int lb, int* per_sm);   // resident CTAs of the blocked kernel
 cudaError_t launch_init(const LatDesc* host_desc, int init_mode, cudaStream_t s);
+// One synchronous round (Fig. 3.2) over Lb tiles with early commits of certain rejections
+// (LatDesc::fmask set; see round_er_kernel), and the pass that fills fmask for every cell.
+cudaError_t launch_round_er(const LatDesc* d_desc, int nlat, int total_tiles, int lb, int parity, int launch_idx,
+                            DevCounters* ctr, cudaStream_t s);
+cudaError_t launch_fmask(const LatDesc* host_desc, cudaStream_t s);
 cudaError_t launch_publish(const LatDesc* d_desc, int nlat, int total_tiles, int lb, int to_pub2,
                            cudaStream_t s);
 cudaError_t launch_round(const LatDesc* d_desc, int nlat, int total_tiles, const LaunchCfg& cfg,

@@ -535,6 +535,222 @@ __global__ void __launch_bounds__(4 * LB) round_kernel(const LatDesc* __restrict
   }
 }
 
+// ---- early commits of certain rejections (the idea behind BKL, Sec. 3 "The BKL algorithm":
+// at low temperature most arrivals change nothing).  A pending arrival whose flip decision is
+// a rejection for every neighbour configuration still possible at its time may be committed
+// before the neighbours that precede it: its spin does not change, so no neighbour's
+// decision depends on whether it came first, and its new tick only lets neighbours that now
+// precede it go ahead.  The neighbours that do not precede the cell keep their spins until
+// after its arrival; those that precede it may still change, so the number j of up
+// neighbours at the arrival lies in [fixed up, fixed up + preceding].  fmask[c] holds the j
+// for which the cell's pending arrival would flip (bit j: u < thr[j + 5 (s > 0)], u the
+// pending acceptance uniform): the arrival is a certain rejection iff no bit of that range
+// is set.  Early commits can be adjacent to each other and to local minima, so the work list
+// holds every cell; no order planes are kept (one synchronous round per launch).
+
+// flip mask of the pending arrival of a cell with spin bit `up` and count n (block n + 1)
+__device__ __forceinline__ unsigned flip_mask(uint32_t c, unsigned n, unsigned up, const unsigned* thr,
+                                              uint32_t seed_lo, uint32_t seed_hi) {
+  const uint32_t u = philox_event(c, n + 1u, 0u, seed_lo, seed_hi).y;
+  unsigned m = 0;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) m |= (u < thr[j + 5 * up] ? 1u : 0u) << j;
+  return m;
+}
+
+__global__ void fmask_kernel(LatDesc L) {
+  const size_t N = (size_t)L.rows * L.cols;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x)
+    L.fmask[c] = (unsigned char)flip_mask((uint32_t)c, L.cnt[c], (unsigned)L.key[c] & 1u, L.thr, L.seed_lo, L.seed_hi);
+}
+
+template <int LB>
+struct TileShapeER {   // TileShape with a work list for every cell of the tile
+  static constexpr int LIST = LB * LB;
+  static constexpr size_t kBytes = TileShape<LB>::kBytes, cBytes = TileShape<LB>::cBytes;
+  static constexpr size_t lBytes = ((size_t(LIST) * 2 + 15) / 16) * 16;
+  static constexpr size_t bytes = kBytes + cBytes + lBytes + TileShape<LB>::mBytes;
+};
+
+// Enable test with early commits over the thread's column segment; list entries carry bit 15
+// for an early commit (a certain rejection).  Returns whether any cell is still live.
+template <int LB>
+__device__ __forceinline__ bool scan_tile_er(unsigned long long* K, unsigned short* list, const LatDesc& L,
+                                             const Geom& g, unsigned long long t2, unsigned int* n_slot,
+                                             unsigned long long& scanned, unsigned long long& early) {
+  constexpr int P = TileShape<LB>::P;
+  const int c = threadIdx.x % LB;
+  const int grp = threadIdx.x / LB;
+  const int rpg = (g.h + 3) >> 2;
+  const int rb = grp * rpg;
+  const int re = min(g.h, rb + rpg);
+  unsigned mask = 0, emask = 0;
+  bool live_any = false;
+  if (c < g.w && rb < re) {
+    const unsigned long long* col = K + (rb + 1) * P + (c + 1);
+    unsigned long long up = col[-P];
+    unsigned long long cur = col[0];
+    for (int r = rb; r < re; ++r) {
+      const unsigned long long down = col[P];
+      const unsigned long long left = col[-1];
+      const unsigned long long right = col[1];
+      const unsigned long long hi = cur | 1ull, lo = cur & ~1ull;
+      const bool live = cur < t2;
+      // the cell precedes each neighbour (the enable test of Fig. 3.2, term by term)
+      const bool cu = hi < up, cl = hi < left, cr = lo <= right, cd = lo <= down;
+      const bool en = live & cu & cl & cr & cd;
+      bool er = false;
+      if (live && !en) {
+        const unsigned upfix = (cu ? (unsigned)up & 1u : 0u) + (cl ? (unsigned)left & 1u : 0u) +
+                               (cr ? (unsigned)right & 1u : 0u) + (cd ? (unsigned)down & 1u : 0u);
+        const unsigned unk = (cu ? 0u : 1u) + (cl ? 0u : 1u) + (cr ? 0u : 1u) + (cd ? 0u : 1u);
+        const unsigned range = ((2u << unk) - 1u) << upfix;
+        const size_t gi = ACI((size_t)(g.r0 + r) * L.cols + g.c0 + c, (long long)L.rows * L.cols, 28);
+        er = (L.fmask[gi] & range) == 0u;
+      }
+      live_any |= live;
+      mask |= (unsigned)(en | er) << (r - rb);
+      emask |= (unsigned)er << (r - rb);
+      up = cur;
+      cur = down;
+      col += P;
+    }
+    scanned += (unsigned long long)(re - rb);
+    early += (unsigned long long)__popc(emask);
+  }
+  const int lane = threadIdx.x & 31;
+  const int cnt = __popc(mask);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
+  }
+  int base = 0;
+  if (lane == 31 && incl) base = (int)atomicAdd(n_slot, (unsigned)incl);
+  base = __shfl_sync(kFull, base, 31);
+  int off = base + incl - cnt;
+  while (mask) {
+    const int b = __ffs(mask) - 1;
+    mask &= mask - 1;
+    list[ACI(off++, TileShapeER<LB>::LIST, 29)] =
+        (unsigned short)(((rb + b) << 8) | c | (((emask >> b) & 1u) << 15));
+  }
+  return live_any;
+}
+
+// One synchronous round of Fig. 3.2 per launch with early commits of certain rejections
+// (keys and counts read from and written to HBM; halos from the previous launch's edge
+// words).  Each commit also writes the flip mask of the cell's next pending arrival.
+template <int LB>
+__global__ void __launch_bounds__(4 * LB) round_er_kernel(const LatDesc* __restrict__ lats, int nlat, int parity,
+                                                          int launch_idx, DevCounters* ctr) {
+  using S = TileShapeER<LB>;
+  constexpr int P = TileShape<LB>::P;
+  constexpr int NT = TileShape<LB>::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned long long* K = reinterpret_cast<unsigned long long*>(smem_raw);
+  unsigned short* list = reinterpret_cast<unsigned short*>(smem_raw + S::kBytes + S::cBytes);
+  unsigned int* n_en = reinterpret_cast<unsigned int*>(smem_raw + S::kBytes + S::cBytes + S::lBytes);
+  unsigned int* thr = n_en + 2;
+  if (launch_idx > 0) {
+    if (*(volatile unsigned*)&ctr->active[(launch_idx + 2) % 3] == 0u) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctr->active[(launch_idx + 1) % 3] = 0u;
+    atomicAdd(&ctr->launched, 1u);
+  }
+  const int tile = blockIdx.x;
+  const LatDesc& L = lats[find_lattice(lats, nlat, tile)];
+  const int t = tile - L.tile_base;
+  const Geom g = tile_geom(L, t);
+  const unsigned long long* pub_in = parity ? L.pub2 : L.pub;
+  unsigned long long* pub_out = (parity ? L.pub : L.pub2) + (size_t)t * 4 * LB;
+  const unsigned long long t2 = L.t2;
+  {
+    const int c = threadIdx.x % LB;
+    if (c < g.w)
+      for (int r = threadIdx.x / LB; r < g.h; r += 4)
+        K[(r + 1) * P + c + 1] = L.key[ACI((size_t)(g.r0 + r) * L.cols + g.c0 + c, (long long)L.rows * L.cols, 21)];
+  }
+  if (threadIdx.x < 10) thr[threadIdx.x] = L.thr[threadIdx.x];
+  if (threadIdx.x == 0) n_en[0] = 0u;
+  const Smem<LB> sm(smem_raw);   // K and the halo layout of the tile engine
+  const HaloSlot hs = halo_slot<LB>(L, g, pub_in);
+  __syncthreads();
+  fill_halo<LB, false>(sm, hs);
+  __syncthreads();
+
+  unsigned long long scanned = 0, early = 0;
+  const bool live = scan_tile_er<LB>(K, list, L, g, t2, &n_en[0], scanned, early);
+  const int any_live = __syncthreads_or(live);
+  const int n = (int)n_en[0];
+  if (n > 0 && any_live) {
+    for (int i = threadIdx.x; i < n; i += NT) {
+      const unsigned e = list[ACI(i, S::LIST, 29)];
+      const bool er = (e >> 15) & 1u;
+      const int r = (int)((e >> 8) & 127u), c = (int)(e & 255u);
+      ACK(r < g.h && c < g.w, 25, e);
+      unsigned long long* kp = K + (r + 1) * P + (c + 1);
+      const unsigned long long key = *kp;
+      const unsigned sp = (unsigned)key & 1u;
+      const uint32_t gidx = (uint32_t)ACI((uint32_t)(g.r0 + r) * (uint32_t)L.cols + (uint32_t)(g.c0 + c),
+                                          (long long)L.rows * L.cols, 26);
+      const unsigned n_old = L.cnt[gidx];
+      const Philox4 b = philox_event(gidx, n_old + 1u, 0u, L.seed_lo, L.seed_hi);
+      unsigned flip = 0u;
+      if (!er) {   // a local minimum: the heat-bath decision on the neighbours' spins
+        const unsigned j = ((unsigned)kp[-P] & 1u) + ((unsigned)kp[P] & 1u) + ((unsigned)kp[-1] & 1u) +
+                           ((unsigned)kp[1] & 1u);
+        flip = b.y < thr[ACI(j + 5u * sp, 10, 9)] ? 1u : 0u;
+      }
+      unsigned long long gap = exp_ticks(b.x, L.two);
+      if (L.rates) gap = rated_gap(gap, L.rates[gidx]);
+      const unsigned ns = sp ^ flip;
+      const unsigned long long nk = (key & ~1ull) + (gap << 1) + ns;
+      *kp = nk;
+      if (L.f_open) write_frames(frame_view(L), gidx, key >> 1, nk >> 1, ns);
+      L.key[gidx] = nk;
+      L.cnt[gidx] = n_old + 1u;
+      L.fmask[gidx] = (unsigned char)flip_mask(gidx, n_old + 1u, ns, thr, L.seed_lo, L.seed_hi);
+      if (L.tr == 1) {                    // vertical self-wrap: keep the mirrored halo rows live
+        if (r == 0) K[(g.h + 1) * P + c + 1] = nk - 2ull;
+        if (r == g.h - 1) K[c + 1] = nk + 2ull;
+      }
+      if (L.tc == 1) {
+        if (c == 0) K[(r + 1) * P + g.w + 1] = nk - 2ull;
+        if (c == g.w - 1) K[(r + 1) * P] = nk + 2ull;
+      }
+    }
+    __syncthreads();
+  }
+  bool unfinished = false;
+  {
+    const int c = threadIdx.x % LB;
+    if (c < g.w)
+      for (int r = threadIdx.x / LB; r < g.h; r += 4) unfinished |= K[(r + 1) * P + c + 1] < t2;
+  }
+  write_edges<LB>(sm, g, pub_out);
+  const int any_unfinished = __syncthreads_or(unfinished);
+  for (int o = 16; o > 0; o >>= 1) {
+    scanned += __shfl_down_sync(kFull, scanned, o);
+    early += __shfl_down_sync(kFull, early, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (scanned) atomicAdd(&ctr->scanned, scanned);
+    if (early) atomicAdd(&ctr->early, early);
+  }
+  if (threadIdx.x == 0) {
+    if (any_unfinished) atomicAdd(&ctr->active[launch_idx % 3], 1u);
+    if (n > 0 && any_live) {
+      atomicAdd(&ctr->events, (unsigned long long)n);
+      atomicAdd(L.events, (unsigned long long)n);
+      atomicAdd(&ctr->enabled, (unsigned long long)n);
+      atomicAdd(&ctr->rounds, 1ull);
+    }
+  }
+}
+
 // (b) Blocked persistent kernel (cooperative launch: all CTAs co-resident).
 template <int LB>
 __global__ void __launch_bounds__(4 * LB) blocked_kernel(const LatDesc* __restrict__ lats, int nlat,
@@ -1915,6 +2131,36 @@ int blocked_max_ctas(int lb, int* per_sm) {
     case 128: return blocked_resident<128>(per_sm);
     default: return 0;
   }
+}
+
+template <int LB>
+cudaError_t round_er_launch(const LatDesc* d, int nlat, int total, int parity, int launch_idx, DevCounters* ctr,
+                            cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(round_er_kernel<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TileShapeER<LB>::bytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  round_er_kernel<LB><<<total, 4 * LB, TileShapeER<LB>::bytes, s>>>(d, nlat, parity, launch_idx, ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round_er(const LatDesc* d, int nlat, int total, int lb, int parity, int launch_idx,
+                            DevCounters* ctr, cudaStream_t s) {
+  switch (lb) {
+    case 32: return round_er_launch<32>(d, nlat, total, parity, launch_idx, ctr, s);
+    case 64: return round_er_launch<64>(d, nlat, total, parity, launch_idx, ctr, s);
+    case 128: return round_er_launch<128>(d, nlat, total, parity, launch_idx, ctr, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fmask(const LatDesc* h, cudaStream_t s) {
+  const size_t N = (size_t)h->rows * h->cols;
+  fmask_kernel<<<grid_for(N, 256), 256, 0, s>>>(*h);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_init(const LatDesc* h, int init_mode, cudaStream_t s) {

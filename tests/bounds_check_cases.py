@@ -24,6 +24,12 @@ def main() -> int:
         for kernel, Lb, rounds, polls in configs:
             s, t, n, _ = lib_state(rows, cols, 0.44, 1.0, 0.05, seed, 3, 0, kernel, Lb, rounds, polls)
             assert_same(ref, s, t, n, f"{rows}x{cols} kernel={kernel} Lb={Lb} rounds={rounds}")
+    for rows, cols, seed in lattices[:5]:       # early commits of certain rejections (one-round kernel)
+        ref = oracle_state(rows, cols, 0.9, 1.0, 0.05, seed, 3, 1)
+        with ac.Sim(rows, cols, 0.9, 1.0, 0.05, seed, init=1, kernel=R, Lb=32, rounds=1) as sim:
+            sim.set_option(ac.AC_OPT_EARLY_REJECT, 1)
+            sim.run_until(3)
+            assert_same(ref, *sim.read_state(), f"early rejection {rows}x{cols}")
     print("kernels ok", flush=True)
     rows, cols, seed = 48, 80, 1
     st = oracle.init(rows, cols, 0, seed)
