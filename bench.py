@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the per-kernel side measurements")
     ap.add_argument("--workload", default="ising4096",
                     choices=["ising4096", "batch", "serve", "frames", "configs", "efficiency", "life", "rates",
-                             "qnbhd", "sizes"],
+                             "qnbhd", "sizes", "slabs"],
                     help="ising4096: the headline step; batch: the 512-lattice batch only; serve: the request stream")
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="length of the replayed request stream (default 60 s for --workload serve, 10 s in the "
@@ -313,6 +313,25 @@ def main():
         __graft_entry__.build()
         import paper_cs_0502039_gb300 as ac
         print(json.dumps({"workload": args.workload, **efficiency_measurement(ac)}), flush=True)
+        return 0
+    if args.workload == "slabs":
+        import torch
+        rank, world, local = dist_env()
+        torch.cuda.set_device(local)
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if rank == 0:
+            import __graft_entry__
+            __graft_entry__.build()
+        if world > 1:
+            tdist.barrier()
+        import paper_cs_0502039_gb300 as ac
+        res = slabs_measurement(ac, args.rounds)
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, **res}), flush=True)
+        if world > 1:
+            tdist.destroy_process_group()
         return 0
     if args.workload in ("batch", "serve", "frames"):
         import torch
@@ -672,6 +691,67 @@ def serve_measurement(ac, seconds=10.0, rounds=None, lb=64):
     dt = time.perf_counter() - t0
     out["serial"] = {"requests": len(reqs), "events": sev, "events_per_s": sev / dt, "seconds": dt}
     out["capacity_over_serial"] = out["saturated"]["events_per_s"] / out["serial"]["events_per_s"]
+    return out
+
+
+def slabs_measurement(ac, rounds=8):
+    """One 4096^2 lattice (beta 0.4407, seed 7, T = 50) split into row slabs.  In one process
+    (one GPU) the slabs are handles stepped one after another with halo rows copied between
+    them; under torchrun each rank holds one slab and the halo rows go over torch.distributed
+    (NCCL).  The fingerprint of the assembled state must equal the unsplit run's."""
+    import torch
+    from paper_cs_0502039_gb300 import slabs
+    rank, world, _ = dist_env()
+    w = WORKLOAD
+    t_end = w["T"] * T32
+    with ac.Sim(w["rows"], w["cols"], 0.4407, w["J"], w["h"], w["seed"], init=w["init"],
+                kernel=ac.AC_KERNEL_ROUND, Lb=64, rounds=rounds) as ref:
+        ref.run_until(w["T"])
+        want = ref.stats()["checksum"]
+    out = {"lattice": f"{w['rows']}x{w['cols']}", "beta": 0.4407, "T": w["T"], "rounds": rounds, "cases": []}
+
+    def gather(sims, plan):
+        for sim, sl in zip(sims[1:], plan[1:]):
+            buf = torch.empty(sl.nrows * w["cols"] * 12, dtype=torch.uint8, device="cuda")
+            ac.ac_slab_export(sim.handle, sl.row0, sl.nrows, buf.data_ptr())
+            ac.ac_slab_import(sims[0].handle, sl.row0, sl.nrows, buf.data_ptr())
+        return sims[0].stats()["checksum"]
+
+    if world == 1:
+        for nslabs in (2, 4):
+            plan = slabs.plan(w["rows"], nslabs, rounds)
+            sims = [ac.Sim(w["rows"], w["cols"], 0.4407, w["J"], w["h"], w["seed"], init=w["init"],
+                           kernel=ac.AC_KERNEL_ROUND, Lb=64, rounds=rounds) for _ in plan]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps = slabs.run_on_one_gpu(ac, sims, plan, rounds, t_end)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            ev = sum(x.stats()["events"] for x in sims)
+            ok = gather(sims, plan) == want
+            for x in sims:
+                x.close()
+            out["cases"].append({"slabs": nslabs, "ranks": 1, "steps": steps, "events": ev, "seconds": dt,
+                                 "events_per_s": ev / dt, "checksum_equal": ok})
+            if not ok:
+                raise RuntimeError(f"{nslabs} slabs: the assembled state differs from the unsplit run")
+    else:
+        import torch.distributed as tdist
+        sim = ac.Sim(w["rows"], w["cols"], 0.4407, w["J"], w["h"], w["seed"], init=w["init"],
+                     kernel=ac.AC_KERNEL_ROUND, Lb=64, rounds=rounds)
+        tdist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps = slabs.run_distributed(ac, sim, rank, world, rounds, t_end)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ev = torch.tensor([float(sim.stats()["events"])], device="cuda", dtype=torch.float64)
+        tm = torch.tensor([dt], device="cuda", dtype=torch.float64)
+        tdist.all_reduce(ev)
+        tdist.all_reduce(tm, op=tdist.ReduceOp.MAX)
+        sim.close()
+        out["cases"].append({"slabs": world, "ranks": world, "steps": steps, "events": ev.item(),
+                             "seconds": tm.item(), "events_per_s": ev.item() / tm.item()})
     return out
 
 

@@ -447,6 +447,34 @@ ac_status ac_run_blocked_static(int32_t rows, int32_t cols, double beta, double 
                                 uint64_t seed, uint64_t* key_dev, uint32_t* cnt_dev, int64_t t_end,
                                 void* stream);
 
+/*
+ * Row slabs of one lattice (Sec. 3, the aggregated algorithm over a partition of the array;
+ * the trajectory does not depend on the partition, the remark after Fig. 3.6).  A handle that
+ * holds the whole lattice can be restricted to rows [row0, row0 + nrows) of the torus and then
+ * advanced one temporal-blocked launch at a time over that slab's tiles only: `rounds` exact
+ * synchronous rounds of Fig. 3.2 per step, reading the `rounds` rows above and below the slab
+ * from its own current state.  Between steps the caller copies each slab's first and last
+ * `rounds` rows into the neighbouring slabs' handles (ac_slab_export / ac_slab_import: device
+ * buffers of count * cols * 12 bytes, the keys tick << 1 | (s > 0) then the uint32 counts), so
+ * that every slab's halo is the neighbours' state after the same number of steps; the steps
+ * are then the global synchronous rounds, and the union of the slabs' own rows is the exact
+ * trajectory.  The rows outside the slab are not kept current by the steps themselves.
+ *   ac_slab_configure  needs the round or epoch kernel with rounds >= 2 (rows, cols >=
+ *                      4 * rounds), the 4-neighbour Ising array, no frames, and
+ *                      rounds <= nrows <= rows - 2 * rounds; nrows = 0 lifts the restriction.
+ *   ac_slab_step       one step toward t_end; *live = 1 if a cell of the slab still has an
+ *                      arrival before t_end.  Run every slab until no slab is live.  Does not
+ *                      change the handle's t_done.  AC_ERR_STATE if the counts of a region left
+ *                      the kernel's 16-bit window (the state is then unchanged).
+ *   ac_slab_export     rows [row, row + count) of the current state into dst (synchronous)
+ *   ac_slab_import     rows [row, row + count) of the current state from src (synchronous)
+ * Errors: AC_ERR_ARG, AC_ERR_STATE, AC_ERR_OOM, AC_ERR_CUDA.
+ */
+ac_status ac_slab_configure(ac_sim* sim, int32_t row0, int32_t nrows);
+ac_status ac_slab_step(ac_sim* sim, int64_t t_end, int32_t* live);
+ac_status ac_slab_export(const ac_sim* sim, int32_t row, int32_t count, void* dst_dev);
+ac_status ac_slab_import(ac_sim* sim, int32_t row, int32_t count, const void* src_dev);
+
 /* Device-primitive probes (DEVICE pointers, n elements), for verification:
  * out[i] = gap of x[i];  out4[4i..4i+3] = Philox({c[i], k[i], w2, 0}) under seed. */
 ac_status ac_dev_exp_ticks(const uint32_t* x_dev, uint64_t* out_dev, int64_t n);

@@ -56,7 +56,8 @@ EXPORTS = ["ac_create", "ac_set_stream", "ac_configure", "ac_run_until", "ac_run
            "ac_destroy", "ac_last_error", "ac_thresholds", "ac_reset", "ac_set_option", "ac_batch_create", "ac_batch_run_until",
            "ac_dev_exp_ticks", "ac_dev_philox", "ac_run_blocked_static", "ac_frames_configure",
            "ac_run_until_frames", "ac_frames_status", "ac_time_model", "ac_create_life", "ac_set_rates",
-           "ac_create_q", "ac_class_counts", "ac_load_state_async", "ac_read_state_async"]
+           "ac_create_q", "ac_class_counts", "ac_load_state_async", "ac_read_state_async", "ac_slab_configure",
+           "ac_slab_step", "ac_slab_export", "ac_slab_import"]
 
 AC_RATE_ONE = 1 << 20
 
@@ -85,6 +86,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ac_read_state_device": ([P, P, P, P], I32),
         "ac_load_state": ([P, P, P, P, I64], I32),
         "ac_load_state_async": ([P, P, P, P, I64, P], I32),
+        "ac_slab_configure": ([P, I32, I32], I32),
+        "ac_slab_step": ([P, I64, ctypes.POINTER(I32)], I32),
+        "ac_slab_export": ([P, I32, I32, P], I32),
+        "ac_slab_import": ([P, I32, I32, P], I32),
         "ac_read_state_async": ([P, P, P, P, P], I32),
         "ac_stats": ([P, ctypes.POINTER(ac_stats_t)], I32),
         "ac_round_history": ([P, P, I32, ctypes.POINTER(I32)], I32),
@@ -209,6 +214,25 @@ def ac_read_state_async(sim: int, s: np.ndarray | None, t: np.ndarray | None, n:
     _check(_lib.ac_read_state_async(sim, None if s is None else _np_ptr(s, np.int8),
                                     None if t is None else _np_ptr(t, np.int64),
                                     None if n is None else _np_ptr(n, np.uint32), stream))
+
+
+def ac_slab_configure(sim: int, row0: int, nrows: int) -> None:
+    _check(_lib.ac_slab_configure(sim, int(row0), int(nrows)))
+
+
+def ac_slab_step(sim: int, t_end: int) -> bool:
+    """One temporal-blocked step of the handle's row slab; True if the slab is still live."""
+    live = ctypes.c_int32(0)
+    _check(_lib.ac_slab_step(sim, int(t_end), ctypes.byref(live)))
+    return bool(live.value)
+
+
+def ac_slab_export(sim: int, row: int, count: int, dst_ptr: int) -> None:
+    _check(_lib.ac_slab_export(sim, int(row), int(count), dst_ptr))
+
+
+def ac_slab_import(sim: int, row: int, count: int, src_ptr: int) -> None:
+    _check(_lib.ac_slab_import(sim, int(row), int(count), src_ptr))
 
 
 def ac_stats(sim: int) -> dict:

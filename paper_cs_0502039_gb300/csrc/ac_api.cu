@@ -104,6 +104,7 @@ struct ac_sim {
   size_t ep_cap = 0;
   unsigned char* d_fmask = nullptr;         // early commits of certain rejections: flip masks
   bool early_reject = false;
+  int slab_row0 = 0, slab_rows = 0;         // row slab of a partitioned lattice (0 rows: none)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // asynchronous state transfers (ac_load_state_async / ac_read_state_async) on a caller's stream
   cudaEvent_t ev_work = nullptr, ev_load = nullptr, ev_read = nullptr;
@@ -1948,6 +1949,94 @@ ac_status ac_batch_run_until(int32_t n, ac_sim* const* sims, const int64_t* t_en
   sims[0]->visits += c.visits;
   sims[0]->polls += c.polls;
   return check_bounds();
+}
+
+ac_status ac_slab_configure(ac_sim* sim, int32_t row0, int32_t nrows) {
+  if (!sim) return fail(AC_ERR_ARG, "sim is NULL");
+  if (nrows == 0) {
+    sim->slab_row0 = sim->slab_rows = 0;
+    return AC_OK;
+  }
+  const int R = sim->cfg.rounds;
+  if (sim->model != 0 || sim->cfg.kernel == ac::kKernelBlocked || R < 2 || !tb_applicable(sim))
+    return fail(AC_ERR_ARG, "row slabs run on the temporal-blocked round kernel (round or epoch kernel, rounds >= 2, "
+                            "rows and cols >= 4 * rounds, the 4-neighbour Ising array)");
+  if (row0 < 0 || row0 >= sim->rows || nrows < R || nrows > sim->rows - 2 * R)
+    return fail(AC_ERR_ARG, "slab rows [%d, %d + %d) must lie in the torus with rounds <= nrows <= rows - 2 * rounds",
+                row0, row0, nrows);
+  if (sim->f_B > 0) return fail(AC_ERR_ARG, "snapshot frames are not taken on row slabs");
+  sim->slab_row0 = row0;
+  sim->slab_rows = nrows;
+  return AC_OK;
+}
+
+ac_status ac_slab_step(ac_sim* sim, int64_t t_end, int32_t* live) {
+  if (!sim || !live) return fail(AC_ERR_ARG, "sim and live are required");
+  if (sim->slab_rows == 0) return fail(AC_ERR_STATE, "no slab configured (ac_slab_configure)");
+  if (t_end < 0 || t_end >= kTickLimit) return fail(AC_ERR_ARG, "t_end must be in [0, 2^61)");
+  AC_SETTLE(sim);
+  const size_t N = sim->ncells();
+  if (!sim->key2) {
+    if (cudaMalloc(&sim->key2, N * 8) != cudaSuccess || cudaMalloc(&sim->cnt2, N * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AC_ERR_OOM, "second state buffer (%zu cells) allocation failed", N);
+    }
+  }
+  const int R = sim->cfg.rounds;
+  const int region = ac::tb_region_for(R, sim->cfg.lb == 128);
+  int tr = 0, tc = 0;
+  tb_tiling(sim->slab_rows, sim->cols, region, R, ac::tb_grid(region), &tr, &tc);
+  tr = std::min(tr, std::max(1, sim->slab_rows / R));   // tile heights >= R: the halo lies in the neighbour slabs
+  ac::LatDesc d = sim->host_desc(t_end, 0);
+  d.tr = tr;
+  d.tc = tc;
+  d.srow0 = sim->slab_row0;
+  d.srows = sim->slab_rows;
+  AC_CUDA(cudaMemcpyAsync(sim->d_desc, &d, sizeof d, cudaMemcpyHostToDevice, sim->stream));
+  AC_CUDA(cudaMemsetAsync(sim->d_ctr, 0, sizeof(ac::DevCounters), sim->stream));
+  AC_CUDA(cudaEventRecord(sim->ev0, sim->stream));
+  AC_CUDA(ac::launch_tb(sim->d_desc, 1, tr * tc, region, R, R, sim->d_ctr, sim->stream, false, 0));
+  AC_CUDA(cudaEventRecord(sim->ev1, sim->stream));
+  ac::DevCounters c{};
+  AC_CUDA(cudaMemcpyAsync(&c, sim->d_ctr, sizeof c, cudaMemcpyDeviceToHost, sim->stream));
+  AC_CUDA(cudaStreamSynchronize(sim->stream));
+  float ms = 0.f;
+  AC_CUDA(cudaEventElapsedTime(&ms, sim->ev0, sim->ev1));
+  if (c.error) return fail(c.error == AC_ERR_STATE ? AC_ERR_STATE : AC_ERR_CUDA,
+                           "slab step: device error %d (counts left the 16-bit window: the state is unchanged)", c.error);
+  // the launch wrote the slab's tiles into the second buffer: it becomes the current state, whose
+  // rows outside the slab the caller refreshes (ac_slab_import) before the next step
+  std::swap(sim->key, sim->key2);
+  std::swap(sim->cnt, sim->cnt2);
+  sim->events += c.events;
+  *live = c.active[0] > 0 ? 1 : 0;
+  sim->last_grid = std::min(tr * tc, ac::tb_grid(region));
+  return accumulate(sim, c, ms, true);
+}
+
+ac_status ac_slab_export(const ac_sim* csim, int32_t row, int32_t count, void* dst_dev) {
+  if (!csim || (!dst_dev && count > 0)) return fail(AC_ERR_ARG, "sim and dst are required");
+  if (row < 0 || count < 0 || row + count > csim->rows) return fail(AC_ERR_ARG, "rows [%d, %d) out of range", row, row + count);
+  ac_sim* sim = const_cast<ac_sim*>(csim);
+  AC_SETTLE(sim);
+  const size_t n = (size_t)count * sim->cols, off = (size_t)row * sim->cols;
+  unsigned char* dst = static_cast<unsigned char*>(dst_dev);
+  AC_CUDA(cudaMemcpyAsync(dst, sim->key + off, n * 8, cudaMemcpyDeviceToDevice, sim->stream));
+  AC_CUDA(cudaMemcpyAsync(dst + n * 8, sim->cnt + off, n * 4, cudaMemcpyDeviceToDevice, sim->stream));
+  AC_CUDA(cudaStreamSynchronize(sim->stream));
+  return AC_OK;
+}
+
+ac_status ac_slab_import(ac_sim* sim, int32_t row, int32_t count, const void* src_dev) {
+  if (!sim || (!src_dev && count > 0)) return fail(AC_ERR_ARG, "sim and src are required");
+  if (row < 0 || count < 0 || row + count > sim->rows) return fail(AC_ERR_ARG, "rows [%d, %d) out of range", row, row + count);
+  AC_SETTLE(sim);
+  const size_t n = (size_t)count * sim->cols, off = (size_t)row * sim->cols;
+  const unsigned char* src = static_cast<const unsigned char*>(src_dev);
+  AC_CUDA(cudaMemcpyAsync(sim->key + off, src, n * 8, cudaMemcpyDeviceToDevice, sim->stream));
+  AC_CUDA(cudaMemcpyAsync(sim->cnt + off, src + n * 8, n * 4, cudaMemcpyDeviceToDevice, sim->stream));
+  AC_CUDA(cudaStreamSynchronize(sim->stream));
+  return AC_OK;
 }
 
 ac_status ac_dev_exp_ticks(const uint32_t* x, uint64_t* out, int64_t n) {

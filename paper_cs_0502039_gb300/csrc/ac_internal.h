@@ -32,6 +32,7 @@ struct LatDesc {
   int rows, cols;
   int tr, tc;
   int cpair;                 // 1: columns are tiled in pairs (every tile column start and width even)
+  int srow0, srows;          // row slab: the tiles cover rows [srow0, srow0 + srows) only (srows = 0: all rows)
   int lb;
   int tile_base;             // first tile of this lattice in the launch's work list
   unsigned int thr[kThrMax]; // flip thresholds, index j + 5*(s > 0) (q-th degree neighbourhood:

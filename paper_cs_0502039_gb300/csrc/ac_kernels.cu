@@ -159,8 +159,9 @@ __device__ __forceinline__ Geom tile_geom(const LatDesc& L, int t) {
   Geom g;
   g.ti = t / L.tc;
   g.tj = t - g.ti * L.tc;
-  int q = L.rows / L.tr, rm = L.rows - q * L.tr;
-  g.r0 = g.ti * q + min(g.ti, rm);
+  const int rn = L.srows ? L.srows : L.rows;   // a row slab tiles only its own rows
+  int q = rn / L.tr, rm = rn - q * L.tr;
+  g.r0 = L.srow0 + g.ti * q + min(g.ti, rm);
   g.h = q + (g.ti < rm);
   const int cu = L.cpair ? 2 : 1;      // column unit: pairs keep every start and width even
   const int cn = L.cols / cu;
