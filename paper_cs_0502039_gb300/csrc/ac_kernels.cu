@@ -1128,6 +1128,39 @@ __device__ __forceinline__ int wrap_index(int x, int n, int& shift, int up_shift
   return x;
 }
 
+// Bulk copies of the region's key rows [i0, i1) into K, issued by the 32 lanes of one
+// warp: one copy per row, two where the row crosses the torus seam (columns x0 .. Lcols-1,
+// then 0 .. RC-n1-1).  Region row i is torus row r0D + i (wrapped).
+template <int RW>
+__device__ __forceinline__ void bulk_key_rows(unsigned long long* K, const unsigned long long* key_in, int i0, int i1,
+                                              int r0D, int Lrows, int Lcols, int x0, int n1, int RC, size_t Ncells,
+                                              unsigned long long* bar, int lane) {
+  for (int i = i0 + lane; i < i1; i += 32) {
+    int shr;
+    const int gr = wrap_index(r0D + i, Lrows, shr, 2);
+    const unsigned long long* src = key_in + (size_t)gr * (size_t)Lcols;
+    ACK((size_t)gr * Lcols + x0 + n1 <= Ncells && (x0 & 1) == 0 && (n1 & 1) == 0 && (Lcols & 1) == 0, 4, i);
+    ACK(i * RW + RC <= (RW + 2) * RW, 5, i);
+    bulk_load(&K[i * RW], src + x0, (unsigned)n1 * 8u, bar);
+    if (n1 < RC) bulk_load(&K[i * RW + n1], src, (unsigned)(RC - n1) * 8u, bar);
+  }
+}
+
+// Bounded wait for the mbarrier phase of `parity`; true if it gave up (2 s).
+__device__ __forceinline__ bool bulk_wait(unsigned long long* bar, unsigned parity) {
+  unsigned long long t0 = 0;
+  for (unsigned n = 0; !mbar_try_wait(bar, parity); ++n) {
+    if ((n & 1023u) != 1023u) continue;
+    const unsigned long long now = global_ns();
+    if (t0 == 0) {
+      t0 = now;
+    } else if (now - t0 > 2000000000ull) {
+      return true;
+    }
+  }
+  return false;
+}
+
 // ---- Life-like automaton on the Moore neighbourhood (the deterministic update of
 // Sec. 3, e.g. Conway's Game of Life): a cell may commit once its key is below the
 // keys of all 8 Moore neighbours (its update reads all of them), so enabled cells
@@ -1339,7 +1372,6 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   }
   const int lane = tid & 31;
   const int lj = tid % RW, li0 = tid / RW;                 // load / store mapping: column, first row
-  unsigned long long scanned = 0, enabled = 0, rounds_done = 0, events_total = 0;
   unsigned ep_phase = 0;                                   // epoch kernel: mbarrier phase of the next load
 
   for (int tile_it = blockIdx.x;; tile_it += gridDim.x) {
@@ -1373,8 +1405,6 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     const int Lrows = L.rows, Lcols = L.cols;
     const unsigned long long* key_in = parity ? L.key2 : L.key;
     const unsigned int* cnt_in = parity ? L.cnt2 : L.cnt;
-    unsigned long long* key_out = parity ? L.key : L.key2;
-    unsigned int* cnt_out = parity ? L.cnt : L.cnt2;
     const int RH = g.h + 2 * D, RC = g.w + 2 * D;
     ACK(RH <= RW && RC <= RW && g.h >= 1 && g.w >= 1, 1, tile);
     ACK(RH <= Lrows && RC <= Lcols, 2, tile);   // the region never overlaps itself
@@ -1382,11 +1412,9 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     const uint32_t g00 = (uint32_t)(g.r0 - D) * (uint32_t)Lcols + (uint32_t)(g.c0 - D);
     // the region wraps across the torus seam (small tiles of interior positions can too)
     const bool edge = (g.r0 < D) || (g.r0 + g.h + D > Lrows) || (g.c0 < D) || (g.c0 + g.w + D > Lcols);
-    // counts are kept as 16-bit offsets from a window start taken at the tile centre
+    // the tile centre (its count starts the region's 16-bit count window)
     const size_t ci = (size_t)(g.r0 + g.h / 2) * Lcols + g.c0 + g.w / 2;
     const size_t Ncells = (size_t)Lrows * (size_t)Lcols;
-    const unsigned ccen = EP ? __ldcg(&cnt_in[ACI(ci, Ncells, 3)]) : __ldg(&cnt_in[ACI(ci, Ncells, 3)]);
-    const unsigned base = ccen > 32768u ? ccen - 32768u : 0u;
     const unsigned cap = 65535u - (unsigned)R;
 
     // ---- load the region: keys by asynchronous copies, counts through registers
@@ -1401,29 +1429,22 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     bool over = false;
     __syncthreads();
     if constexpr (EP) {
-      // one warp issues the region's rows as bulk copies: one per row, two where the
-      // row crosses the torus seam (even cols, an even region start and an even width
-      // keep every source, destination and size a multiple of 16 bytes)
       if (tid < 32) {
+        // one warp issues the region's rows as bulk copies: one per row, two where the
+        // row crosses the torus seam (even cols, an even region start and an even width
+        // keep every source, destination and size a multiple of 16 bytes)
         if (tid == 0) mbar_expect_tx(ep_bar, (unsigned)(RH * RC) * 8u);
         __syncwarp();
         fence_proxy_async();
         int shx;
         const int x0 = wrap_index(g.c0 - D, Lcols, shx, 2);
-        const int n1 = min(RC, Lcols - x0);
-        for (int i = tid; i < RH; i += 32) {
-          int shr;
-          const int gr = wrap_index(g.r0 - D + i, Lrows, shr, 2);
-          const unsigned long long* src = key_in + (size_t)gr * (size_t)Lcols;
-          ACK((size_t)gr * Lcols + x0 + n1 <= Ncells && (x0 & 1) == 0 && (n1 & 1) == 0 && (Lcols & 1) == 0, 4, i);
-          ACK(i * RW + RC <= (RW + 2) * RW, 5, i);
-          bulk_load(&K[i * RW], src + x0, (unsigned)n1 * 8u, ep_bar);
-          if (n1 < RC) bulk_load(&K[i * RW + n1], src, (unsigned)(RC - n1) * 8u, ep_bar);
-        }
-        // while the rows are in flight: publish the previous item, claim the next one and
-        // check its dependencies once
+        bulk_key_rows<RW>(K, key_in, 0, RH, g.r0 - D, Lrows, Lcols, x0, min(RC, Lcols - x0), RC, Ncells, ep_bar, tid);
+      } else if (tid < 64) {
+        // meanwhile the next warp publishes the previous item, claims the next one and
+        // checks its dependencies once
+        const int lw = tid - 32;
         unsigned kn = ~0u;
-        if (tid == 0) {
+        if (lw == 0) {
           if (ep_ctl[3] != ~0u) {
             ep_publish(lats, nlat, total_tiles, ep, ctr, ep_ctl[3], ep_ctl[4] != 0u);
             ep_ctl[3] = ~0u;
@@ -1433,44 +1454,50 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         }
         kn = __shfl_sync(kFull, kn, 0);
         bool met = true;
-        if (kn != ~0u && tid < 9) {
+        if (kn != ~0u && lw < 9) {
           unsigned need;
-          const unsigned* f = ep_dep(lats, nlat, total_tiles, ep, kn, tid, &need);
+          const unsigned* f = ep_dep(lats, nlat, total_tiles, ep, kn, lw, &need);
           met = (f == nullptr) || ld_acquire_u32(f) >= need;
         }
         met = __all_sync(kFull, met);
-        if (tid == 0) ep_ctl[1] = met ? 1u : 0u;
+        if (lw == 0) ep_ctl[1] = met ? 1u : 0u;
       }
     }
-    // the thread's own-tile cells' count offsets at load (the write-back uses the same
+    // counts are kept as 16-bit offsets from a window start taken at the tile centre; the
+    // thread's own-tile cells' offsets at load are summed (the write-back uses the same
     // column and rows, so its difference is the tile's committed arrivals)
-    unsigned own_before = 0;
     const bool own_col = lj >= D && lj < D + g.w;
-    if (lj < RC) {
-      // all of the thread's global loads are in flight together (one batch)
-      constexpr int MROWS = RW / Cfg::LSTRIDE;
-      unsigned cvs[MROWS];
-      int shr0;
-      int gr = wrap_index(g.r0 - D + li0, Lrows, shr0, 2);   // the wrapped lattice row, stepped
+    unsigned base = 0, own_before = 0;
+    {
+      // the centre count (every thread loads it) and the thread's counts: one batch of
+      // loads in flight together (the launch kernel's key copies too)
+      const unsigned ccen = EP ? __ldcg(&cnt_in[ACI(ci, Ncells, 3)]) : __ldg(&cnt_in[ACI(ci, Ncells, 3)]);
+      base = ccen > 32768u ? ccen - 32768u : 0u;
+      if (lj < RC) {
+        constexpr int MROWS = RW / Cfg::LSTRIDE;
+        unsigned cvs[MROWS];
+        int shr0;
+        int gr = wrap_index(g.r0 - D + li0, Lrows, shr0, 2);   // the wrapped lattice row, stepped
 #pragma unroll
-      for (int m = 0; m < MROWS; ++m) {
-        const int i = li0 + Cfg::LSTRIDE * m;
-        if (i < RH) {
-          const uint32_t gi = (uint32_t)ACI((uint32_t)gr * (uint32_t)Lcols + (uint32_t)gc, Ncells, 3);
-          if constexpr (!EP) cp_async8(&K[i * RW + lj], &key_in[gi]);
-          cvs[m] = EP ? __ldcg(&cnt_in[gi]) : cnt_in[gi];
+        for (int m = 0; m < MROWS; ++m) {
+          const int i = li0 + Cfg::LSTRIDE * m;
+          if (i < RH) {
+            const uint32_t gi = (uint32_t)ACI((uint32_t)gr * (uint32_t)Lcols + (uint32_t)gc, Ncells, 3);
+            if constexpr (!EP) cp_async8(&K[i * RW + lj], &key_in[gi]);
+            cvs[m] = EP ? __ldcg(&cnt_in[gi]) : cnt_in[gi];
+          }
+          gr += Cfg::LSTRIDE;
+          if (gr >= Lrows) gr -= Lrows;
         }
-        gr += Cfg::LSTRIDE;
-        if (gr >= Lrows) gr -= Lrows;
-      }
 #pragma unroll
-      for (int m = 0; m < MROWS; ++m) {
-        const int i = li0 + Cfg::LSTRIDE * m;
-        if (i < RH) {
-          const unsigned cv = cvs[m] - base;
-          over |= cv > cap;
-          C[i * RW + lj] = (unsigned short)cv;
-          if (own_col && i >= D && i < D + g.h) own_before += cv;
+        for (int m = 0; m < MROWS; ++m) {
+          const int i = li0 + Cfg::LSTRIDE * m;
+          if (i < RH) {
+            const unsigned cv = cvs[m] - base;
+            over |= cv > cap;
+            C[i * RW + lj] = (unsigned short)cv;
+            if (own_col && i >= D && i < D + g.h) own_before += cv;
+          }
         }
       }
     }
@@ -1484,19 +1511,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     if (over) atomicOr(s_over, 1u);
     if constexpr (EP) {
       // the region's bulk copies: bounded wait on the mbarrier phase of this load
-      bool late = false;
-      unsigned long long t0 = 0;
-      for (unsigned n = 0; !mbar_try_wait(ep_bar, ep_phase); ++n) {
-        if ((n & 1023u) != 1023u) continue;
-        const unsigned long long now = global_ns();
-        if (t0 == 0) {
-          t0 = now;
-        } else if (now - t0 > 2000000000ull) {
-          late = true;
-          break;
-        }
-      }
-      if (late) {   // reported; the copies of this phase are waited on again before the CTA exits
+      if (bulk_wait(ep_bar, ep_phase)) {   // reported; its copies are waited on again before the CTA exits
         atomicCAS(&ctr->error, 0, 4 /* AC_ERR_STALL */);
         ep_ctl[5] = 0x10u | ep_phase;
       }
@@ -1526,6 +1541,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     }
 
     // ---- R synchronous rounds over the shrinking region
+    // (the visit's statistics are added to the counters at its end: 32-bit accumulators)
+    unsigned scanned = 0, enabled = 0, rounds_done = 0;
     const unsigned long long t2 = L.t2;
     const uint32_t two = L.two, seed_lo = L.seed_lo, seed_hi = L.seed_hi;
     // (the per-cell rate array is read through the descriptor at each commit: a pointer kept
@@ -1657,7 +1674,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
               }
             }
             mask = m;
-            scanned += (unsigned long long)__popc(cm);
+            scanned += (unsigned)__popc(cm);
           }
         }
       }
@@ -1809,7 +1826,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         if (FR && r >= D && r < D + g.h && cc >= D && cc < D + g.w)
           write_frames(*fv, gidx, key >> 1, nk >> 1, (unsigned)nk & 1u);
       }
-      enabled += (unsigned long long)n;
+      enabled += (unsigned)n;
       ++rounds_done;
       if (tid == 0) n_en[cur ^ 1] = 0u;
       __syncthreads();
@@ -1822,6 +1839,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     if (own_col) {
       // own rows i = li0 + 4m - D for region rows li0 + 4m in [D, D + h): the same cells
       // whose offsets own_before summed at load
+      unsigned long long* key_out = parity ? L.key : L.key2;
+      unsigned int* cnt_out = parity ? L.cnt : L.cnt2;
       unsigned own_after = 0;
       for (int ri = li0; ri < D + g.h; ri += Cfg::LSTRIDE) {
         if (ri < D) continue;
@@ -1843,10 +1862,20 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       for (int o = 16; o > 0; o >>= 1) kmin = min(kmin, __shfl_down_sync(kFull, kmin, o));
       if (lane == 0 && kmin != ~0ull) atomicMin(&ctr->kmin[launch_idx % 3], kmin);
     }
-    for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
-    if (lane == 0 && ev) {
-      atomicAdd(L.events, ev);
-      events_total += ev;
+    for (int o = 16; o > 0; o >>= 1) {
+      ev += __shfl_down_sync(kFull, ev, o);
+      scanned += __shfl_down_sync(kFull, scanned, o);
+    }
+    if (lane == 0) {
+      if (ev) {
+        atomicAdd(L.events, ev);
+        atomicAdd(&ctr->events, ev);
+      }
+      if (scanned) atomicAdd(&ctr->scanned, (unsigned long long)scanned);
+    }
+    if (tid == 0) {
+      atomicAdd(&ctr->enabled, (unsigned long long)enabled);
+      atomicAdd(&ctr->rounds, (unsigned long long)rounds_done);
     }
     const int any_live = __syncthreads_or(live);
     if constexpr (EP) {
@@ -1860,15 +1889,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       if (tid == 0 && any_live) atomicAdd(&ctr->active[launch_idx % 3], 1u);
     }
   }
-  for (int o = 16; o > 0; o >>= 1) scanned += __shfl_down_sync(kFull, scanned, o);
-  if (lane == 0) {
-    if (scanned) atomicAdd(&ctr->scanned, scanned);
-    if (events_total) atomicAdd(&ctr->events, events_total);
-  }
   __syncthreads();
   if (tid == 0) {
-    atomicAdd(&ctr->enabled, enabled);
-    atomicAdd(&ctr->rounds, rounds_done);
     if constexpr (EP) {
       if (ep_ctl[3] != ~0u) ep_publish(lats, nlat, total_tiles, ep, ctr, ep_ctl[3], ep_ctl[4] != 0u);
       if (ep_ctl[5]) {   // a region load timed out: wait once more (bounded) for its copies
