@@ -6,6 +6,7 @@
 // round of Fig. 3.2, checked for completion in chunks) and the blocked
 // persistent kernel (one cooperative launch per run call, Fig. 3.4), and
 // captures batched runs into CUDA graphs.
+#include <cuda.h>   // CUtensorMap and its enums (the encoder is reached through the runtime)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -103,6 +104,13 @@ struct ac_sim {
   unsigned int* d_ep = nullptr;             // epoch kernel: tile done words, per-epoch counts
   size_t ep_cap = 0;
   unsigned char* d_fmask = nullptr;         // early commits of certain rejections: flip masks
+  // epoch kernel: 2D tensor maps of the key buffers (encoded for the pair tmap_a / tmap_b):
+  // h_tmap / d_tmap hold [96: a, b; 128: a, b] then the same with a and b exchanged
+  CUtensorMap h_tmap[8];
+  void* d_tmap = nullptr;
+  const void* tmap_a = nullptr;
+  const void* tmap_b = nullptr;
+  bool tmap_off = false;                    // the encoder is unavailable or refused the maps
   bool early_reject = false;
   int slab_row0 = 0, slab_rows = 0;         // row slab of a partitioned lattice (0 rows: none)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -283,6 +291,7 @@ void free_sim(ac_sim* s) {
   cudaFree(s->d_red);
   cudaFree(s->d_ep);
   cudaFree(s->d_fmask);
+  cudaFree(s->d_tmap);
   cudaFree(s->frames);
   cudaFree(s->d_rates);
   if (s->frame_host) cudaFreeHost(s->frame_host);
@@ -518,6 +527,71 @@ void ep_tiling(int rows, int cols, int region, int halo, int* tr, int* tc) {
   *tc = std::max(2, ceil_div(cols / 2, own / 2));
 }
 
+// ---- 2D tensor maps of the key buffers (epoch kernel region copies)
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, looked up once through the runtime (nullptr: none)
+EncodeTiledFn tensor_map_encoder() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// rows x cols uint64 keys, row-major, boxes of box x box elements, no swizzle, zero fill
+bool encode_key_map(CUtensorMap* m, void* buf, int rows, int cols, int box) {
+  const EncodeTiledFn fn = tensor_map_encoder();
+  if (!fn) return false;
+  const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)cols * 8u};
+  const cuuint32_t boxd[2] = {(cuuint32_t)box, (cuuint32_t)box};
+  const cuuint32_t es[2] = {1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, buf, dim, stride, boxd, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+// Device address of the four maps [96: key, key2; 128: key, key2] of the handle's current
+// buffers, encoded and uploaded (on `stream`) the first time the pair is seen; nullptr when
+// the epoch kernel is to copy region rows instead (no encoder, or the maps were refused).
+const void* ensure_tmaps(ac_sim* s, cudaStream_t stream) {
+  if (s->tmap_off || !s->key2 || (s->cols & 1)) return nullptr;
+  const bool known = (s->key == s->tmap_a && s->key2 == s->tmap_b) || (s->key == s->tmap_b && s->key2 == s->tmap_a);
+  if (!known) {
+    void* a = s->key;
+    void* b = s->key2;
+    bool ok = encode_key_map(&s->h_tmap[0], a, s->rows, s->cols, 96) &&
+              encode_key_map(&s->h_tmap[1], b, s->rows, s->cols, 96) &&
+              encode_key_map(&s->h_tmap[2], a, s->rows, s->cols, 128) &&
+              encode_key_map(&s->h_tmap[3], b, s->rows, s->cols, 128);
+    s->h_tmap[4] = s->h_tmap[1];
+    s->h_tmap[5] = s->h_tmap[0];
+    s->h_tmap[6] = s->h_tmap[3];
+    s->h_tmap[7] = s->h_tmap[2];
+    if (ok && !s->d_tmap) ok = cudaMalloc(&s->d_tmap, sizeof s->h_tmap) == cudaSuccess;
+    if (ok) ok = cudaMemcpyAsync(s->d_tmap, s->h_tmap, sizeof s->h_tmap, cudaMemcpyHostToDevice, stream) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      s->tmap_off = true;
+      return nullptr;
+    }
+    s->tmap_a = a;
+    s->tmap_b = b;
+  }
+  return static_cast<const char*>(s->d_tmap) + (s->key == s->tmap_a ? 0 : 4) * sizeof(CUtensorMap);
+}
+
 // The epoch kernel runs the 4-neighbour Ising array without frames, on even cols with
 // an even halo (its bulk row copies need 16-byte alignment) and rows, cols >= 4D.
 bool ep_applicable(const ac_sim* s) {
@@ -606,6 +680,7 @@ ac_status run_ep(ac_sim* s, long long t_end, bool* fallback) {
     d.tr = tr;
     d.tc = tc;
     d.cpair = 1;
+    d.tmap = ensure_tmaps(s, s->stream);
     AC_CUDA(ac::launch_store_desc(d, s->d_desc, s->stream));
     st = reset_ep_counters(s->d_ctr, s->d_ep, words, s->stream);
     if (st != AC_OK) return st;
@@ -970,6 +1045,7 @@ ac_status batch_run_ep(int32_t n, ac_sim* const* sims, const int64_t* t_end, Bat
       R->h_desc[i].tr = tiles_tr[i];
       R->h_desc[i].tc = tiles_tc[i];
       R->h_desc[i].cpair = 1;
+      R->h_desc[i].tmap = ensure_tmaps(sims[i], stream);
       b += tiles_tr[i] * tiles_tc[i];
     }
   };

@@ -63,7 +63,12 @@ struct LatDesc {
   // early commits of certain rejections (one-round kernel): flip mask of each cell's pending
   // arrival, bit j set iff it flips with j up neighbours; nullptr = off
   unsigned char* fmask;
+  // epoch kernel: four 128-byte 2D tensor maps (driver CUtensorMap) of the key buffers,
+  // RW x RW boxes of uint64: box 96 over key and key2, then box 128 over key and key2;
+  // nullptr = region rows by row copies only
+  const void* tmap;
 };
+constexpr int kTmapBytes = 128;
 
 // Device counters of one run call (zeroed by the host before the call).
 struct DevCounters {

@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(4 * LB) round_kernel(const LatDesc* __restrict
                                                        int R, int parity, int launch_idx,
                                                        DevCounters* ctr, unsigned long long* hist,
                                                        int hist_len, int round_idx) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const Smem<LB> sm(smem_raw);
   if (launch_idx > 0) {
     if (*(volatile unsigned*)&ctr->active[(launch_idx + 2) % 3] == 0u) return;
@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(4 * LB) round_er_kernel(const LatDesc* __restr
   using S = TileShapeER<LB>;
   constexpr int P = TileShape<LB>::P;
   constexpr int NT = TileShape<LB>::NT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned long long* K = reinterpret_cast<unsigned long long*>(smem_raw);
   unsigned short* list = reinterpret_cast<unsigned short*>(smem_raw + S::kBytes + S::cBytes);
   unsigned int* n_en = reinterpret_cast<unsigned int*>(smem_raw + S::kBytes + S::cBytes + S::lBytes);
@@ -758,7 +758,7 @@ __global__ void __launch_bounds__(4 * LB) blocked_kernel(const LatDesc* __restri
                                                          int total_tiles, int polls, int refresh,
                                                          int max_rounds, long long watchdog_ns,
                                                          unsigned int* tile_done, DevCounters* ctr) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const Smem<LB> sm(smem_raw);
   unsigned long long scanned = 0, events = 0, rounds = 0, visits = 0, npolls = 0;
   unsigned long long last_progress = global_ns();
@@ -1103,6 +1103,15 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
+// global -> shared, the box at element (x, y) of a 2D tensor map (a 128-byte map in global
+// memory); x times the element size a multiple of 16 bytes, the destination 128-byte aligned
+__device__ __forceinline__ void tensor_box_load(void* dst, const void* tmap, int x, int y, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_addr(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
 // orders this thread's earlier generic-proxy accesses before its later async-proxy ones
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -1310,7 +1319,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   static_assert(!(EP && FR), "the epoch kernel does not write snapshot frames");
   using Cfg = TbCfg<RW>;
   constexpr int NT = Cfg::NT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned long long* K = reinterpret_cast<unsigned long long*>(smem_raw) + RW;   // row 0
   unsigned short* C = reinterpret_cast<unsigned short*>(smem_raw + Cfg::kBytes);
   unsigned short* list = reinterpret_cast<unsigned short*>(smem_raw + Cfg::kBytes + Cfg::cBytes);
@@ -1429,17 +1438,28 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     bool over = false;
     __syncthreads();
     if constexpr (EP) {
-      if (tid < 32) {
-        // one warp issues the region's rows as bulk copies: one per row, two where the
-        // row crosses the torus seam (even cols, an even region start and an even width
-        // keep every source, destination and size a multiple of 16 bytes)
+      if (!edge && L.tmap != nullptr && ((g.c0 - D) & 1) == 0) {
+        // a region inside the lattice: one 2D tensor copy of the RW x RW box at its first
+        // cell (the box's rows and columns past the region arrive too, zeros past the
+        // lattice's edge, and are never read)
+        if (tid == 0) {
+          mbar_expect_tx(ep_bar, (unsigned)(RW * RW) * 8u);
+          fence_proxy_async();
+          tensor_box_load(K, static_cast<const unsigned char*>(L.tmap) + ((RW == 128 ? 2 : 0) + parity) * kTmapBytes,
+                          g.c0 - D, g.r0 - D, ep_bar);
+        }
+      } else if (tid < 32) {
+        // a region across the torus seam: one warp issues its rows as bulk copies, one per
+        // row, two where the row crosses the seam (even cols, an even region start and an
+        // even width keep every source, destination and size a multiple of 16 bytes)
         if (tid == 0) mbar_expect_tx(ep_bar, (unsigned)(RH * RC) * 8u);
         __syncwarp();
         fence_proxy_async();
         int shx;
         const int x0 = wrap_index(g.c0 - D, Lcols, shx, 2);
         bulk_key_rows<RW>(K, key_in, 0, RH, g.r0 - D, Lrows, Lcols, x0, min(RC, Lcols - x0), RC, Ncells, ep_bar, tid);
-      } else if (tid < 64) {
+      }
+      if (tid >= 32 && tid < 64) {
         // meanwhile the next warp publishes the previous item, claims the next one and
         // checks its dependencies once
         const int lw = tid - 32;
