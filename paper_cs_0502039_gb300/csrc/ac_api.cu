@@ -609,6 +609,12 @@ int ep_epochs(double span, int D, int total) {
   return std::max(1, std::min(cap, (int)e));
 }
 
+// Epoch-kernel words: the tiles' done words, then (8-byte aligned) one 64-bit count per epoch.
+size_t ep_words(int total, int E) { return (((size_t)total + 1) & ~(size_t)1) + 2 * (size_t)E; }
+unsigned long long* ep_counts(unsigned* d_ep, int total) {
+  return reinterpret_cast<unsigned long long*>(d_ep + (((size_t)total + 1) & ~(size_t)1));
+}
+
 ac_status ensure_ep_words(unsigned int** buf, size_t* cap, size_t words) {
   if (words <= *cap) return AC_OK;
   if (*buf) cudaFree(*buf);
@@ -658,14 +664,13 @@ ac_status run_ep(ac_sim* s, long long t_end, bool* fallback) {
   const int total = tr * tc;
   const double span = (double)(t_end - s->t_done) / kTicksPerUnit;
   const int E = ep_epochs(span, D, total);
-  const size_t words = (size_t)total + 2 * (size_t)E;
+  const size_t words = ep_words(total, E);
   ac_status st = ensure_ep_words(&s->d_ep, &s->ep_cap, words);
   if (st != AC_OK) return st;
   unsigned* d_range = reinterpret_cast<unsigned*>(s->d_red);
   ac::EpArgs ep{};
   ep.done = s->d_ep;
-  ep.ep_done = s->d_ep + total;
-  ep.ep_live = s->d_ep + total + E;
+  ep.ep_count = ep_counts(s->d_ep, total);
   ep.max_epochs = E;
   ep.watchdog_ns = s->cfg.watchdog_ns;
   ep.range = d_range;
@@ -1077,12 +1082,11 @@ ac_status batch_run_ep(int32_t n, ac_sim* const* sims, const int64_t* t_end, Bat
     }
   }
   const int E = ep_epochs(span, D, total);
-  ac_status st = ensure_ep_words(&R->d_ep, &R->ep_cap, (size_t)total + 2 * (size_t)E);
+  ac_status st = ensure_ep_words(&R->d_ep, &R->ep_cap, ep_words(total, E));
   if (st != AC_OK) return st;
   ac::EpArgs ep{};
   ep.done = R->d_ep;
-  ep.ep_done = R->d_ep + total;
-  ep.ep_live = R->d_ep + total + E;
+  ep.ep_count = ep_counts(R->d_ep, total);
   ep.max_epochs = E;
   ep.watchdog_ns = sims[0]->cfg.watchdog_ns;
   ac::DevCounters c0{};
@@ -1093,7 +1097,7 @@ ac_status batch_run_ep(int32_t n, ac_sim* const* sims, const int64_t* t_end, Bat
   const int grid = (int)std::min<long long>((long long)total * E, ac::tb_grid(R->region));
   for (;;) {
     AC_CUDA(cudaMemcpyAsync(R->d_ctr, &c0, sizeof c0, cudaMemcpyHostToDevice, stream));
-    AC_CUDA(cudaMemsetAsync(R->d_ep, 0, ((size_t)total + 2 * (size_t)E) * 4, stream));
+    AC_CUDA(cudaMemsetAsync(R->d_ep, 0, ep_words(total, E) * 4, stream));
     AC_CUDA(ac::launch_ep(R->d_desc, n, total, R->region, D, D, R->d_ctr, ep, stream, 0));
     ac::DevCounters c{};
     AC_CUDA(cudaMemcpyAsync(&c, R->d_ctr, sizeof c, cudaMemcpyDeviceToHost, stream));

@@ -94,16 +94,15 @@ struct DevCounters {
 
 // Epoch kernel (the persistent temporal-blocked kernel): per-tile and per-epoch words.
 //   done[tile]        epochs the tile has completed (release / acquire)
-//   ep_done[e]        tiles that completed epoch e
-//   ep_live[e]        tiles with an arrival before t_end left after epoch e
-// All zero before a launch; ep_done and ep_live hold max_epochs entries.
+//   ep_count[e]       high word: tiles that completed epoch e; low word: those of them with
+//                     an arrival before t_end left (one atomic carries both)
+// All zero before a launch; ep_count holds max_epochs entries.
 // range: nrange (min, max) count pairs from count_range kernels; if any max - min >= limit
 // the kernel does no work and reports kEpWindow (the 16-bit count window of a region could
 // overflow during the call; the caller falls back to the exact one-round kernel).
 struct EpArgs {
   unsigned int* done;
-  unsigned int* ep_done;
-  unsigned int* ep_live;
+  unsigned long long* ep_count;
   int max_epochs;
   long long watchdog_ns;
   const unsigned int* range;

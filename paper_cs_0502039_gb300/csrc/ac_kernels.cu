@@ -1239,24 +1239,47 @@ __device__ __forceinline__ unsigned ep_claim(DevCounters* ctr, const EpArgs& ep,
   return k;
 }
 
-// publish item k: its tile has completed epoch e + 1 (its stores precede this call on the
-// CTA's barrier; fence, then release); the last tile of an epoch decides whether any
-// arrival before t_end is left anywhere
+// Publish item kp (~0: none) and claim the next item, their global-memory round trips in
+// flight together.  Publishing: its tile has completed epoch e + 1 (the CTA's stores
+// precede this call on its barrier; fence, then release the done word), and one atomic
+// adds the tile to epoch e's count and, if live, to its live count; the tile that
+// completes the epoch sees every other tile's live flag in the value it gets back and
+// ends the run if none has an arrival before t_end left.  Claiming: as ep_claim, with the
+// error word, the claim and the stop epoch read together (an item claimed while an error
+// is reported is dropped; the stop epoch this call sets itself counts).
+__device__ __forceinline__ unsigned ep_publish_claim(const LatDesc* lats, int nlat, int total, const EpArgs& ep,
+                                                     DevCounters* ctr, unsigned kp, bool live, bool claim) {
+  unsigned long long old = 0;
+  int pe = -1;
+  if (kp != ~0u) {
+    const int tile = ep_tile(kp, total, &pe);
+    __threadfence();
+    // (the verification hook that suppresses edge publication also withholds the epoch
+    // words, so that the neighbours' bounded waits and the watchdog end the run)
+    ACK(tile >= 0 && tile < total && pe < ep.max_epochs, 13, tile);
+    if (!lats[find_lattice(lats, nlat, tile)].drop_publish) st_release_u32(&ep.done[tile], (unsigned)pe + 1u);
+    old = atomicAdd(&ep.ep_count[pe], (1ull << 32) | (live ? 1ull : 0ull));
+  }
+  int err = 0;
+  unsigned k = ~0u, stop = ~0u;
+  if (claim) {
+    err = *(volatile int*)&ctr->error;
+    k = atomicAdd(&ctr->next_item, 1u);
+    stop = *(volatile unsigned*)&ctr->stop_epoch;
+  }
+  if (pe >= 0 && (unsigned)(old >> 32) == (unsigned)total - 1u && (unsigned)old + (live ? 1u : 0u) == 0u) {
+    atomicMin(&ctr->stop_epoch, (unsigned)pe + 1u);
+    stop = min(stop, (unsigned)pe + 1u);
+  }
+  if (!claim) return ~0u;
+  const unsigned e = k / (unsigned)total;
+  return (err != 0 || e >= (unsigned)ep.max_epochs || e >= stop) ? ~0u : k;
+}
+
+// publish item k (see ep_publish_claim)
 __device__ __forceinline__ void ep_publish(const LatDesc* lats, int nlat, int total, const EpArgs& ep,
                                            DevCounters* ctr, unsigned k, bool live) {
-  int epoch;
-  const int tile = ep_tile(k, total, &epoch);
-  __threadfence();
-  // (the verification hook that suppresses edge publication also withholds the epoch
-  // words, so that the neighbours' bounded waits and the watchdog end the run)
-  ACK(tile >= 0 && tile < total && epoch < ep.max_epochs, 13, tile);
-  if (!lats[find_lattice(lats, nlat, tile)].drop_publish) st_release_u32(&ep.done[tile], (unsigned)epoch + 1u);
-  if (live) atomicAdd(&ep.ep_live[epoch], 1u);
-  __threadfence();
-  if (atomicAdd(&ep.ep_done[epoch], 1u) == (unsigned)total - 1u) {
-    __threadfence();
-    if (*(volatile unsigned*)&ep.ep_live[epoch] == 0u) atomicMin(&ctr->stop_epoch, (unsigned)epoch + 1u);
-  }
+  ep_publish_claim(lats, nlat, total, ep, ctr, k, live, false);
 }
 
 // threads 0..8: wait until dependency `tid` of item k is met -- bounded polls, then sleeps,
@@ -1465,11 +1488,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const int lw = tid - 32;
         unsigned kn = ~0u;
         if (lw == 0) {
-          if (ep_ctl[3] != ~0u) {
-            ep_publish(lats, nlat, total_tiles, ep, ctr, ep_ctl[3], ep_ctl[4] != 0u);
-            ep_ctl[3] = ~0u;
-          }
-          kn = ep_claim(ctr, ep, total_tiles);
+          kn = ep_publish_claim(lats, nlat, total_tiles, ep, ctr, ep_ctl[3], ep_ctl[4] != 0u, true);
+          ep_ctl[3] = ~0u;
           ep_ctl[0] = kn;
         }
         kn = __shfl_sync(kFull, kn, 0);
