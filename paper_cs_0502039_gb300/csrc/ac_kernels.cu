@@ -1504,8 +1504,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       }
     }
     // counts are kept as 16-bit offsets from a window start taken at the tile centre; the
-    // thread's own-tile cells' offsets at load are summed (the write-back uses the same
-    // column and rows, so its difference is the tile's committed arrivals)
+    // thread's own-tile cells' offsets at load are summed (against the sum at the
+    // write-back, it gives the tile's committed arrivals)
     const bool own_col = lj >= D && lj < D + g.w;
     unsigned base = 0, own_before = 0;
     {
@@ -1513,7 +1513,42 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       // loads in flight together (the launch kernel's key copies too)
       const unsigned ccen = EP ? __ldcg(&cnt_in[ACI(ci, Ncells, 3)]) : __ldg(&cnt_in[ACI(ci, Ncells, 3)]);
       base = ccen > 32768u ? ccen - 32768u : 0u;
-      if (lj < RC) {
+      if constexpr (EP) {
+        // the epoch kernel loads two adjacent counts per thread (8-byte loads: the region's
+        // first column, its width and the lattice's columns are even, so a pair never
+        // crosses the torus seam): thread (pj, pi0) takes columns 2 pj, 2 pj + 1 of rows
+        // pi0 + PSTRIDE m
+        constexpr int PW = RW / 2, PSTRIDE = NT / PW, PROWS = RW / PSTRIDE;
+        const int pj = tid % PW, pi0 = tid / PW, cj = 2 * pj;
+        if (cj < RC) {
+          int shp;
+          const int gcp = wrap_index(g.c0 - D + cj, Lcols, shp, 2);
+          uint2 cv2[PROWS];
+          int shr0;
+          int gr = wrap_index(g.r0 - D + pi0, Lrows, shr0, 2);
+#pragma unroll
+          for (int m = 0; m < PROWS; ++m) {
+            const int i = pi0 + PSTRIDE * m;
+            if (i < RH) {
+              const uint32_t gi = (uint32_t)ACI((uint32_t)gr * (uint32_t)Lcols + (uint32_t)gcp, Ncells - 1, 3);
+              cv2[m] = __ldcg(reinterpret_cast<const uint2*>(&cnt_in[gi]));
+            }
+            gr += PSTRIDE;
+            if (gr >= Lrows) gr -= Lrows;
+          }
+          const bool own_p = cj >= D && cj < D + g.w;   // both columns or neither (D, w even)
+#pragma unroll
+          for (int m = 0; m < PROWS; ++m) {
+            const int i = pi0 + PSTRIDE * m;
+            if (i < RH) {
+              const unsigned a = cv2[m].x - base, b = cv2[m].y - base;
+              over |= (a > cap) | (b > cap);
+              *reinterpret_cast<unsigned*>(&C[i * RW + cj]) = (a & 0xFFFFu) | (b << 16);
+              if (own_p && i >= D && i < D + g.h) own_before += a + b;
+            }
+          }
+        }
+      } else if (lj < RC) {
         constexpr int MROWS = RW / Cfg::LSTRIDE;
         unsigned cvs[MROWS];
         int shr0;
@@ -1615,12 +1650,16 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       __syncthreads();
     } else {
       // order planes of the loaded region; a warp covers 32 consecutive columns of one
-      // row.  Relations with cells outside the loaded rectangle are never read (the
-      // reads past the region's last row and column stay inside shared memory).
-      for (int i = li0; i < RW; i += Cfg::LSTRIDE) {
-        const unsigned long long kc = K[i * RW + lj];
+      // row, and a thread RW / LSTRIDE consecutive rows (the key below a row is the next
+      // row's own key).  Relations with cells outside the loaded rectangle are never read
+      // (the reads past the region's last row and column stay inside shared memory).
+      constexpr int RPT = RW / Cfg::LSTRIDE;
+      unsigned long long kcarry = K[li0 * RPT * RW + lj];
+      for (int i = li0 * RPT; i < (li0 + 1) * RPT; ++i) {
+        const unsigned long long kc = kcarry;
         const unsigned long long kr = K[i * RW + lj + 1];
         const unsigned long long kd = K[(i + 1) * RW + lj];
+        kcarry = kd;
         bool ph, pv, pse = false, psw = false, ph2 = false, pv2 = false;
         if (MODEL != 0 && edge) {   // wider neighbourhoods across the seam: exact order
           const unsigned gc = rowoff[i] + colg[lj], gd = rowoff[i + 1];
@@ -1731,13 +1770,16 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       int wbase = 0;
       if (lane == 0 && total) wbase = (int)atomicAdd(&n_en[cur], (unsigned)total);
       wbase = __shfl_sync(kFull, wbase, 0);
+      // the lane's entries, two per iteration (the list holds every enabled cell: they
+      // form an independent set of the scanned rectangle)
       int off = wbase + excl;
+      const unsigned ebase = (unsigned)((oi << 8) | (32 * ow));
       while (mask) {
-        const int b = __ffs(mask) - 1;
-        mask &= mask - 1;
-        if (off < Cfg::LIST)
-          list[off] = (unsigned short)((oi << 8) | (32 * ow + b));
-        ++off;
+        const unsigned m2 = mask & (mask - 1);
+        list[ACI(off, Cfg::LIST, 6)] = (unsigned short)(ebase + (unsigned)__ffs(mask) - 1u);
+        if (m2) list[ACI(off + 1, Cfg::LIST, 6)] = (unsigned short)(ebase + (unsigned)__ffs(m2) - 1u);
+        mask = m2 & (m2 - 1);
+        off += 2;
       }
       __syncthreads();
       const int n = min((int)n_en[cur], Cfg::LIST);
@@ -1876,12 +1918,11 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     // ---- write the tile back; count its arrivals; is anything left before t_end?
     bool live = false;
     unsigned long long ev = 0, kmin = ~0ull;
+    unsigned own_after = 0;
     if (own_col) {
-      // own rows i = li0 + 4m - D for region rows li0 + 4m in [D, D + h): the same cells
-      // whose offsets own_before summed at load
+      // own rows i = li0 + 4m - D for region rows li0 + 4m in [D, D + h)
       unsigned long long* key_out = parity ? L.key : L.key2;
       unsigned int* cnt_out = parity ? L.cnt : L.cnt2;
-      unsigned own_after = 0;
       for (int ri = li0; ri < D + g.h; ri += Cfg::LSTRIDE) {
         if (ri < D) continue;
         const int i = ri - D;
@@ -1896,8 +1937,11 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         live |= kk < t2;
         if (FR) kmin = min(kmin, kk);
       }
-      ev = (unsigned long long)(own_after - own_before);
     }
+    // the tile's committed arrivals: summed over the CTA, the own cells' offsets at the
+    // write-back less those at load (signed per thread: the epoch kernel loads counts in
+    // column pairs, so a thread's cells at load and at the write-back differ)
+    ev = (unsigned long long)((long long)own_after - (long long)own_before);
     if (FR) {   // the launch's smallest output key: frames below its tick are complete
       for (int o = 16; o > 0; o >>= 1) kmin = min(kmin, __shfl_down_sync(kFull, kmin, o));
       if (lane == 0 && kmin != ~0ull) atomicMin(&ctr->kmin[launch_idx % 3], kmin);
