@@ -1919,7 +1919,28 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     bool live = false;
     unsigned long long ev = 0, kmin = ~0ull;
     unsigned own_after = 0;
-    if (own_col) {
+    if constexpr (EP) {
+      // the epoch kernel writes own cells in column pairs: 16-byte key and 8-byte count
+      // stores (the tile's first column and width are even)
+      constexpr int PW = RW / 2, PSTRIDE = NT / PW;
+      const int pj = tid % PW, pi0 = tid / PW, cj = 2 * pj;
+      if (cj >= D && cj < D + g.w) {
+        unsigned long long* key_out = parity ? L.key : L.key2;
+        unsigned int* cnt_out = parity ? L.cnt : L.cnt2;
+        for (int ri = pi0; ri < D + g.h; ri += PSTRIDE) {
+          if (ri < D) continue;
+          const int si = ri * RW + cj;
+          const uint32_t gi = (uint32_t)ACI((uint32_t)(g.r0 + ri - D) * (uint32_t)Lcols + (uint32_t)(g.c0 + cj - D), Ncells - 1, 11);
+          const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(&K[si]);
+          const unsigned c2 = *reinterpret_cast<const unsigned*>(&C[si]);
+          const unsigned ca = c2 & 0xFFFFu, cb = c2 >> 16;
+          own_after += ca + cb;
+          *reinterpret_cast<ulonglong2*>(&key_out[gi]) = kk;
+          *reinterpret_cast<uint2*>(&cnt_out[gi]) = make_uint2(base + ca, base + cb);
+          live |= (kk.x < t2) | (kk.y < t2);
+        }
+      }
+    } else if (own_col) {
       // own rows i = li0 + 4m - D for region rows li0 + 4m in [D, D + h)
       unsigned long long* key_out = parity ? L.key : L.key2;
       unsigned int* cnt_out = parity ? L.cnt : L.cnt2;
