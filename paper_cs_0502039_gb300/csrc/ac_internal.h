@@ -1,6 +1,7 @@
 // ac_internal.h -- structures shared by the kernels (ac_kernels.cu) and the host
 // runtime (ac_api.cu).  Not part of the public C ABI (include/ac.h).
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -87,10 +88,15 @@ struct DevCounters {
   unsigned long long kmin[3];   // temporal-blocked kernel with frames: smallest output key of a
                                 // launch (mod-3 ring like active; the host presets all to ~0)
   unsigned long long early;     // one-round kernel: arrivals committed early as certain rejections
-  unsigned int next_item;       // epoch kernel: next work item to claim
-  unsigned int stop_epoch;      // epoch kernel: epochs after which no arrival before t_end is left
-                                // (the host presets ~0)
+  // epoch kernel: the claim word, one 64-bit word (low half first): the next work item to
+  // claim, and the epochs after which no arrival before t_end is left (the host presets ~0).
+  // A claim is one 64-bit atomic add, so it sees the stop epoch as of its own place in the
+  // word's order: refusals are monotone in the item index
+  unsigned int next_item;
+  unsigned int stop_epoch;
 };
+static_assert(offsetof(DevCounters, next_item) % 8 == 0 && offsetof(DevCounters, stop_epoch) == offsetof(DevCounters, next_item) + 4,
+              "the claim word");
 
 // Epoch kernel (the persistent temporal-blocked kernel): per-tile and per-epoch words.
 //   done[tile]        epochs the tile has completed (release / acquire)

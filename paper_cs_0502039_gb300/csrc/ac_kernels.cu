@@ -1230,13 +1230,30 @@ __device__ __forceinline__ const unsigned* ep_dep(const LatDesc* lats, int nlat,
   return ep.done + L.tile_base + ti * L.tc + tj;
 }
 
+// the claim word: next item (low half), stop epoch (high half)
+__device__ __forceinline__ unsigned long long* ep_claim_word(DevCounters* ctr) {
+  return reinterpret_cast<unsigned long long*>(&ctr->next_item);
+}
+
 // claim the next item (~0: none left, an error was reported, or the run has finished)
 __device__ __forceinline__ unsigned ep_claim(DevCounters* ctr, const EpArgs& ep, int total) {
   if (*(volatile int*)&ctr->error != 0) return ~0u;
-  const unsigned k = atomicAdd(&ctr->next_item, 1u);
-  const unsigned e = k / (unsigned)total;
-  if (e >= (unsigned)ep.max_epochs || e >= *(volatile unsigned*)&ctr->stop_epoch) return ~0u;
-  return k;
+  const unsigned long long w = atomicAdd(ep_claim_word(ctr), 1ull);
+  const unsigned k = (unsigned)w, e = k / (unsigned)total;
+  return (e >= (unsigned)ep.max_epochs || e >= (unsigned)(w >> 32)) ? ~0u : k;
+}
+
+// stop epoch = min(stop epoch, s) in the claim word's high half (claims change only the low
+// half; a bounded compare-and-swap loop -- a stop epoch that is not set only costs identity
+// epochs up to the launch's epoch budget)
+__device__ __forceinline__ void ep_set_stop(DevCounters* ctr, unsigned s) {
+  unsigned long long* cw = ep_claim_word(ctr);
+  unsigned long long old = *(volatile unsigned long long*)cw;
+  for (int it = 0; it < 4096 && (unsigned)(old >> 32) > s; ++it) {
+    const unsigned long long seen = atomicCAS(cw, old, ((unsigned long long)s << 32) | (old & 0xFFFFFFFFull));
+    if (seen == old) break;
+    old = seen;
+  }
 }
 
 // Publish item kp (~0: none) and claim the next item, their global-memory round trips in
@@ -1244,9 +1261,8 @@ __device__ __forceinline__ unsigned ep_claim(DevCounters* ctr, const EpArgs& ep,
 // precede this call on its barrier; fence, then release the done word), and one atomic
 // adds the tile to epoch e's count and, if live, to its live count; the tile that
 // completes the epoch sees every other tile's live flag in the value it gets back and
-// ends the run if none has an arrival before t_end left.  Claiming: as ep_claim, with the
-// error word, the claim and the stop epoch read together (an item claimed while an error
-// is reported is dropped; the stop epoch this call sets itself counts).
+// ends the run if none has an arrival before t_end left.  Claiming: as ep_claim (an item
+// claimed while an error is reported is dropped).
 __device__ __forceinline__ unsigned ep_publish_claim(const LatDesc* lats, int nlat, int total, const EpArgs& ep,
                                                      DevCounters* ctr, unsigned kp, bool live, bool claim) {
   unsigned long long old = 0;
@@ -1261,19 +1277,19 @@ __device__ __forceinline__ unsigned ep_publish_claim(const LatDesc* lats, int nl
     old = atomicAdd(&ep.ep_count[pe], (1ull << 32) | (live ? 1ull : 0ull));
   }
   int err = 0;
-  unsigned k = ~0u, stop = ~0u;
+  unsigned long long w = ~0ull;
   if (claim) {
     err = *(volatile int*)&ctr->error;
-    k = atomicAdd(&ctr->next_item, 1u);
-    stop = *(volatile unsigned*)&ctr->stop_epoch;
+    w = atomicAdd(ep_claim_word(ctr), 1ull);
   }
-  if (pe >= 0 && (unsigned)(old >> 32) == (unsigned)total - 1u && (unsigned)old + (live ? 1u : 0u) == 0u) {
-    atomicMin(&ctr->stop_epoch, (unsigned)pe + 1u);
-    stop = min(stop, (unsigned)pe + 1u);
-  }
+  if (pe >= 0 && (unsigned)(old >> 32) == (unsigned)total - 1u && (unsigned)old + (live ? 1u : 0u) == 0u)
+    ep_set_stop(ctr, (unsigned)pe + 1u);
   if (!claim) return ~0u;
-  const unsigned e = k / (unsigned)total;
-  return (err != 0 || e >= (unsigned)ep.max_epochs || e >= stop) ? ~0u : k;
+  // refused only by the stop epoch the claim itself returned: a later claim sees the same
+  // or a smaller stop epoch, so every accepted item's dependencies (claimed earlier) were
+  // accepted too, and none waits on an item nobody runs
+  const unsigned k = (unsigned)w, e = k / (unsigned)total;
+  return (err != 0 || e >= (unsigned)ep.max_epochs || e >= (unsigned)(w >> 32)) ? ~0u : k;
 }
 
 // publish item k (see ep_publish_claim)

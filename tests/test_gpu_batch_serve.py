@@ -85,3 +85,28 @@ def test_served_jobs_equal_alone():
         if req["rows"] <= 128:
             ref = oracle_state(req["rows"], req["cols"], req["beta"], 1.0, 0.0, req["seed"], req["T"])
             assert res.checksum == oracle.checksum(ref)
+
+
+def test_batched_epoch_many_short_calls():
+    """Many short batched epoch-kernel calls over a few small lattices (far fewer tiles than
+    resident CTAs, so several epochs are claimed at once and every call ends on the stop
+    epoch while claims are in flight): every call completes, and the states equal the
+    oracle's.  A claim refused by the stop epoch must never leave an accepted item waiting
+    on it (the stop epoch travels in the claim word)."""
+    ws = workloads.batch_workload(n=6, lmin=48, lmax=128, T=1, seed=5)
+    for w in ws:
+        w["rows"] -= w["rows"] % 2
+        w["cols"] -= w["cols"] % 2
+    sims = _make(ws, ac.AC_KERNEL_EPOCH, 4)
+    try:
+        horizons = [0] * len(ws)
+        for call in range(60):
+            horizons = [h + T32 // 4 + 977 * (i + 1) * (call % 3) for i, h in enumerate(horizons)]
+            ac.ac_batch_run_until([s.handle for s in sims], horizons)
+        for w, s, te in zip(ws, sims, horizons):
+            ref = oracle.init(w["rows"], w["cols"], w["init"], w["seed"])
+            oracle.run(ref, oracle.thresholds(w["beta"], w["J"], w["h"]), w["seed"], te)
+            assert_same(ref, *s.read_state(), f"{w['rows']}x{w['cols']} after 60 calls")
+    finally:
+        for s in sims:
+            s.close()
