@@ -1382,7 +1382,10 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
   unsigned int* ep_ctl = reinterpret_cast<unsigned int*>(smem_raw + Cfg::fOff + 8);
   // ep_ctl: [0] next item, [1] its dependencies were met at the early check,
   //         [2] current item, [3] previous item not yet published, [4] its live flag,
-  //         [5] 0x10 | phase of a region load whose wait timed out (0: none)
+  //         [5] 0x10 | phase of a region load whose wait timed out (0: none),
+  //         [6] the item after the next one, [7] the one claimed during this visit's load
+  //         (a CTA holds its claims in claim order and runs them in that order, so the
+  //         smallest unfinished claimed item is always at the head of its CTA's queue)
 
   const int tid = threadIdx.x;
   // this launch's number, advanced by the last CTA of the previous launch
@@ -1412,6 +1415,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
       mbar_init(ep_bar);
       if (wide && blockIdx.x == 0) atomicCAS(&ctr->error, 0, kEpWindow);
       ep_ctl[0] = wide ? ~0u : ep_claim(ctr, ep, total_tiles);
+      ep_ctl[6] = ep_ctl[0] == ~0u ? ~0u : ep_claim(ctr, ep, total_tiles);
+      ep_ctl[7] = ~0u;
       ep_ctl[1] = 0u;
       ep_ctl[3] = ~0u;
       ep_ctl[5] = 0u;
@@ -1498,25 +1503,11 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const int x0 = wrap_index(g.c0 - D, Lcols, shx, 2);
         bulk_key_rows<RW>(K, key_in, 0, RH, g.r0 - D, Lrows, Lcols, x0, min(RC, Lcols - x0), RC, Ncells, ep_bar, tid);
       }
-      if (tid >= 32 && tid < 64) {
-        // meanwhile the next warp publishes the previous item, claims the next one and
-        // checks its dependencies once
-        const int lw = tid - 32;
-        unsigned kn = ~0u;
-        if (lw == 0) {
-          kn = ep_publish_claim(lats, nlat, total_tiles, ep, ctr, ep_ctl[3], ep_ctl[4] != 0u, true);
-          ep_ctl[3] = ~0u;
-          ep_ctl[0] = kn;
-        }
-        kn = __shfl_sync(kFull, kn, 0);
-        bool met = true;
-        if (kn != ~0u && lw < 9) {
-          unsigned need;
-          const unsigned* f = ep_dep(lats, nlat, total_tiles, ep, kn, lw, &need);
-          met = (f == nullptr) || ld_acquire_u32(f) >= need;
-        }
-        met = __all_sync(kFull, met);
-        if (lw == 0) ep_ctl[1] = met ? 1u : 0u;
+      if (tid == 32) {
+        // meanwhile the next warp publishes the previous item and claims the item after
+        // the next one (the next one was claimed a visit ago)
+        ep_ctl[7] = ep_publish_claim(lats, nlat, total_tiles, ep, ctr, ep_ctl[3], ep_ctl[4] != 0u, ep_ctl[6] != ~0u);
+        ep_ctl[3] = ~0u;
       }
     }
     // counts are kept as 16-bit offsets from a window start taken at the tile centre; the
@@ -1536,10 +1527,10 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         // pi0 + PSTRIDE m
         constexpr int PW = RW / 2, PSTRIDE = NT / PW, PROWS = RW / PSTRIDE;
         const int pj = tid % PW, pi0 = tid / PW, cj = 2 * pj;
+        uint2 cv2[PROWS];
         if (cj < RC) {
           int shp;
           const int gcp = wrap_index(g.c0 - D + cj, Lcols, shp, 2);
-          uint2 cv2[PROWS];
           int shr0;
           int gr = wrap_index(g.r0 - D + pi0, Lrows, shr0, 2);
 #pragma unroll
@@ -1552,6 +1543,22 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
             gr += PSTRIDE;
             if (gr >= Lrows) gr -= Lrows;
           }
+        }
+        if (tid >= 64 && tid < 96) {
+          // with its counts in flight, warp 2 checks the next item's dependencies once
+          // (acquire loads: they order only what follows them)
+          const int lw = tid - 64;
+          const unsigned kn = ep_ctl[6];
+          bool met = true;
+          if (kn != ~0u && lw < 9) {
+            unsigned need;
+            const unsigned* f = ep_dep(lats, nlat, total_tiles, ep, kn, lw, &need);
+            met = (f == nullptr) || ld_acquire_u32(f) >= need;
+          }
+          met = __all_sync(kFull, met);
+          if (lw == 0) ep_ctl[1] = met ? 1u : 0u;
+        }
+        if (cj < RC) {
           const bool own_p = cj >= D && cj < D + g.w;   // both columns or neither (D, w even)
 #pragma unroll
           for (int m = 0; m < PROWS; ++m) {
@@ -1621,6 +1628,13 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         }
       }
       __syncthreads();
+    }
+    if constexpr (EP) {
+      // the claimed items move up (every reader of these slots is behind a barrier)
+      if (tid == 0) {
+        ep_ctl[0] = ep_ctl[6];
+        ep_ctl[6] = ep_ctl[7];
+      }
     }
     if (s_over[0]) {
       // the counts of this region do not fit the 16-bit window (the host checks the
