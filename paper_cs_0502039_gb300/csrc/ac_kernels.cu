@@ -1119,6 +1119,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -1264,16 +1267,24 @@ __device__ __forceinline__ void ep_set_stop(DevCounters* ctr, unsigned s) {
 // ends the run if none has an arrival before t_end left.  Claiming: as ep_claim (an item
 // claimed while an error is reported is dropped).
 __device__ __forceinline__ unsigned ep_publish_claim(const LatDesc* lats, int nlat, int total, const EpArgs& ep,
-                                                     DevCounters* ctr, unsigned kp, bool live, bool claim) {
+                                                     DevCounters* ctr, unsigned kp, bool live, bool claim,
+                                                     bool fenced = false) {
   unsigned long long old = 0;
   int pe = -1;
   if (kp != ~0u) {
     const int tile = ep_tile(kp, total, &pe);
-    __threadfence();
+    // (fenced: the caller's fence after the CTA's barrier already orders the tile's stores,
+    // and a relaxed store completes the release)
+    if (!fenced) __threadfence();
     // (the verification hook that suppresses edge publication also withholds the epoch
     // words, so that the neighbours' bounded waits and the watchdog end the run)
     ACK(tile >= 0 && tile < total && pe < ep.max_epochs, 13, tile);
-    if (!lats[find_lattice(lats, nlat, tile)].drop_publish) st_release_u32(&ep.done[tile], (unsigned)pe + 1u);
+    if (!lats[find_lattice(lats, nlat, tile)].drop_publish) {
+      if (fenced)
+        st_relaxed_u32(&ep.done[tile], (unsigned)pe + 1u);
+      else
+        st_release_u32(&ep.done[tile], (unsigned)pe + 1u);
+    }
     old = atomicAdd(&ep.ep_count[pe], (1ull << 32) | (live ? 1ull : 0ull));
   }
   int err = 0;
@@ -1503,12 +1514,10 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const int x0 = wrap_index(g.c0 - D, Lcols, shx, 2);
         bulk_key_rows<RW>(K, key_in, 0, RH, g.r0 - D, Lrows, Lcols, x0, min(RC, Lcols - x0), RC, Ncells, ep_bar, tid);
       }
-      if (tid == 32) {
-        // meanwhile the next warp publishes the previous item and claims the item after
-        // the next one (the next one was claimed a visit ago)
-        ep_ctl[7] = ep_publish_claim(lats, nlat, total_tiles, ep, ctr, ep_ctl[3], ep_ctl[4] != 0u, ep_ctl[6] != ~0u);
-        ep_ctl[3] = ~0u;
-      }
+      // the next warp's first lane fences before its count loads (the tile's stores of
+      // the previous visit are then visible), publishes the previous item once the loads
+      // are in flight, and claims the item after the next one (claimed a visit ahead)
+      if (tid == 32 && ep_ctl[3] != ~0u) __threadfence();
     }
     // counts are kept as 16-bit offsets from a window start taken at the tile centre; the
     // thread's own-tile cells' offsets at load are summed (against the sum at the
@@ -1543,6 +1552,11 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
             gr += PSTRIDE;
             if (gr >= Lrows) gr -= Lrows;
           }
+        }
+        if (tid == 32) {
+          ep_ctl[7] = ep_publish_claim(lats, nlat, total_tiles, ep, ctr, ep_ctl[3], ep_ctl[4] != 0u, ep_ctl[6] != ~0u,
+                                       true);
+          ep_ctl[3] = ~0u;
         }
         if (tid >= 64 && tid < 96) {
           // with its counts in flight, warp 2 checks the next item's dependencies once
