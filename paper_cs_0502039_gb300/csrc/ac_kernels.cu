@@ -921,22 +921,26 @@ struct TbCfg {
 };
 
 // Order planes of the 4-neighbour array (one bit per lattice edge, packed 32 cells to a
-// word): H bit (i, j) says cell (i, j) precedes its right neighbour in (tick, index)
-// order, V bit (i, j) that it precedes the cell below, LV bit (i, j) that its tick is
-// below the commit bound.  Cell (i, j) is enabled (Fig. 3.2) iff H(i, j), V(i, j),
-// LV(i, j) are set and H(i, j-1), V(i-1, j) are clear, so a round's enable test is a
-// few word operations per 32 cells.  An edge's bit changes only when one of its two
-// cells commits, and the cells committed in one round are pairwise non-adjacent, so
-// every bit has at most one writer per round.  A committed cell's old bits are known
-// (it was enabled), so it updates them with xor masks.
+// word): H bit (i, j) says cell (i, j) is live (its tick below the commit bound) and
+// precedes its right neighbour in (tick, index) order, V bit (i, j) that it is live and
+// precedes the cell below.  Cell (i, j) is enabled (Fig. 3.2) iff H(i, j) and V(i, j)
+// are set and H(i, j-1), V(i-1, j) are clear, so a round's enable test is a few word
+// operations per 32 cells.  Folding liveness into the planes changes no decision: a cell
+// past the bound precedes no live cell, so clearing its bits never frees a live
+// neighbour, and its own clear bits keep it from being enabled.  An edge's bit changes
+// only when one of its two cells commits (a cell's liveness changes only with its own
+// key), and the cells committed in one round are pairwise non-adjacent, so every bit has
+// at most one writer per round.  A committed cell's old bits are known (it was enabled),
+// so it updates them with xor masks.  (LV is unused here; the other models keep it.)
 __device__ __forceinline__ void order_update(unsigned* H, unsigned* V, unsigned* LV, int W, int r, int c,
                                              unsigned long long nk, unsigned long long kl, unsigned long long kr,
                                              unsigned long long ku, unsigned long long kd, unsigned long long t2) {
   const unsigned long long lo = nk & ~1ull;
+  const bool live = nk < t2;
   const unsigned bit = 1u << (c & 31);
   const int wc = r * W + (c >> 5);
-  const unsigned hc = (lo <= kr) ? 0u : bit;           // no longer before the right neighbour
-  const bool hl = (kl & ~1ull) <= nk;                  // the left neighbour now precedes it
+  const unsigned hc = (live && lo <= kr) ? 0u : bit;   // no longer (live and) before the right neighbour
+  const bool hl = (kl & ~1ull) <= nk && kl < t2;       // the (live) left neighbour now precedes it
   if (c & 31) {
     const unsigned m = hc | (hl ? (bit >> 1) : 0u);
     if (m) atomicXor(&H[wc], m);
@@ -944,9 +948,8 @@ __device__ __forceinline__ void order_update(unsigned* H, unsigned* V, unsigned*
     if (hc) atomicXor(&H[wc], hc);
     if (hl) atomicXor(&H[wc - 1], 0x80000000u);
   }
-  if (!(lo <= kd)) atomicXor(&V[wc], bit);
-  if ((ku & ~1ull) <= nk) atomicXor(&V[wc - W], bit);
-  if (nk >= t2) atomicAnd(&LV[wc], ~bit);
+  if (!(live && lo <= kd)) atomicXor(&V[wc], bit);
+  if ((ku & ~1ull) <= nk && ku < t2) atomicXor(&V[wc - W], bit);
 }
 
 // (tick, lattice index) order of two cells from their keys and indices: the exact order
@@ -1728,9 +1731,12 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
             pv2 = lo <= K[(i + 2) * RW + lj];
           }
         }
-        const unsigned hb = __ballot_sync(kFull, ph);
-        const unsigned vb = __ballot_sync(kFull, pv);
-        const unsigned lb = __ballot_sync(kFull, kc < t2);
+        // the 4-neighbour array folds the bound into its two planes (a cell at or past the
+        // bound precedes nobody): H and V bits of a cell are set only while it is live
+        const bool lv = kc < t2;
+        const unsigned hb = __ballot_sync(kFull, MODEL == 0 ? (ph && lv) : ph);
+        const unsigned vb = __ballot_sync(kFull, MODEL == 0 ? (pv && lv) : pv);
+        const unsigned lb = MODEL == 0 ? 0u : __ballot_sync(kFull, lv);
         unsigned seb = 0u, swb = 0u, h2b = 0u, v2b = 0u;
         if (MODEL != 0) {
           seb = __ballot_sync(kFull, pse);
@@ -1744,7 +1750,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
           const int wi = i * W + (lj >> 5);
           OH[wi] = hb;
           OV[wi] = vb;
-          OL[wi] = lb;
+          if (MODEL != 0) OL[wi] = lb;
           if (MODEL != 0) {
             OSE[wi] = seb;
             OSW[wi] = swb;
@@ -1772,7 +1778,8 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
             ACK(wi >= qn * W && wi < RW * W, 7, wi);   // the words qn rows up exist
             const unsigned h = OH[wi];
             const unsigned hl = (h << 1) | (ow > 0 ? (OH[wi - 1] >> 31) : 0u);
-            unsigned m = h & ~hl & OV[wi] & ~OV[wu] & OL[wi] & cm;
+            unsigned m = h & ~hl & OV[wi] & ~OV[wu] & cm;
+            if (MODEL != 0) m &= OL[wi];
             if (MODEL != 0) {   // the diagonals: SE of the up-left cell, SW of the up-right cell
               const unsigned seu = (OSE[wu] << 1) | (ow > 0 ? (OSE[wu - 1] >> 31) : 0u);
               const unsigned swu = (OSW[wu] >> 1) | (ow + 1 < W ? (OSW[wu + 1] << 31) : 0u);
