@@ -1207,7 +1207,7 @@ __device__ __forceinline__ unsigned q_up(const unsigned long long* kp, int q) {
   return j;
 }
 
-// ---- epoch kernel control (one thread claims and publishes; threads 0..8 check the
+// ---- epoch kernel control (one thread claims and publishes; nine threads check the
 // nine dependencies of an item)
 
 // tile of work item k: epoch k / total, position k % total in the work list, rotated
@@ -1359,12 +1359,14 @@ __device__ __forceinline__ bool ep_wait(const LatDesc* lats, int nlat, int total
 // waits only on items claimed before it, so the schedule cannot deadlock, whatever
 // the number of resident CTAs.  Within an epoch, items go in work-list order, rotated
 // by half the list on odd epochs, so that an item's dependencies were claimed about
-// half an epoch earlier.  Region rows arrive by bulk asynchronous copies (the TMA
-// unit, through L2, never a stale L1 line); counts are read with ld.global.cg.
-// The control work is overlapped with the region load: while a visit's rows are in
-// flight, thread 0 publishes the CTA's previous item and claims the next one, whose
-// nine dependencies threads 0..8 check once; only if that check fails does the CTA
-// publish at once and wait at the end of the visit (so it never waits on itself).
+// half an epoch earlier.  Region keys arrive by the TMA unit (one 2D tensor copy for a
+// region inside the lattice, row copies across the torus seam; through L2, never a stale
+// L1 line); counts are read with ld.global.cg.  A CTA holds its claims one visit ahead,
+// and the control work overlaps the region load: while the copy and the count loads are
+// in flight, warp 1 publishes the CTA's previous item and claims the item after the next
+// one, and warp 2 checks the next item's nine dependencies once; only if that check fails
+// does the CTA, at the top of its next visit, publish at once and wait (so it never waits
+// on itself).
 template <int RW, bool FR, int MODEL, bool EP>
 __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     tb_kernel(const LatDesc* __restrict__ lats, int nlat, int total_tiles, int D, int R, DevCounters* ctr,
