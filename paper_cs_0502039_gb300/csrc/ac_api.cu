@@ -696,7 +696,7 @@ ac_status run_ep(ac_sim* s, long long t_end, bool* fallback) {
     } else {
       ep.nrange = 0;    // the first launch checked the window for the whole call
     }
-    AC_CUDA(ac::launch_ep(s->d_desc, 1, total, region, D, D, s->d_ctr, ep, s->stream, 0));
+    AC_CUDA(ac::launch_ep(s->d_desc, 1, total, region, D, D, s->d_ctr, ep, s->stream, 0, s->d_rates != nullptr));
     ac::DevCounters c{};
     AC_CUDA(cudaMemcpyAsync(&c, s->d_ctr, sizeof c, cudaMemcpyDeviceToHost, s->stream));
     AC_CUDA(cudaStreamSynchronize(s->stream));
@@ -1023,6 +1023,8 @@ ac_status batch_run_tb(int32_t n, ac_sim* const* sims, const int64_t* t_end, Bat
 // lattices advance by the same epochs of D rounds.
 ac_status batch_run_ep(int32_t n, ac_sim* const* sims, const int64_t* t_end, BatchRunner* R) {
   const cudaStream_t stream = R->stream;
+  bool any_rates = false;   // the rate-free kernel serves batches without per-cell rates
+  for (int i = 0; i < n; ++i) any_rates |= sims[i]->d_rates != nullptr;
   for (int i = 0; i < n; ++i) {
     ac_sim* s = sims[i];
     if (!s->key2) {
@@ -1098,7 +1100,7 @@ ac_status batch_run_ep(int32_t n, ac_sim* const* sims, const int64_t* t_end, Bat
   for (;;) {
     AC_CUDA(cudaMemcpyAsync(R->d_ctr, &c0, sizeof c0, cudaMemcpyHostToDevice, stream));
     AC_CUDA(cudaMemsetAsync(R->d_ep, 0, ep_words(total, E) * 4, stream));
-    AC_CUDA(ac::launch_ep(R->d_desc, n, total, R->region, D, D, R->d_ctr, ep, stream, 0));
+    AC_CUDA(ac::launch_ep(R->d_desc, n, total, R->region, D, D, R->d_ctr, ep, stream, 0, any_rates));
     ac::DevCounters c{};
     AC_CUDA(cudaMemcpyAsync(&c, R->d_ctr, sizeof c, cudaMemcpyDeviceToHost, stream));
     AC_CUDA(cudaStreamSynchronize(stream));

@@ -190,7 +190,7 @@ cudaError_t launch_tb(const LatDesc* d_desc, int nlat, int total_tiles, int regi
 // odd e.  Needs even cols, even halo, a cpair tiling whose tile sides are >= halo, and
 // 16-byte aligned key buffers (the region rows are loaded by bulk asynchronous copies).
 cudaError_t launch_ep(const LatDesc* d_desc, int nlat, int total_tiles, int region, int halo, int rounds,
-                      DevCounters* ctr, const EpArgs& ep, cudaStream_t s, int model = 0);
+                      DevCounters* ctr, const EpArgs& ep, cudaStream_t s, int model = 0, bool rates = true);
 // Bounds-checked build (-DAC_CHECK): the first index violation the kernels recorded since the
 // last call, (site << 40) | index, and clears it; always 0 in the production build.
 cudaError_t read_check_word(unsigned long long* word);

@@ -1367,7 +1367,9 @@ __device__ __forceinline__ bool ep_wait(const LatDesc* lats, int nlat, int total
 // one, and warp 2 checks the next item's nine dependencies once; only if that check fails
 // does the CTA, at the top of its next visit, publish at once and wait (so it never waits
 // on itself).
-template <int RW, bool FR, int MODEL, bool EP>
+// RATES: some lattice of the launch has per-cell rates (otherwise the commits skip the
+// rate test).
+template <int RW, bool FR, int MODEL, bool EP, bool RATES = true>
 __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
     tb_kernel(const LatDesc* __restrict__ lats, int nlat, int total_tiles, int D, int R, DevCounters* ctr,
               EpArgs ep) {
@@ -1888,7 +1890,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
         const Philox4 pa = philox_event(gia, base + c16a + 1u, 0u, seed_lo, seed_hi);
         const Philox4 pb = philox_event(gib, base + c16b + 1u, 0u, seed_lo, seed_hi);
         unsigned long long gapa = exp_ticks(pa.x, two), gapb = exp_ticks(pb.x, two);
-        if (L.rates) {
+        if (RATES && L.rates) {
           gapa = rated_gap(gapa, L.rates[gia]);
           gapb = rated_gap(gapb, L.rates[gib]);
         }
@@ -1947,7 +1949,7 @@ __global__ void __launch_bounds__(TbCfg<RW>::NT, TbCfg<RW>::MIN_CTAS)
           ns = sp ^ (b.y < thr[ACI(j + 5u * sp, 10, 9)] ? 1u : 0u);
         }
         unsigned long long gap = exp_ticks(b.x, two);
-        if (L.rates) gap = rated_gap(gap, L.rates[gidx]);
+        if (RATES && L.rates) gap = rated_gap(gap, L.rates[gidx]);
         const unsigned long long nk = (key & ~1ull) + (gap << 1) + ns;
         *kp = nk;
         C[r * RW + cc] = (unsigned short)(c16 + 1u);
@@ -2441,19 +2443,19 @@ cudaError_t tb_launch_rw(const LatDesc* d, int nlat, int total, int halo, int ro
   return cudaGetLastError();
 }
 
-template <int RW, int MODEL>
+template <int RW, int MODEL, bool RATES>
 cudaError_t ep_launch_rw(const LatDesc* d, int nlat, int total, int halo, int rounds, DevCounters* ctr,
                          const EpArgs& ep, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW, false, MODEL, true>,
+    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW, false, MODEL, true, RATES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TbCfg<RW>::bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int grid = std::min(total * ep.max_epochs, tb_grid(RW));
-  tb_kernel<RW, false, MODEL, true><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds,
-                                                                                  ctr, ep);
+  tb_kernel<RW, false, MODEL, true, RATES><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo,
+                                                                                         rounds, ctr, ep);
   return cudaGetLastError();
 }
 
@@ -2505,13 +2507,17 @@ cudaError_t launch_store_desc(const LatDesc& d, LatDesc* out, cudaStream_t s) {
 }
 
 cudaError_t launch_ep(const LatDesc* d, int nlat, int total, int region, int halo, int rounds, DevCounters* ctr,
-                      const EpArgs& ep, cudaStream_t s, int model) {
+                      const EpArgs& ep, cudaStream_t s, int model, bool rates) {
   if (halo < 2 || (halo & 1) || rounds < 1 || rounds > halo || 4 * halo >= region || total < 1 ||
       ep.max_epochs < 1 || (long long)total * ep.max_epochs >= (1ll << 31) || model != 0)
     return cudaErrorInvalidValue;
   switch (region) {
-    case 96: return ep_launch_rw<96, 0>(d, nlat, total, halo, rounds, ctr, ep, s);
-    case 128: return ep_launch_rw<128, 0>(d, nlat, total, halo, rounds, ctr, ep, s);
+    case 96:
+      return rates ? ep_launch_rw<96, 0, true>(d, nlat, total, halo, rounds, ctr, ep, s)
+                   : ep_launch_rw<96, 0, false>(d, nlat, total, halo, rounds, ctr, ep, s);
+    case 128:
+      return rates ? ep_launch_rw<128, 0, true>(d, nlat, total, halo, rounds, ctr, ep, s)
+                   : ep_launch_rw<128, 0, false>(d, nlat, total, halo, rounds, ctr, ep, s);
     default: return cudaErrorInvalidValue;
   }
 }
