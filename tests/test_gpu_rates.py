@@ -18,8 +18,11 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 ONE = ac.AC_RATE_ONE
-ROUND, BLOCKED = ac.AC_KERNEL_ROUND, ac.AC_KERNEL_BLOCKED
-CONFIGS = [(ROUND, 32, 1, 0), (ROUND, 64, 2, 0), (ROUND, 64, 6, 0), (BLOCKED, 32, 1, 8), (BLOCKED, 64, 1, 2)]
+ROUND, BLOCKED, EPOCH = ac.AC_KERNEL_ROUND, ac.AC_KERNEL_BLOCKED, ac.AC_KERNEL_EPOCH
+# (the epoch kernel needs even cols and rows, cols >= 4 x its halo; a handle outside that
+# runs the one-round kernel, which these cases then check as well)
+CONFIGS = [(ROUND, 32, 1, 0), (ROUND, 64, 2, 0), (ROUND, 64, 6, 0), (BLOCKED, 32, 1, 8), (BLOCKED, 64, 1, 2),
+           (EPOCH, 64, 4, 0), (EPOCH, 64, 6, 0)]
 
 
 def _rates(N, seed, lo=ONE // 8, hi=ONE * 8):
@@ -50,7 +53,7 @@ def test_rates_in_batches_and_reset():
     dims = [(40, 50), (96, 96), (130, 70)]
     ms = [_rates(r * c, 10 + i) for i, (r, c) in enumerate(dims)]
     refs = [_oracle(r, c, 0.44, 0.0, 20 + i, m, 3 * T32) for i, ((r, c), m) in enumerate(zip(dims, ms))]
-    for kernel, rounds in [(ROUND, 6), (BLOCKED, 1)]:
+    for kernel, rounds in [(ROUND, 6), (BLOCKED, 1), (EPOCH, 4)]:
         handles = ac.ac_batch_create([(r, c, 0) for r, c in dims], [0.44] * 3, [1.0] * 3, [0.0] * 3, [20, 21, 22])
         sims = [ac.Sim(r, c, 0.44, 1.0, 0.0, 20 + i, handle=h) for i, ((r, c), h) in enumerate(zip(dims, handles))]
         try:
@@ -119,3 +122,33 @@ def test_rates_with_frames_and_resume():
         sim.run_until(T)
         s, t, n = sim.read_state()
     assert_same(st, s, t, n, "rates after a reload")
+
+
+@pytest.mark.parametrize("kernel,rounds", [(ROUND, 6), (EPOCH, 4), (EPOCH, 6)])
+def test_rates_on_some_lattices_of_a_batch(kernel, rounds):
+    """A batch whose lattices mix per-cell rates and rate 1: the launch runs with rates, and
+    a lattice without them keeps its plain trajectory."""
+    dims = [(48, 64), (96, 96), (64, 130)]
+    ms = [_rates(48 * 64, 31), None, _rates(64 * 130, 33)]
+    refs = []
+    for i, ((r, c), m) in enumerate(zip(dims, ms)):
+        if m is None:
+            st = oracle.init(r, c, 0, 40 + i)
+            oracle.run(st, oracle.thresholds(0.44, 1.0, 0.0), 40 + i, 3 * T32)
+        else:
+            st = _oracle(r, c, 0.44, 0.0, 40 + i, m, 3 * T32)
+        refs.append(st)
+    handles = ac.ac_batch_create([(r, c, 0) for r, c in dims], [0.44] * 3, [1.0] * 3, [0.0] * 3, [40, 41, 42])
+    sims = [ac.Sim(r, c, 0.44, 1.0, 0.0, 40 + i, handle=h) for i, ((r, c), h) in enumerate(zip(dims, handles))]
+    try:
+        for sim, m in zip(sims, ms):
+            sim.configure(kernel, 64, rounds, 8)
+            if m is not None:
+                sim.set_rates(m)
+        ac.ac_batch_run_until([s.handle for s in sims], [3 * T32] * 3)
+        for sim, ref, m in zip(sims, refs, ms):
+            s, t, n = sim.read_state()
+            assert_same(ref, s, t, n, f"mixed batch kernel={kernel} rates={m is not None}")
+    finally:
+        for sim in sims:
+            sim.close()
