@@ -487,7 +487,8 @@ ac_status run_tb(ac_sim* s, long long t_end, int D, int R) {
   int launch_idx = 0;
   for (;;) {
     for (int i = 0; i < chunk; ++i) {
-      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, R, s->d_ctr, s->stream, s->f_B > 0, s->model));
+      AC_CUDA(ac::launch_tb(s->d_desc, 1, total, region, D, R, s->d_ctr, s->stream, s->f_B > 0, s->model,
+                            s->d_rates != nullptr));
       ++launch_idx;
     }
     ac::DevCounters cc{};
@@ -2077,7 +2078,7 @@ ac_status ac_slab_step(ac_sim* sim, int64_t t_end, int32_t* live) {
   AC_CUDA(cudaMemcpyAsync(sim->d_desc, &d, sizeof d, cudaMemcpyHostToDevice, sim->stream));
   AC_CUDA(cudaMemsetAsync(sim->d_ctr, 0, sizeof(ac::DevCounters), sim->stream));
   AC_CUDA(cudaEventRecord(sim->ev0, sim->stream));
-  AC_CUDA(ac::launch_tb(sim->d_desc, 1, tr * tc, region, R, R, sim->d_ctr, sim->stream, false, 0));
+  AC_CUDA(ac::launch_tb(sim->d_desc, 1, tr * tc, region, R, R, sim->d_ctr, sim->stream, false, 0, sim->d_rates != nullptr));
   AC_CUDA(cudaEventRecord(sim->ev1, sim->stream));
   ac::DevCounters c{};
   AC_CUDA(cudaMemcpyAsync(&c, sim->d_ctr, sizeof c, cudaMemcpyDeviceToHost, sim->stream));

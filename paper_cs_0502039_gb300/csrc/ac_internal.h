@@ -179,8 +179,10 @@ cudaError_t launch_pack(const LatDesc* host_desc, const int8_t* s_in, const long
 // model: the lattices' model (LatDesc::model; all lattices of a launch share it).
 // The q-th degree neighbourhood model shrinks the region by q rings per round:
 // halo = q * rounds.
+// rates = false: no lattice of the launch has per-cell rates (the 4-neighbour array without
+// frames then runs a kernel without the per-commit rate test); captured graphs keep true.
 cudaError_t launch_tb(const LatDesc* d_desc, int nlat, int total_tiles, int region, int halo, int rounds,
-                      DevCounters* ctr, cudaStream_t s, bool frames = false, int model = 0);
+                      DevCounters* ctr, cudaStream_t s, bool frames = false, int model = 0, bool rates = true);
 // One launch of the epoch kernel: the temporal-blocked tile visit of launch_tb run as a
 // persistent dataflow over (epoch, tile) work items.  Each item advances one tile by
 // `rounds` synchronous rounds; it starts once the tile and its 8 neighbours have

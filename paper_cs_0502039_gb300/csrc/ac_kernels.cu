@@ -2427,19 +2427,19 @@ cudaError_t launch_pack(const LatDesc* h, const int8_t* si, const long long* ti,
 }
 
 
-template <int RW, bool FR, int MODEL>
+template <int RW, bool FR, int MODEL, bool RATES = true>
 cudaError_t tb_launch_rw(const LatDesc* d, int nlat, int total, int halo, int rounds, DevCounters* ctr,
                          cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW, FR, MODEL, false>,
+    cudaError_t e = cudaFuncSetAttribute(tb_kernel<RW, FR, MODEL, false, RATES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TbCfg<RW>::bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int grid = std::min(total, tb_grid(RW));
-  tb_kernel<RW, FR, MODEL, false><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds, ctr,
-                                                                                EpArgs{});
+  tb_kernel<RW, FR, MODEL, false, RATES><<<grid, TbCfg<RW>::NT, TbCfg<RW>::bytes, s>>>(d, nlat, total, halo, rounds,
+                                                                                       ctr, EpArgs{});
   return cudaGetLastError();
 }
 
@@ -2461,28 +2461,31 @@ cudaError_t ep_launch_rw(const LatDesc* d, int nlat, int total, int halo, int ro
 
 template <int RW, int MODEL>
 cudaError_t tb_launch_frames(const LatDesc* d, int nlat, int total, int halo, int rounds, DevCounters* ctr,
-                             cudaStream_t s, bool frames) {
+                             cudaStream_t s, bool frames, bool rates) {
+  if constexpr (MODEL == 0) {   // the Ising array without frames or rates: the rate-free kernel
+    if (!frames && !rates) return tb_launch_rw<RW, false, 0, false>(d, nlat, total, halo, rounds, ctr, s);
+  }
   return frames ? tb_launch_rw<RW, true, MODEL>(d, nlat, total, halo, rounds, ctr, s)
                 : tb_launch_rw<RW, false, MODEL>(d, nlat, total, halo, rounds, ctr, s);
 }
 
 template <int RW>
 cudaError_t tb_launch_model(const LatDesc* d, int nlat, int total, int halo, int rounds, DevCounters* ctr,
-                            cudaStream_t s, bool frames, int model) {
+                            cudaStream_t s, bool frames, int model, bool rates) {
   switch (model) {
-    case 0: return tb_launch_frames<RW, 0>(d, nlat, total, halo, rounds, ctr, s, frames);
-    case 1: return tb_launch_frames<RW, 1>(d, nlat, total, halo, rounds, ctr, s, frames);
-    case 2: return tb_launch_frames<RW, 2>(d, nlat, total, halo, rounds, ctr, s, frames);
+    case 0: return tb_launch_frames<RW, 0>(d, nlat, total, halo, rounds, ctr, s, frames, rates);
+    case 1: return tb_launch_frames<RW, 1>(d, nlat, total, halo, rounds, ctr, s, frames, rates);
+    case 2: return tb_launch_frames<RW, 2>(d, nlat, total, halo, rounds, ctr, s, frames, rates);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_tb(const LatDesc* d, int nlat, int total, int region, int halo, int rounds, DevCounters* ctr,
-                      cudaStream_t s, bool frames, int model) {
+                      cudaStream_t s, bool frames, int model, bool rates) {
   if (halo < 1 || rounds < 1 || rounds > halo || 4 * halo >= region) return cudaErrorInvalidValue;
   switch (region) {
-    case 96: return tb_launch_model<96>(d, nlat, total, halo, rounds, ctr, s, frames, model);
-    case 128: return tb_launch_model<128>(d, nlat, total, halo, rounds, ctr, s, frames, model);
+    case 96: return tb_launch_model<96>(d, nlat, total, halo, rounds, ctr, s, frames, model, rates);
+    case 128: return tb_launch_model<128>(d, nlat, total, halo, rounds, ctr, s, frames, model, rates);
     default: return cudaErrorInvalidValue;
   }
 }
